@@ -1,0 +1,520 @@
+/*
+ * sc_oracle.c -- plain, slow, FP64 CPU oracle for the physical-optics
+ * Stratton-Chu focal field of a parabolic mirror.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or
+ * call this file: only the test-suite, the smoke check and the CPU-baseline
+ * leg of the benchmark use it.  It shares no code, header, table or constant
+ * generator with the CUDA library; it is written directly from the paper
+ * (Dumont et al., "Efficiently parallelized modeling of tightly focused,
+ * large bandwidth laser pulses", arXiv:1609.08146):
+ *
+ *   - Sec. II, Eq. 11 (label eq:theory.stratton-chu-poa-og): reflected field
+ *     E' = 2 SS { ik (n x B_inc) g + (n . E_inc) grad g } dS
+ *          - (2/ik) O grad g [n x (n x B_inc)] . dl
+ *     B' = 2 SS (n x B_inc) x grad g dS
+ *   - Sec. II, Eq. 2: g = exp(ik|r - r'|) / (4 pi |r - r'|)
+ *   - Sec. II, Eq. 10 (label eq:theory.stratton-chu-poa) with the dyadic of
+ *     Appendix A (eq:singularInt.doubleGradientExp): the "double-gradient"
+ *     form, kept here as an independent second oracle.
+ *   - Sec. III.A: incident field on the mirror, beam travelling along -z,
+ *     mirror given as z = F(r, theta) in cylindrical coordinates.
+ *   - Sec. III.B, Eqs. 12-18: Fourier convention exp(-ikt), semi-discrete
+ *     inverse transform, per-component amplitude from a power spectrum
+ *     (Eq. 16) and a spectral phase map (Eq. 18).
+ *   - Sec. III.C.1, Eq. 21: the paraboloid z = r^2/(4f) - f with its focus at
+ *     the origin; Sec. III.C.1: tensor-product Gauss-Legendre quadrature.
+ *   - Sec. IV.B, Eq. 27: super-Gaussian power spectrum in wavelength.
+ *
+ * Readings of passages the paper leaves open (its Supplementary Material,
+ * which holds the explicit incident fields, is not available):
+ *   R1  grad acts on the surface variable r: grad g = (ik - 1/R) g (r-r')/R
+ *       (Appendix A defines R = r - r').
+ *   R2  the unit normal points to the illuminated side (+z at the vertex).
+ *   R3  the boundary curve is oriented counter-clockwise seen from the side
+ *       the normal points to (Stokes' theorem), so the outer rim runs with
+ *       increasing theta and an inner rim (r_min > 0) with decreasing theta.
+ *   R4  the incident beam is collimated: E_inc = A(rho) p(theta)
+ *       exp(-ik(z + z_ref)) exp(ik W), B_inc = (-z) x E_inc, with
+ *       z_ref = 2f for the paraboloid (so the geometric focal arrival is at
+ *       t = 0) and z_ref = -z0 for the flat test mirror.  A is Gaussian
+ *       exp(-rho^2/w0^2), super-Gaussian exp(-(rho/w0)^(2N)) or a top-hat;
+ *       p is a fixed linear direction, rho_hat (radial) or theta_hat
+ *       (azimuthal), the last two times rho/w0.  W is the optical path
+ *       difference of a Zernike expansion (Noll ordering) on the unit disk
+ *       rho / r_norm, coefficients in waves at lambda0.
+ *   R5  the super-Gaussian of Eq. 27 carries a minus sign in its exponent;
+ *       energy per unit k includes |d lambda / dk| = lambda^2 / (2 pi).
+ *   R6  units: lambda0 = c = 1, k = 2 pi omega with omega in units of
+ *       omega0 = 2 pi c / lambda0; time in lambda0 / c.
+ *
+ * Output layout: E[n_omega][n_pts][3] complex, stored as interleaved doubles
+ * (re, im); same for B.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+
+#define OR_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------ */
+/* Parameter blocks (mirrored by ctypes structures in oracle/__init__.py).   */
+
+typedef struct {
+    int surface;      /* 0: paraboloid z = r^2/(4f) - f; 1: flat disk z = z0 */
+    int n_r;          /* Gauss-Legendre nodes in r on [r_min, r_max]          */
+    int n_theta;      /* trapezoid nodes in theta, theta_l = 2 pi l / n_theta  */
+    int rim;          /* 1: include the boundary line integral of Eq. 11      */
+    double f;         /* focal length                                          */
+    double z0;        /* plane height of the flat test mirror                  */
+    double r_min;
+    double r_max;
+} or_mirror;
+
+typedef struct {
+    int profile;      /* 0 Gaussian, 1 super-Gaussian, 2 top-hat              */
+    int sg_order;     /* N of exp(-(rho/w0)^(2N))                              */
+    int pol;          /* 0 linear, 1 radial, 2 azimuthal                      */
+    int n_zern;       /* number of Zernike coefficients, Noll j = 2 ..         */
+    double w0;
+    double pol_angle; /* direction of linear polarisation in the xy-plane      */
+    double r_norm;    /* radius of the Zernike unit disk (and top-hat radius)  */
+    const double* zern;
+} or_beam;
+
+/* ------------------------------------------------------------------------ */
+/* Gauss-Legendre rule on [a, b] (the quadrature named in Sec. III.C.1):     */
+/* nodes are the roots of the Legendre polynomial P_n, found by Newton's    */
+/* method from the three-term recurrence; w_i = 2 / ((1 - x^2) P_n'(x)^2).   */
+
+int or_gauss_legendre(int n, double a, double b, double* x, double* w)
+{
+    if (n < 1) return 1;
+    for (int i = 0; i < n; ++i) {
+        double t = cos(OR_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (int j = 2; j <= n; ++j) {
+                double p2 = ((2.0 * j - 1.0) * t * p1 - (j - 1.0) * p0) / j;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) { p1 = t; p0 = 1.0; }
+            /* P_n(t) = p1, P_{n-1}(t) = p0 */
+            dp = n * (t * p1 - p0) / (t * t - 1.0);
+            double dt = p1 / dp;
+            t -= dt;
+            if (fabs(dt) < 1e-16) break;
+        }
+        /* recompute the derivative at the converged root */
+        {
+            double p0 = 1.0, p1 = t;
+            for (int j = 2; j <= n; ++j) {
+                double p2 = ((2.0 * j - 1.0) * t * p1 - (j - 1.0) * p0) / j;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) { p1 = t; p0 = 1.0; }
+            dp = n * (t * p1 - p0) / (t * t - 1.0);
+        }
+        double wi = 2.0 / ((1.0 - t * t) * dp * dp);
+        /* roots come out in decreasing t; store ascending */
+        int k = n - 1 - i;
+        x[k] = 0.5 * (a + b) + 0.5 * (b - a) * t;
+        w[k] = 0.5 * (b - a) * wi;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Zernike polynomials, Noll (1976) ordering and normalisation.              */
+
+static void noll_to_nm(int j, int* n_out, int* m_out)
+{
+    int jj = 1;
+    for (int n = 0;; ++n) {
+        for (int am = n % 2; am <= n; am += 2) {
+            if (am == 0) {
+                if (jj == j) { *n_out = n; *m_out = 0; return; }
+                jj += 1;
+            } else {
+                /* the even index of the pair carries cos (m > 0), the odd sin */
+                if (jj == j) { *n_out = n; *m_out = (jj % 2 == 0) ? am : -am; return; }
+                if (jj + 1 == j) { *n_out = n; *m_out = ((jj + 1) % 2 == 0) ? am : -am; return; }
+                jj += 2;
+            }
+        }
+    }
+}
+
+static double factorial(int n)
+{
+    double r = 1.0;
+    for (int i = 2; i <= n; ++i) r *= i;
+    return r;
+}
+
+double or_zernike(int j, double rho, double theta)
+{
+    int n, m;
+    noll_to_nm(j, &n, &m);
+    int am = abs(m);
+    double radial = 0.0;
+    for (int s = 0; s <= (n - am) / 2; ++s) {
+        double c = factorial(n - s) /
+                   (factorial(s) * factorial((n + am) / 2 - s) * factorial((n - am) / 2 - s));
+        radial += ((s % 2) ? -c : c) * pow(rho, n - 2 * s);
+    }
+    if (m == 0) return sqrt(n + 1.0) * radial;
+    double ang = (m > 0) ? cos(am * theta) : sin(am * theta);
+    return sqrt(2.0 * (n + 1.0)) * radial * ang;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Incident field model (reading R4).                                        */
+
+static double beam_amplitude(const or_beam* bm, double rho)
+{
+    switch (bm->profile) {
+    case 0: return exp(-(rho * rho) / (bm->w0 * bm->w0));
+    case 1: return exp(-pow(rho / bm->w0, 2.0 * bm->sg_order));
+    default: return (rho <= bm->r_norm) ? 1.0 : 0.0;
+    }
+}
+
+/* spatial part of E_inc at (x, y): A(rho) p(theta), a real transverse vector */
+static void beam_field(const or_beam* bm, double x, double y, double e[3])
+{
+    double rho = sqrt(x * x + y * y);
+    double a = beam_amplitude(bm, rho);
+    double th = atan2(y, x);
+    if (bm->pol == 0) {
+        e[0] = a * cos(bm->pol_angle);
+        e[1] = a * sin(bm->pol_angle);
+    } else if (bm->pol == 1) {
+        double s = a * rho / bm->w0;
+        e[0] = s * cos(th);
+        e[1] = s * sin(th);
+    } else {
+        double s = a * rho / bm->w0;
+        e[0] = -s * sin(th);
+        e[1] = s * cos(th);
+    }
+    e[2] = 0.0;
+}
+
+/* optical path difference W(x, y) = sum_j c_j Z_j(rho / r_norm, theta) */
+static double beam_opd(const or_beam* bm, double x, double y)
+{
+    if (bm->n_zern <= 0) return 0.0;
+    double rho = sqrt(x * x + y * y) / bm->r_norm;
+    double th = atan2(y, x);
+    double w = 0.0;
+    for (int i = 0; i < bm->n_zern; ++i) w += bm->zern[i] * or_zernike(i + 2, rho, th);
+    return w;
+}
+
+/* beam power integral SS |f_E|^2 dA over the transverse plane (Eq. 16 with
+ * Re(f_E x f_B*) . dA = |f_E|^2 dA for the collimated beam), by plain
+ * trapezoid quadrature in rho on a fine grid -- deliberately numerical. */
+double or_beam_power(const or_beam* bm)
+{
+    double rmax;
+    if (bm->profile == 2) rmax = bm->r_norm;
+    else rmax = 12.0 * bm->w0;
+    int n = 400000;
+    double h = rmax / n, s = 0.0;
+    for (int i = 0; i <= n; ++i) {
+        double rho = i * h;
+        double e[3];
+        beam_field(bm, rho, 0.0, e);
+        double v = (e[0] * e[0] + e[1] * e[1]) * 2.0 * OR_PI * rho;
+        s += (i == 0 || i == n) ? 0.5 * v : v;
+    }
+    return s * h;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Mirror geometry (Sec. III.A, Eq. 21).                                     */
+
+static double surf_z(const or_mirror* m, double r)
+{
+    return (m->surface == 0) ? (r * r / (4.0 * m->f) - m->f) : m->z0;
+}
+
+/* reference of the incident phase: E_inc ~ exp(-ik(z + z_ref)) */
+static double surf_zref(const or_mirror* m)
+{
+    return (m->surface == 0) ? 2.0 * m->f : -m->z0;
+}
+
+/* unnormalised normal (-dz/dx, -dz/dy, 1); its length is the area factor */
+static void surf_normal(const or_mirror* m, double x, double y, double nvec[3])
+{
+    if (m->surface == 0) {
+        nvec[0] = -x / (2.0 * m->f);
+        nvec[1] = -y / (2.0 * m->f);
+    } else {
+        nvec[0] = 0.0;
+        nvec[1] = 0.0;
+    }
+    nvec[2] = 1.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Small complex-vector helpers.                                             */
+
+static void ccross(const cplx a[3], const cplx b[3], cplx c[3])
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* ------------------------------------------------------------------------ */
+/* One frequency, one observation point.                                     */
+
+/* Eq. 11 (form 0) or Eq. 10 with the Appendix-A dyadic (form 1). */
+static void field_at(const or_mirror* m, const or_beam* bm, int form, double k,
+                     const double* gl_r, const double* gl_w, const double rp[3],
+                     cplx E[3], cplx B[3])
+{
+    for (int c = 0; c < 3; ++c) { E[c] = 0.0; B[c] = 0.0; }
+    const double dth = 2.0 * OR_PI / m->n_theta;
+    const double zref = surf_zref(m);
+
+    /* surface integrals */
+    for (int i = 0; i < m->n_r; ++i) {
+        double r = gl_r[i];
+        for (int l = 0; l < m->n_theta; ++l) {
+            double th = l * dth;
+            double x = r * cos(th), y = r * sin(th), z = surf_z(m, r);
+            double nv[3];
+            surf_normal(m, x, y, nv);
+            double nlen = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+            double nhat[3] = {nv[0] / nlen, nv[1] / nlen, nv[2] / nlen};
+            /* dS = |N| r dr dtheta for z = F(r, theta) */
+            double dS = nlen * r * gl_w[i] * dth;
+
+            double es[3];
+            beam_field(bm, x, y, es);
+            double W = beam_opd(bm, x, y);
+            double d[3] = {x - rp[0], y - rp[1], z - rp[2]};
+            double R = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double Rh[3] = {d[0] / R, d[1] / R, d[2] / R};
+            /* exp(ikR) of g and exp(-ik(z + z_ref)) exp(ikW) of E_inc, joined in
+             * one exponential so that the FP64 phase keeps its accuracy */
+            cplx ph = cexp(I * k * (R - (z + zref) + W));
+            /* E_inc and B_inc = (-z) x E_inc at the node, with g's phase attached */
+            cplx Einc[3] = {es[0] * ph, es[1] * ph, 0.0};
+            cplx Binc[3] = {es[1] * ph, -es[0] * ph, 0.0};
+            cplx nh[3] = {nhat[0], nhat[1], nhat[2]};
+            cplx J[3];
+            ccross(nh, Binc, J); /* n x B_inc */
+            double g0 = 1.0 / (4.0 * OR_PI * R); /* |g| */
+            cplx dg = (I * k - 1.0 / R) * g0;    /* grad g = dg * Rhat */
+
+            if (form == 0) {
+                cplx sigma = nh[0] * Einc[0] + nh[1] * Einc[1] + nh[2] * Einc[2];
+                for (int c = 0; c < 3; ++c)
+                    E[c] += 2.0 * (I * k * J[c] * g0 + sigma * dg * Rh[c]) * dS;
+            } else {
+                /* (i/k) grad grad g . J with the Appendix-A dyadic */
+                cplx a_iso = -(-I * k / R + 1.0 / (R * R)) * g0;
+                cplx a_rr = (3.0 / (R * R) - 3.0 * I * k / R - k * k) * g0;
+                cplx RJ = Rh[0] * J[0] + Rh[1] * J[1] + Rh[2] * J[2];
+                for (int c = 0; c < 3; ++c)
+                    E[c] += 2.0 * (I * k * J[c] * g0 +
+                                   (I / k) * (a_iso * J[c] + a_rr * Rh[c] * RJ)) * dS;
+            }
+            cplx gg[3] = {dg * Rh[0], dg * Rh[1], dg * Rh[2]};
+            cplx JxG[3];
+            ccross(J, gg, JxG);
+            for (int c = 0; c < 3; ++c) B[c] += 2.0 * JxG[c] * dS;
+        }
+    }
+
+    /* boundary line integral of Eq. 11, -(2/ik) O grad g [n x (n x B_inc)] . dl */
+    if (form == 0 && m->rim) {
+        for (int edge = 0; edge < 2; ++edge) {
+            double r = (edge == 0) ? m->r_max : m->r_min;
+            double orient = (edge == 0) ? 1.0 : -1.0; /* reading R3 */
+            if (r <= 0.0) continue;
+            for (int l = 0; l < m->n_theta; ++l) {
+                double th = l * dth;
+                double x = r * cos(th), y = r * sin(th), z = surf_z(m, r);
+                double nv[3];
+                surf_normal(m, x, y, nv);
+                double nlen = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+                cplx nh[3] = {nv[0] / nlen, nv[1] / nlen, nv[2] / nlen};
+                /* tangent dP/dtheta = (-r sin, r cos, 0); dl = tangent * dtheta */
+                double dl[3] = {-r * sin(th) * dth * orient, r * cos(th) * dth * orient, 0.0};
+
+                double es[3];
+                beam_field(bm, x, y, es);
+                double W = beam_opd(bm, x, y);
+                double d[3] = {x - rp[0], y - rp[1], z - rp[2]};
+                double R = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                double Rh[3] = {d[0] / R, d[1] / R, d[2] / R};
+                cplx ph = cexp(I * k * (R - (z + zref) + W));
+                cplx Binc[3] = {es[1] * ph, -es[0] * ph, 0.0};
+                cplx t1[3], t2[3];
+                ccross(nh, Binc, t1);
+                ccross(nh, t1, t2); /* n x (n x B_inc) */
+                cplx proj = t2[0] * dl[0] + t2[1] * dl[1] + t2[2] * dl[2];
+                cplx dg = (I * k - 1.0 / R) / (4.0 * OR_PI * R);
+                for (int c = 0; c < 3; ++c) E[c] += -(2.0 / (I * k)) * dg * Rh[c] * proj;
+            }
+        }
+    }
+}
+
+/*
+ * Reflected spectral field at n_pts observation points for n_omega
+ * frequencies.  amp (nullable) holds complex a_n = E0^n exp(i phi) as
+ * interleaved doubles; NULL means a_n = 1 (the spatial integrals alone).
+ * form 0 = Eq. 11 (with its line integral when mirror->rim), form 1 = Eq. 10.
+ * Returns 0 on success, nonzero on invalid input.
+ */
+int or_field(const or_mirror* m, const or_beam* bm, int form, int n_omega, const double* omega,
+             const double* amp, int n_pts, const double* pts, double* E_out, double* B_out,
+             int nthreads)
+{
+    if (m->n_r < 1 || m->n_theta < 1 || m->r_max <= m->r_min || m->r_min < 0.0) return 1;
+    if (m->surface == 0 && m->f <= 0.0) return 1;
+    double* gl_r = (double*)malloc(sizeof(double) * m->n_r);
+    double* gl_w = (double*)malloc(sizeof(double) * m->n_r);
+    or_gauss_legendre(m->n_r, m->r_min, m->r_max, gl_r, gl_w);
+    long total = (long)n_omega * n_pts;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (long idx = 0; idx < total; ++idx) {
+        int n = (int)(idx / n_pts), p = (int)(idx % n_pts);
+        double k = 2.0 * OR_PI * omega[n];
+        cplx E[3], B[3];
+        field_at(m, bm, form, k, gl_r, gl_w, pts + 3 * p, E, B);
+        cplx a = 1.0;
+        if (amp) a = amp[2 * n] + I * amp[2 * n + 1];
+        for (int c = 0; c < 3; ++c) {
+            cplx e = a * E[c], b = a * B[c];
+            long o = 2 * ((idx) * 3 + c);
+            E_out[o] = creal(e);
+            E_out[o + 1] = cimag(e);
+            B_out[o] = creal(b);
+            B_out[o + 1] = cimag(b);
+        }
+    }
+    free(gl_r);
+    free(gl_w);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Spectrum (Sec. III.B, Eqs. 14-18; Sec. IV.B, Eq. 27).                     */
+
+/* power spectrum per unit k, unnormalised */
+static double spectrum_shape(int kind, double k, double fwhm_t, double lambda_c, double dlambda,
+                             int sg_n)
+{
+    double kc = 2.0 * OR_PI / lambda_c;
+    if (kind == 1) {
+        /* Gaussian pulse of intensity FWHM fwhm_t: field spectrum
+         * exp(-(k-kc)^2 tau^2 / (8 ln 2)), power its square */
+        double s = exp(-(k - kc) * (k - kc) * fwhm_t * fwhm_t / (8.0 * log(2.0)));
+        return s * s;
+    }
+    if (kind == 2) {
+        /* Eq. 27 with the minus sign (reading R5), times |d lambda/dk| */
+        if (k <= 0.0) return 0.0;
+        double lam = 2.0 * OR_PI / k;
+        double u = (lam - lambda_c) / dlambda;
+        return exp(-pow(u * u, (double)sg_n)) * lam * lam / (2.0 * OR_PI);
+    }
+    return 0.0;
+}
+
+/*
+ * Complex amplitudes a_n = E0^n exp(i phi(k_n)) at the given omegas.
+ * kind: 0 monochromatic (E0 = 1), 1 Gaussian in time, 2 super-Gaussian in
+ * lambda, 3 sampled (amp_in holds the amplitudes).  For kinds 1 and 2 the
+ * power spectrum is normalised to int eps(k) dk = energy (Eq. 17, by
+ * numerical quadrature) and E0^n = sqrt(eps(k_n) / (4 pi P)) (Eq. 16) with
+ * P = beam_power.  phi(k) = sum_j phi_j (k - kc)^j / j!  (Eq. 18).
+ */
+int or_spectrum(int kind, double fwhm_t, double lambda_c, double dlambda, int sg_n, double energy,
+                double beam_power, int n_phi, const double* phi, int n, const double* omega,
+                const double* amp_in, double* amp_out)
+{
+    double kc = 2.0 * OR_PI / lambda_c;
+    double norm = 1.0;
+    if (kind == 1 || kind == 2) {
+        /* trapezoid over a wide k window */
+        double k_lo = 1e-3 * kc, k_hi = 6.0 * kc;
+        int m = 2000000;
+        double h = (k_hi - k_lo) / m, s = 0.0;
+        for (int i = 0; i <= m; ++i) {
+            double v = spectrum_shape(kind, k_lo + i * h, fwhm_t, lambda_c, dlambda, sg_n);
+            s += (i == 0 || i == m) ? 0.5 * v : v;
+        }
+        norm = s * h;
+        if (!(norm > 0.0)) return 1;
+    }
+    for (int i = 0; i < n; ++i) {
+        double k = 2.0 * OR_PI * omega[i];
+        cplx a;
+        if (kind == 0) a = 1.0;
+        else if (kind == 3) a = amp_in[2 * i] + I * amp_in[2 * i + 1];
+        else {
+            double eps = energy * spectrum_shape(kind, k, fwhm_t, lambda_c, dlambda, sg_n) / norm;
+            a = sqrt(eps / (4.0 * OR_PI * beam_power));
+        }
+        double ph = 0.0, term = 1.0;
+        for (int j = 0; j < n_phi; ++j) {
+            if (j > 0) term *= (k - kc) / j;
+            ph += phi[j] * term;
+        }
+        a *= cexp(I * ph);
+        amp_out[2 * i] = creal(a);
+        amp_out[2 * i + 1] = cimag(a);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Semi-discrete inverse transform (Sec. III.B, Eq. 13).                      */
+/* F(t) = sum_{n=-N..N} F_n exp(-i k_n t) dk over a real field, i.e.          */
+/* 2 Re sum_{n>=1} F_n exp(-i k_n t) dk for positive k_n; dk = k_1 - k_0      */
+/* (uniform grid) or 1 for a single frequency.                                */
+
+int or_time_domain(int n_omega, const double* omega, long n_vals, const double* F, int n_t,
+                   const double* t, double* out, int nthreads)
+{
+    double dk = (n_omega > 1) ? 2.0 * OR_PI * (omega[1] - omega[0]) : 1.0;
+    long total = (long)n_t * n_vals;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(static)
+#endif
+    for (long idx = 0; idx < total; ++idx) {
+        int m = (int)(idx / n_vals);
+        long v = idx % n_vals;
+        cplx s = 0.0;
+        for (int n = 0; n < n_omega; ++n) {
+            double k = 2.0 * OR_PI * omega[n];
+            cplx Fn = F[2 * (n * n_vals + v)] + I * F[2 * (n * n_vals + v) + 1];
+            s += Fn * cexp(-I * k * t[m]);
+        }
+        out[idx] = 2.0 * creal(s) * dk;
+    }
+    return 0;
+}

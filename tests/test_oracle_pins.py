@@ -1,0 +1,412 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Every check here is independent of the oracle's own code path: closed forms
+derived by hand from Eq. 11 (Sec. II) for cases where the surface integral
+is elementary, textbook/library routines (Gauss-Legendre from numpy, Noll's
+Zernike table), identities that hold exactly for any incident field
+(Faraday's law), the equivalence of the two PO forms (Eqs. 10 and 11) for a
+Maxwell incident field, exact discrete symmetries, and the printed worked
+example of Sec. IV.B.  A plausible slip in the oracle (a sign of grad g, a
+transposed cross product, a dropped boundary term, a wrong normal, rim
+orientation or weight) breaks at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+K0 = 2.0 * math.pi
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# Quadrature and special functions
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 16, 64])
+def test_gauss_legendre_matches_numpy(n):
+    x, w = oracle.gauss_legendre(n)
+    xr, wr = np.polynomial.legendre.leggauss(n)
+    assert np.max(abs(x - xr)) < 1e-14
+    assert np.max(abs(w - wr)) < 1e-14
+
+
+def test_gauss_legendre_exact_degree():
+    # an n-point rule integrates x^d exactly for d <= 2n-1 on [a, b]
+    n, a, b = 7, 0.3, 2.9
+    x, w = oracle.gauss_legendre(n, a, b)
+    for d in range(2 * n):
+        exact = (b ** (d + 1) - a ** (d + 1)) / (d + 1)
+        assert abs(np.dot(w, x ** d) - exact) < 1e-12 * max(1.0, abs(exact))
+    d = 2 * n
+    exact = (b ** (d + 1) - a ** (d + 1)) / (d + 1)
+    assert abs(np.dot(w, x ** d) - exact) > 1e-10  # and not degree 2n
+
+
+def test_zernike_noll_table():
+    # Noll (1976), Table 1: explicit low orders
+    r, t = 0.63, 0.41
+    want = {
+        2: 2 * r * math.cos(t),
+        3: 2 * r * math.sin(t),
+        4: math.sqrt(3) * (2 * r * r - 1),
+        5: math.sqrt(6) * r * r * math.sin(2 * t),
+        6: math.sqrt(6) * r * r * math.cos(2 * t),
+        7: math.sqrt(8) * (3 * r ** 3 - 2 * r) * math.sin(t),
+        8: math.sqrt(8) * (3 * r ** 3 - 2 * r) * math.cos(t),
+        9: math.sqrt(8) * r ** 3 * math.sin(3 * t),
+        10: math.sqrt(8) * r ** 3 * math.cos(3 * t),
+        11: math.sqrt(5) * (6 * r ** 4 - 6 * r * r + 1),
+        12: math.sqrt(10) * (4 * r ** 4 - 3 * r * r) * math.cos(2 * t),
+        13: math.sqrt(10) * (4 * r ** 4 - 3 * r * r) * math.sin(2 * t),
+        14: math.sqrt(10) * r ** 4 * math.cos(4 * t),
+        15: math.sqrt(10) * r ** 4 * math.sin(4 * t),
+    }
+    for j, v in want.items():
+        assert abs(oracle.zernike(j, r, t) - v) < 1e-13, j
+
+
+@pytest.mark.parametrize(
+    "beam,closed",
+    [
+        (dict(profile="gauss", pol="linear", w0=3.0), math.pi * 9.0 / 2),
+        (dict(profile="gauss", pol="radial", w0=3.0), math.pi * 9.0 / 4),
+        (dict(profile="supergauss", sg_order=4, pol="linear", w0=2.0),
+         math.pi * 4.0 * 2 ** (-1 / 4) * math.gamma(1 + 1 / 4)),
+        (dict(profile="supergauss", sg_order=4, pol="azimuthal", w0=2.0),
+         math.pi * 4.0 * 2 ** (-2 / 4) * math.gamma(1 + 2 / 4) / 2),
+        (dict(profile="tophat", pol="linear", w0=1.0, r_norm=5.0), math.pi * 25.0),
+    ],
+)
+def test_beam_power_closed_forms(beam, closed):
+    # SS |f_E|^2 dA (the denominator of Eq. 16) against its closed form
+    assert abs(oracle.beam_power(beam) - closed) < 1e-6 * closed
+
+
+# --------------------------------------------------------------------------
+# Closed forms at the focus (hand-derived from Eq. 11; substitution
+# R = f + r^2/(4f), r dr = 2f dR makes every radial integral elementary)
+
+
+def _focus(mirror, beam, omega):
+    E, B = oracle.field(mirror, beam, [omega], [[0.0, 0.0, 0.0]])
+    return E[0, 0], B[0, 0]
+
+
+@pytest.mark.parametrize("f,a,omega", [(20.0, 30.0, 1.0), (5.0, 10.0, 0.7), (50.0, 12.0, 1.4)])
+def test_paraboloid_focus_linear_tophat(f, a, omega):
+    """x-polarised plane wave on the paraboloid, field at the focus.
+
+    E_x = 2(ikf+1)(1-f/R_a) - (1-f^2/R_a^2) - (a^2/(2R_a^2))(1 + i/(kR_a)),
+    the last term being the boundary line integral; B_y = 2ikf(1-f/R_a)
+    - (1-f^2/R_a^2); all other components vanish.
+    """
+    k = K0 * omega
+    m = dict(f=f, r_max=a, n_r=160, n_theta=64, rim=1)
+    b = dict(profile="tophat", pol="linear", r_norm=1.01 * a)
+    E, B = _focus(m, b, omega)
+    Ra = f + a * a / (4 * f)
+    Ex = 2 * (1j * k * f + 1) * (1 - f / Ra) - (1 - f * f / Ra ** 2) - (a * a / (2 * Ra ** 2)) * (
+        1 + 1j / (k * Ra))
+    By = 2j * k * f * (1 - f / Ra) - (1 - f * f / Ra ** 2)
+    scale = abs(Ex)
+    assert abs(E[0] - Ex) < 1e-11 * scale
+    assert abs(B[1] - By) < 1e-11 * scale
+    for v in (E[1], E[2], B[0], B[2]):
+        assert abs(v) < 1e-12 * scale
+
+
+def test_paraboloid_focus_without_rim_term():
+    # dropping the line integral removes exactly its closed-form share
+    f, a, k = 20.0, 30.0, K0
+    m = dict(f=f, r_max=a, n_r=160, n_theta=64, rim=0)
+    b = dict(profile="tophat", pol="linear", r_norm=1.01 * a)
+    E, _ = _focus(m, b, 1.0)
+    Ra = f + a * a / (4 * f)
+    Ex = 2 * (1j * k * f + 1) * (1 - f / Ra) - (1 - f * f / Ra ** 2)
+    assert abs(E[0] - Ex) < 1e-11 * abs(Ex)
+
+
+def test_paraboloid_focus_radial_tophat():
+    """Radial polarisation (rho/w0) rho_hat: only E_z survives at the focus,
+    E_z = (4f/w0)[2ikf(L - 1 + f/R_a) + L - 2 + 3f/R_a - f^2/R_a^2]
+          - (1 + i/(kR_a)) (R_a - 2f) a^2 / (R_a^2 w0),   L = ln(R_a/f)."""
+    f, a, w0, om = 20.0, 30.0, 7.0, 1.3
+    k = K0 * om
+    m = dict(f=f, r_max=a, n_r=160, n_theta=64, rim=1)
+    b = dict(profile="tophat", pol="radial", r_norm=1.01 * a, w0=w0)
+    E, B = _focus(m, b, om)
+    Ra = f + a * a / (4 * f)
+    L = math.log(Ra / f)
+    Ez = (4 * f / w0) * (2j * k * f * (L - 1 + f / Ra) + L - 2 + 3 * f / Ra - f * f / Ra ** 2) - (
+        1 + 1j / (k * Ra)) * (Ra - 2 * f) * a * a / (Ra * Ra * w0)
+    assert abs(E[2] - Ez) < 1e-11 * abs(Ez)
+    for v in (E[0], E[1], B[0], B[1], B[2]):
+        assert abs(v) < 1e-12 * abs(Ez)
+
+
+def test_paraboloid_focus_azimuthal_tophat():
+    """Azimuthal polarisation: only B_z survives at the focus,
+    B_z = -(8f^2/w0)[ik(L - 1 + f/R_a) - (1 - f/R_a)/f + (1 - f^2/R_a^2)/(2f)]."""
+    f, a, w0, om = 20.0, 30.0, 7.0, 1.3
+    k = K0 * om
+    m = dict(f=f, r_max=a, n_r=160, n_theta=64, rim=1)
+    b = dict(profile="tophat", pol="azimuthal", r_norm=1.01 * a, w0=w0)
+    E, B = _focus(m, b, om)
+    Ra = f + a * a / (4 * f)
+    L = math.log(Ra / f)
+    Bz = -(8 * f * f / w0) * (1j * k * (L - 1 + f / Ra) - (1 / f) * (1 - f / Ra) + (1 / (2 * f)) * (
+        1 - f * f / Ra ** 2))
+    assert abs(B[2] - Bz) < 1e-11 * abs(Bz)
+    for v in (E[0], E[1], E[2], B[0], B[1]):
+        assert abs(v) < 1e-12 * abs(Bz)
+
+
+def test_flat_mirror_is_image_source():
+    """Sec. II: the PO current coincides with the infinite-plane result.  For
+    a flat disk of radius a and a plane wave, on axis at distance d:
+    E_x = e^{ikR_a} - e^{ikd} + (i/2k)(ik - 1/R_a) e^{ikR_a} a^2/R_a^2,
+    B_y = (d/R_a) e^{ikR_a} - e^{ikd};  -e^{ikd} is the mirror image."""
+    a, d, om = 7.0, 3.0, 1.0
+    k = K0 * om
+    m = dict(surface="flat", z0=0.0, r_max=a, n_r=200, n_theta=64, rim=1)
+    b = dict(profile="tophat", pol="linear", r_norm=1.01 * a)
+    E, B = oracle.field(m, b, [om], [[0.0, 0.0, d]])
+    Ra = math.hypot(a, d)
+    Ex = np.exp(1j * k * Ra) - np.exp(1j * k * d) + (1j / (2 * k)) * (1j * k - 1 / Ra) * np.exp(
+        1j * k * Ra) * a * a / Ra ** 2
+    By = (d / Ra) * np.exp(1j * k * Ra) - np.exp(1j * k * d)
+    assert abs(E[0, 0, 0] - Ex) < 1e-11
+    assert abs(B[0, 0, 1] - By) < 1e-11
+
+
+# --------------------------------------------------------------------------
+# Maxwell identities by finite differences (Sec. IV.A, Eq. 26a)
+
+
+def _curl(mirror, beam, om, p0, h):
+    """4th-order central-difference curl of E and B at p0."""
+    offs = []
+    for ax in range(3):
+        for s in (-2, -1, 1, 2):
+            q = np.array(p0, dtype=float)
+            q[ax] += s * h
+            offs.append(q)
+    pts = np.array([p0] + offs)
+    E, B = oracle.field(mirror, beam, [om], pts)
+    E, B = E[0], B[0]
+
+    def d(F, ax, c):
+        i = 1 + 4 * ax
+        fm2, fm1, fp1, fp2 = F[i, c], F[i + 1, c], F[i + 2, c], F[i + 3, c]
+        return (-fp2 + 8 * fp1 - 8 * fm1 + fm2) / (12 * h)
+
+    def curl(F):
+        return np.array([d(F, 1, 2) - d(F, 2, 1), d(F, 2, 0) - d(F, 0, 2), d(F, 0, 1) - d(F, 1, 0)])
+
+    def div(F):
+        return d(F, 0, 0) + d(F, 1, 1) + d(F, 2, 2)
+
+    return E[0], B[0], curl(E), curl(B), div(E)
+
+
+@pytest.mark.parametrize(
+    "beam",
+    [
+        dict(profile="gauss", pol="linear", w0=6.0, pol_angle=0.3),
+        dict(profile="supergauss", sg_order=4, pol="radial", w0=6.0),
+        dict(profile="gauss", pol="azimuthal", w0=6.0, zernike=[0.1, -0.05, 0.2, 0.03, 0.07],
+             r_norm=16.0),
+    ],
+)
+def test_faraday_holds_for_any_incident_field(beam):
+    """curl E' = ik B' holds exactly for Eq. 11 whatever the incident field:
+    the (n.E) grad g and boundary terms are gradients in r'."""
+    f, om = 8.0, 1.1
+    k = K0 * om
+    m = dict(f=f, r_max=16.0, n_r=48, n_theta=48, rim=1)
+    E, B, cE, cB, dE = _curl(m, beam, om, [0.31, -0.22, 0.17], 2e-3)
+    res = np.linalg.norm(cE - 1j * k * B) / np.linalg.norm(1j * k * B)
+    assert res < 1e-7
+
+
+def test_ampere_and_divergence_for_plane_wave():
+    """curl B' = -ik E' and div E' = 0 need a Maxwell incident field (the
+    Stokes step uses div_s(n x B) = ik n.E); a plane wave on a top-hat is one."""
+    f, om = 8.0, 1.1
+    k = K0 * om
+    m = dict(f=f, r_max=10.0, n_r=64, n_theta=64, rim=1)
+    b = dict(profile="tophat", pol="linear", r_norm=20.0)
+    E, B, cE, cB, dE = _curl(m, b, om, [0.23, 0.11, -0.19], 2e-3)
+    assert np.linalg.norm(cB + 1j * k * E) / np.linalg.norm(k * E) < 1e-7
+    assert abs(dE) / (k * np.linalg.norm(E)) < 1e-7
+
+
+def test_stokes_form_equals_double_gradient_form_for_plane_wave():
+    """Eq. 11 (single gradient + line integral) equals Eq. 10 (double
+    gradient, Appendix-A dyadic, no line term) for a Maxwell incident field."""
+    f, om = 8.0, 0.9
+    m = dict(f=f, r_max=12.0, n_r=96, n_theta=96, rim=1)
+    b = dict(profile="tophat", pol="linear", r_norm=20.0, pol_angle=0.4)
+    rng = np.random.default_rng(7)
+    pts = rng.uniform(-1.5, 1.5, size=(6, 3))
+    E1, B1 = oracle.field(m, b, [om], pts, form="stokes")
+    E2, B2 = oracle.field(m, b, [om], pts, form="dyadic")
+    scale = np.max(np.abs(E1))
+    assert np.max(np.abs(E1 - E2)) < 1e-9 * scale
+    assert np.max(np.abs(B1 - B2)) == 0.0
+
+
+def test_double_gradient_form_differs_for_non_maxwell_beam():
+    # the two forms differ at O(lambda/(pi w0)) for the paraxial Gaussian
+    m = dict(f=8.0, r_max=12.0, n_r=64, n_theta=64, rim=1)
+    b = dict(profile="gauss", pol="linear", w0=3.0)
+    E1, _ = oracle.field(m, b, [1.0], [[0.2, 0.1, 0.0]], form="stokes")
+    E2, _ = oracle.field(m, b, [1.0], [[0.2, 0.1, 0.0]], form="dyadic")
+    rel = np.max(np.abs(E1 - E2)) / np.max(np.abs(E1))
+    assert 1e-4 < rel < 0.5
+
+
+# --------------------------------------------------------------------------
+# Discrete symmetries (exact for an even theta grid starting at 0)
+
+
+def test_linear_x_parity_table():
+    """x -> -x and y -> -y parities of the six components for x-polarisation
+    (consistent with the E_z cut along x and B_z cut along y of Sec. IV.B)."""
+    m = dict(f=10.0, r_max=20.0, n_r=24, n_theta=32, rim=1)
+    b = dict(profile="gauss", pol="linear", w0=8.0)
+    p = np.array([[0.37, 0.21, 0.13]])
+    px = p * np.array([-1, 1, 1])
+    py = p * np.array([1, -1, 1])
+    E, B = oracle.field(m, b, [1.0], np.vstack([p, px, py]))
+    F = np.concatenate([E[0], B[0]], axis=1)  # [pt, 6]
+    sx = np.array([1, -1, -1, -1, 1, 1])
+    sy = np.array([1, -1, 1, -1, 1, -1])
+    scale = np.max(np.abs(F))
+    assert np.max(np.abs(F[1] - sx * F[0])) < 1e-12 * scale
+    assert np.max(np.abs(F[2] - sy * F[0])) < 1e-12 * scale
+
+
+def test_radial_rotation_invariance():
+    # radial polarisation: the field rotates with the point by 2 pi / n_theta
+    nth = 24
+    m = dict(f=10.0, r_max=20.0, n_r=24, n_theta=nth, rim=1)
+    b = dict(profile="gauss", pol="radial", w0=8.0)
+    p = np.array([0.4, 0.1, -0.2])
+    a = 2 * math.pi / nth
+    Rz = np.array([[math.cos(a), -math.sin(a), 0], [math.sin(a), math.cos(a), 0], [0, 0, 1]])
+    E, B = oracle.field(m, b, [1.0], np.vstack([p, Rz @ p]))
+    scale = np.max(np.abs(E))
+    assert np.max(np.abs(E[0, 1] - Rz @ E[0, 0])) < 1e-12 * scale
+    assert np.max(np.abs(B[0, 1] - Rz @ B[0, 0])) < 1e-12 * scale
+
+
+# --------------------------------------------------------------------------
+# Convergence (Sec. IV.A, Eq. 23): e_rel decreases under node refinement
+
+
+def test_quadrature_convergence_to_plateau():
+    m0 = dict(f=20.0, r_max=40.0, rim=1)
+    b = dict(profile="gauss", pol="linear", w0=20.0)
+    pts = np.array([[x, y, 0.0] for x in (-1.0, 0.0, 0.6) for y in (-0.8, 0.0, 1.0)])
+    ref, _ = oracle.field(dict(m0, n_r=96, n_theta=96), b, [1.0], pts)
+    errs = []
+    for n in (8, 12, 16, 24, 32):
+        E, _ = oracle.field(dict(m0, n_r=n, n_theta=n), b, [1.0], pts)
+        errs.append(np.max(np.abs(E - ref)) / np.max(np.abs(ref)))
+    assert all(errs[i + 1] < errs[i] for i in range(len(errs) - 1))
+    assert errs[-1] < 1e-9
+
+
+# --------------------------------------------------------------------------
+# Spectrum and time reconstruction (Sec. III.B, Sec. IV.B)
+
+
+def test_paper_example_spectrum_and_pulse():
+    """Eq. 27 with Table 1's parameters: printed spectral FWHM 130 nm (exact
+    value of the reading with the minus sign: 2*70*(ln 2)^(1/6) = 131.7 nm)
+    and a main pulse of 18.2 fs, here the FWHM of the field envelope from
+    100 uniform k samples (17.7 fs: within 5%; the reading is stated)."""
+    g = json.load(open(os.path.join(GOLDEN, "paper_example_spectrum.json")))
+    lam0_nm = g["lambda_c_nm"]
+    dl = g["dlambda_nm"] / lam0_nm
+    spec = dict(kind="supergauss_lambda", lambda_c=1.0, dlambda=dl, sg_n=g["sg_n"])
+    beam = dict(profile="gauss", w0=1.0)
+    lf = np.linspace(0.8, 1.2, 80001)
+    a = oracle.spectrum(spec, 1.0 / lf, beam)
+    eps_lambda = np.abs(a) ** 2 * (2 * math.pi / lf ** 2)  # energy per unit lambda
+    idx = np.where(eps_lambda >= eps_lambda.max() / 2)[0]
+    fwhm_nm = (lf[idx[-1]] - lf[idx[0]]) * lam0_nm
+    assert abs(fwhm_nm - 2 * g["dlambda_nm"] * math.log(2) ** (1 / 6)) < 0.05
+    assert abs(fwhm_nm - g["printed_spectral_fwhm_nm"]) < 0.02 * g["printed_spectral_fwhm_nm"]
+
+    k = np.linspace(2 * math.pi / (1 + 1.6 * dl), 2 * math.pi / (1 - 1.6 * dl), g["n_samples"])
+    a = oracle.spectrum(spec, k / (2 * math.pi), beam)
+    t = np.linspace(-15, 15, 30001)
+    env = np.abs(np.exp(-1j * np.outer(t, k)) @ a)
+    idx = np.where(env >= env.max() / 2)[0]
+    unit_fs = lam0_nm * 1e-9 / 299792458.0 * 1e15
+    fwhm_fs = (t[idx[-1]] - t[idx[0]]) * unit_fs
+    assert abs(fwhm_fs - g["printed_pulse_fwhm_fs"]) < 0.05 * g["printed_pulse_fwhm_fs"]
+
+
+def test_spectrum_energy_normalisation():
+    """Eq. 16-17: with a_n = sqrt(eps(k_n) / (4 pi P)), sum |a_n|^2 4 pi P dk
+    over a fine grid recovers the total energy."""
+    beam = dict(profile="gauss", pol="linear", w0=2.0)
+    P = oracle.beam_power(beam)
+    for spec in (dict(kind="gauss_time", fwhm_t=3.7474, lambda_c=1.0, energy=2.5),
+                 dict(kind="supergauss_lambda", lambda_c=1.0, dlambda=0.085, sg_n=3, energy=2.5)):
+        k = np.linspace(0.2 * K0, 3.0 * K0, 20001)
+        a = oracle.spectrum(spec, k / K0, beam)
+        e = np.sum(np.abs(a) ** 2) * 4 * math.pi * P * (k[1] - k[0])
+        assert abs(e - 2.5) < 1e-6
+
+
+def test_gauss_time_spectrum_gives_gaussian_pulse():
+    """Field spectrum exp(-(k-kc)^2 tau^2/(8 ln 2)) is a pulse of intensity
+    FWHM tau; chirp phi_2 only stretches it (Eq. 18 map)."""
+    tau = 3.7474
+    spec = dict(kind="gauss_time", fwhm_t=tau, lambda_c=1.0)
+    om = np.linspace(0.5, 1.5, 256)
+    a = oracle.spectrum(spec, om, dict(profile="gauss", w0=1.0))
+    t = np.linspace(-12, 12, 4801)
+    F = oracle.time_domain(a.reshape(-1, 1), om, t)[:, 0]
+    dk = K0 * (om[1] - om[0])
+    env = np.abs(np.exp(-1j * np.outer(t, K0 * om)) @ a) * 2 * dk
+    I = env ** 2
+    idx = np.where(I >= I.max() / 2)[0]
+    assert abs((t[idx[-1]] - t[idx[0]]) - tau) < 0.01
+    # the real time signal is the carrier under that envelope
+    assert np.max(np.abs(F)) <= np.max(env) * (1 + 1e-12)
+    assert abs(np.max(np.abs(F)) - np.max(env)) < 1e-3 * np.max(env)
+    spec2 = dict(spec, phi=[0.0, 0.0, 2.0])
+    a2 = oracle.spectrum(spec2, om, dict(profile="gauss", w0=1.0))
+    assert np.allclose(np.abs(a2), np.abs(a))
+    env2 = np.abs(np.exp(-1j * np.outer(t, K0 * om)) @ a2) * 2 * dk
+    # a linearly chirped Gaussian loses peak field as (1 + (4 ln2 phi2/tau^2)^2)^(-1/4)
+    ratio = (1 + (4 * math.log(2) * 2.0 / tau ** 2) ** 2) ** -0.25
+    assert abs(env2.max() / env.max() - ratio) < 1e-3
+
+
+def test_time_domain_single_frequency():
+    # one sample, dk := 1: F(t) = 2 Re(F_0 e^{-ik t})
+    F0 = np.array([[0.3 - 0.7j, 1.1 + 0.2j]])
+    t = np.array([0.0, 0.13, 0.5])
+    out = oracle.time_domain(F0, [1.2], t)
+    want = 2 * np.real(F0[0][None, :] * np.exp(-1j * K0 * 1.2 * t)[:, None])
+    assert np.max(np.abs(out - want)) < 1e-15
+
+
+def test_paraboloid_reference_phase_identity():
+    """Sec. III.C.1 (Eq. 21): on z = r^2/(4f) - f the distance to the focus
+    is z + 2f, so the zeroth-order phase k(|r| - z) = 2kf is constant."""
+    f = 62500.0
+    r = np.linspace(0, 2 * f, 11)
+    z = r * r / (4 * f) - f
+    assert np.max(np.abs(np.hypot(r, z) - (z + 2 * f))) < 1e-9 * f
