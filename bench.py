@@ -1,0 +1,353 @@
+"""Benchmark of the Stratton-Chu focal-field hot path on GB300.
+
+One step = one pass of the whole path over the broadband workload
+(512 x 512 mirror nodes, 256 uniform omegas, 4160 focal points, 10 fs pulse
+at f = 62,500 lambda0, NA = 1): spectrum a_n (Eqs. 16-18), per-pair geometry
+with the compensated phase, the 26-op field-sum inner loop with the omega
+rotation recurrence (Eq. 11), the FP64 cross-split reduction and epilogue,
+and the inverse transform to 512 time samples (Eq. 13).
+
+Metric: obs x node x omega evaluations per second (surface nodes), whole job.
+  value   device-resident inputs and outputs, CUDA events on the library's
+          stream around each step; an L2 flush (256 MB memset) runs between
+          steps outside the events.
+  e2e     the same step through the C-ABI with host buffers: points from
+          pinned host memory in, time-domain E(t), B(t) back to pinned host
+          memory, copies inside the timed region.
+  roofline  the dominant kernel (FP32 field sum) against the FP32-pipe peak
+          SMs x 128 lanes x clock at 26 FP32 lane-ops per evaluation.
+  cpu_baseline  the FP64 oracle on the host cores over a bounded sample of
+          the same workload.
+--impl reference times that oracle as the reference arm.
+Multi-GPU (torchrun): every rank evaluates its own copy of the workload
+(weak scaling, no data-path collective); timing is max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+OPS_PER_EVAL = 26  # FP32 lane-ops per (point, node, omega) in the field-sum inner loop
+FIELD_KERNEL = "field_grouped_kernel<32>"
+PROFILE_JSON = os.path.join(ROOT, "profiles", "field_grouped_broadband.json")
+FIELD_SRC = os.path.join(ROOT, "paper_1609_08146_gb300", "csrc", "sc_field.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = self.rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": num(rows[0][1]),
+                "reasons": reasons, "samples": len(rows),
+                "power_w_median": statistics.median([num(r[2]) for r in rows if num(r[2]) is not None] or [0])}
+
+
+def dist_setup(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")  # barrier and timing only: no data-path collective
+        pg = dist
+    return rank, world, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x: float) -> float:
+    if pg is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(pg, x: float) -> float:
+    if pg is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+def oracle_sample_rate(w, seconds: float):
+    """FP64 oracle on the host cores over a bounded sample of the workload:
+    all nodes and omegas at a seeded subset of points, sized to ~seconds."""
+    import oracle
+    from paper_1609_08146_gb300 import workloads as wl
+
+    m, b = wl.oracle_args(w)
+    om = w["omegas"]
+    nodes = m["n_r"] * m["n_theta"]
+    rng = np.random.Generator(np.random.PCG64(7))
+    pts = w["points"]
+    # calibrate on one point
+    t0 = time.perf_counter()
+    oracle.field(m, b, om, pts[:1])
+    dt1 = time.perf_counter() - t0
+    n = int(max(1, min(len(pts), seconds / max(dt1, 1e-6))))
+    idx = rng.choice(len(pts), size=n, replace=False)
+    t0 = time.perf_counter()
+    oracle.field(m, b, om, pts[idx])
+    dt = time.perf_counter() - t0
+    evals = n * nodes * len(om)
+    return evals / dt, n, dt, os.cpu_count()
+
+
+def profile_traffic():
+    """DRAM bytes per launch of the field kernel from the committed ncu
+    summary, only while the kernel source is unchanged since the capture."""
+    try:
+        prof = json.load(open(PROFILE_JSON))
+        sha = hashlib.sha256(open(FIELD_SRC, "rb").read()).hexdigest()
+        if prof.get("source_sha256") == sha:
+            return prof.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def run_reference(args, rank, world, pg):
+    from paper_1609_08146_gb300 import workloads as wl
+
+    w = wl.broadband()
+    if rank != 0:
+        return
+    per_step = max(2.0, args.cpu_seconds / max(1, args.steps))
+    rates = []
+    for i in range(args.warmup + args.steps):
+        r, n, dt, cores = oracle_sample_rate(w, per_step)
+        if i >= args.warmup:
+            rates.append((r, n, dt, cores))
+    value = statistics.median([r[0] for r in rates])
+    cores = rates[0][3]
+    sample = "%d of %d points x all %d nodes x %d omegas per step (FP64 oracle, OpenMP)" % (
+        rates[0][1], len(w["points"]), w["mirror"]["n_r"] * w["mirror"]["n_theta"], len(w["omegas"]))
+    line = {
+        "impl": "reference", "metric": "Stratton-Chu obs*node*omega evals/s", "value": value,
+        "unit": "evals/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * statistics.median([r[2] for r in rates]), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "sampled": True},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world, pg)
+        return
+    import torch
+
+    import paper_1609_08146_gb300 as sc
+    from paper_1609_08146_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = sc.Context(local, stream=stream)
+    w = wl.broadband()
+    mc = w["mirror"]
+    m = ctx.mirror(mc["f"], mc["r_min"], mc["r_max"], mc["n_r"], mc["n_theta"], rim=mc["rim"])
+    inc = ctx.incident(profile=w["beam"]["profile"], w0=w["beam"]["w0"], pol=w["beam"]["pol"],
+                       spectrum=w["spectrum"])
+    om, times = w["omegas"], w["times"]
+    n_nodes = mc["n_r"] * mc["n_theta"]
+    npts = len(w["points"])
+    evals_per_step = float(npts) * n_nodes * len(om)
+
+    with torch.cuda.stream(stream):
+        P = torch.tensor(w["points"], device=dev)
+        E = torch.empty((len(om), npts, 3), dtype=torch.complex64, device=dev)
+        B = torch.empty_like(E)
+        Et = torch.empty((len(times), npts, 3), dtype=torch.float32, device=dev)
+        Bt = torch.empty_like(Et)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        ctx.eval(m, inc, om, P, out=(E, B))
+        ctx.time_domain(E, B, om, times, out=(Et, Bt))
+
+    # warm-up (builds and uploads the node table on the first call)
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+
+    # ---- device-resident timed region
+    ctx.reset_counters()
+    ctx.set_option(sc.SC_OPT_TIME_FIELD, 1)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(pg)
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()  # L2 flush between steps, outside the events
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    barrier(pg)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ctr = ctx.counters()
+    ctx.set_option(sc.SC_OPT_TIME_FIELD, 0)
+    total_ms = max_over_ranks(pg, sum(step_ms))
+    value = sum_over_ranks(pg, evals_per_step * args.steps) / (total_ms / 1000.0)
+    launches_per_step = ctr["launches"] / args.steps
+    field_ms = ctr["field_ms"] / max(1, ctr["field_launches"])
+    field_evals = evals_per_step * args.steps / max(1, ctr["field_launches"])
+
+    # ---- end to end through the C-ABI with host buffers
+    Ph = torch.tensor(w["points"]).pin_memory()
+    Eth = torch.empty((len(times), npts, 3), dtype=torch.float32).pin_memory()
+    Bth = torch.empty_like(Eth).pin_memory()
+    ctx.eval(m, inc, om, Ph.to(dev), out=(E, B))  # keep the table resident
+    barrier(pg)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.eval(m, inc, om, Ph, out=(E, B))          # points: pinned host -> device
+        ctx.time_domain(E, B, om, times, out=(Eth, Bth))  # E(t), B(t): device -> pinned host
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
+    e2e_value = sum_over_ranks(pg, evals_per_step * args.steps) / e2e_s
+    h2d = int(Ph.numel() * 8 + om.size * 8)
+    d2h = int(Eth.numel() * 4 + Bth.numel() * 4)
+
+    # ---- roofline of the dominant kernel
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    max_mhz = clk.get("sm_max_mhz") or 2070.0
+    peak = sms * 128 * max_mhz * 1e6 * 1e-12  # TOP/s of FP32 lane-ops at the maximum SM clock
+    achieved = field_evals * OPS_PER_EVAL / (field_ms / 1000.0) * 1e-12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s",
+            "frac": achieved / peak, "traffic": profile_traffic(),
+            "kernel": FIELD_KERNEL, "ops_per_eval": OPS_PER_EVAL,
+            "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (max SM clock)" % (sms, max_mhz),
+            "kernel_ms": field_ms}
+    if clk.get("sm_mhz"):
+        roof["frac_at_sampled_clock"] = achieved / (sms * 128 * clk["sm_mhz"] * 1e6 * 1e-12)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, n, dt, cores = oracle_sample_rate(w, args.cpu_seconds)
+        cpu = {"value": r, "unit": "evals/s", "cores": cores, "kind": "oracle",
+               "sample": "%d of %d points x all %d nodes x %d omegas (%.1f s, FP64 OpenMP)"
+               % (n, npts, n_nodes, len(om), dt)}
+
+    if rank == 0:
+        line = {
+            "metric": "Stratton-Chu obs*node*omega evals/s", "value": value, "unit": "evals/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["name"], "mirror_nodes": n_nodes, "points": npts,
+                       "omegas": len(om), "time_samples": len(times), "f_lambda0": mc["f"],
+                       "precision": "FP32 compensated phase, FP64 cross-split reduction",
+                       "l2": "256 MB memset between steps, outside the timed events",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(ctr["launches"]),
+            "gpu_launches_per_step": launches_per_step,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

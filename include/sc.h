@@ -1,0 +1,258 @@
+/*
+ * sc.h -- C-ABI of libsc, the GB300 (sm_103a) evaluator of the
+ * physical-optics Stratton-Chu focal field of a parabolic mirror
+ * (Dumont et al., arXiv:1609.08146).
+ *
+ * What it computes.  For every frequency omega_n of an incident pulse and
+ * every observation point r' near the focus, the reflected field of
+ * Sec. II, Eq. 11 (physical-optics surface currents after Stokes' theorem):
+ *
+ *   E'(r', k) = 2 SS { ik (n x B_inc) g + (n . E_inc) grad g } dS
+ *               - (2/ik) O grad g [n x (n x B_inc)] . dl
+ *   B'(r', k) = 2 SS (n x B_inc) x grad g dS,   g = e^{ikR} / (4 pi R)
+ *
+ * discretised by tensor-product quadrature on the mirror (Sec. III.C.1),
+ * followed on request by the semi-discrete inverse transform of Sec. III.B,
+ * Eq. 13.  The mirror is the paraboloid z = r^2/(4f) - f of Eq. 21 with its
+ * focus at the origin; the incident beam travels along -z (Sec. III.A).
+ *
+ * Units: lengths in lambda0 (the reference wavelength), c = 1, angular
+ * frequencies omega in units of omega0 = 2 pi c / lambda0, so the
+ * wavenumber is k = 2 pi omega; times in lambda0 / c.
+ *
+ * Conventions shared by every call:
+ *  - Status codes only: no call aborts, prints or throws.  On failure the
+ *    context keeps a message readable with sc_last_error().
+ *  - Every GPU step runs in this library's own CUDA kernels on the stream
+ *    given to sc_create(); there is no CPU fallback.  A call that takes
+ *    device buffers is asynchronous on that stream unless it says otherwise.
+ *  - Pointers marked "host or device" are classified with
+ *    cudaPointerGetAttributes; host buffers are staged through device memory
+ *    owned by the context and the call then returns after its results are
+ *    back in host memory.
+ *  - The library owns every handle and every device table it creates; the
+ *    caller owns every input and output buffer it passes.
+ *  - Complex arrays are interleaved (re, im).
+ */
+#ifndef SC_H
+#define SC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SC_OK = 0,
+    SC_ERR_INVALID = 1,   /* bad argument or geometry                        */
+    SC_ERR_OOM = 2,       /* device allocation failed or budget exceeded     */
+    SC_ERR_CUDA = 3,      /* a CUDA runtime call failed                      */
+    SC_ERR_TIMEOUT = 4,   /* a bounded device wait ran out                   */
+    SC_ERR_BUSY = 5,      /* request can never be admitted                   */
+    SC_ERR_CANCELLED = 6, /* request cancelled before completion             */
+    SC_ERR_NOT_FOUND = 7  /* unknown ticket                                  */
+} sc_status;
+
+typedef struct sc_ctx sc_ctx;
+typedef struct sc_mirror_t sc_mirror_t;
+typedef struct sc_incident_t sc_incident_t;
+
+/* ---------------------------------------------------------------------- */
+/* Context                                                                 */
+
+/*
+ * Create a context bound to CUDA device `device` and stream `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  `hbm_budget_bytes`
+ * caps the device memory the context itself holds (node tables, workspace,
+ * staging); 0 means "no cap beyond what cudaMalloc grants".
+ * Errors: SC_ERR_INVALID (null out, bad device), SC_ERR_CUDA.
+ */
+sc_status sc_create(int device, void* cuda_stream, size_t hbm_budget_bytes, sc_ctx** out);
+
+/* Release every device buffer and handle cache of the context.  Waits for
+ * the context's stream.  NULL is accepted. */
+sc_status sc_destroy(sc_ctx* ctx);
+
+/* Message of the most recent failing call on this context (owned by the
+ * context, valid until its next call).  Never NULL. */
+const char* sc_last_error(const sc_ctx* ctx);
+
+/* ---------------------------------------------------------------------- */
+/* Mirror (Sec. III.A; Sec. III.C.1, Eq. 21 and the quadrature it names)    */
+
+enum { SC_QUAD_GAUSS_LEGENDRE = 0 };
+
+typedef struct {
+    int radial_kind; /* SC_QUAD_GAUSS_LEGENDRE: n_r nodes in r on [r_min, r_max]      */
+    int n_r;         /* >= 1                                                          */
+    int n_theta;     /* >= 1, periodic trapezoid theta_l = 2 pi l / n_theta           */
+    int rim_term;    /* 1: include the boundary line integral of Eq. 11 (outer rim,   */
+                     /*    and the inner rim when r_min > 0)                          */
+} sc_quadrature;
+
+/*
+ * Describe the paraboloid z = r^2/(4f) - f (focus at the origin) cut to
+ * r_min <= r <= r_max, and the quadrature used on it.
+ * Errors: SC_ERR_INVALID when f <= 0, r_min < 0, r_min >= r_max, n_r < 1,
+ * n_theta < 1 or an unknown radial_kind.  The handle is host-side only;
+ * device tables are built lazily per (mirror, incident) pair by sc_eval.
+ */
+sc_status sc_mirror(sc_ctx* ctx, double f, double r_min, double r_max, const sc_quadrature* q,
+                    sc_mirror_t** out);
+void sc_mirror_free(sc_mirror_t* m);
+
+/* ---------------------------------------------------------------------- */
+/* Incident field (Sec. III.A; Sec. III.B, Eqs. 14-18; Sec. IV.B, Eq. 27)   */
+
+enum { SC_PROFILE_GAUSS = 0, SC_PROFILE_SUPERGAUSS = 1, SC_PROFILE_TOPHAT = 2 };
+enum { SC_POL_LINEAR = 0, SC_POL_RADIAL = 1, SC_POL_AZIMUTHAL = 2 };
+enum {
+    SC_SPEC_MONO = 0,              /* a_n = 1                                     */
+    SC_SPEC_GAUSS_TIME = 1,        /* Gaussian pulse, intensity FWHM fwhm_t       */
+    SC_SPEC_SUPERGAUSS_LAMBDA = 2, /* Eq. 27 in wavelength, centre lambda_c,      */
+                                   /* width dlambda, order sg_n                   */
+    SC_SPEC_SAMPLED = 3            /* a_n given at n omegas                       */
+};
+
+/*
+ * Collimated beam on the mirror (the Supplementary Material with the
+ * paper's explicit fields is not available; this is the waist-plane limit
+ * of its paraxial modes): E_inc = A(rho) p(theta) e^{-ik(z + 2f)} e^{ikW},
+ * B_inc = (-z_hat) x E_inc.
+ *   A: Gaussian exp(-rho^2/w0^2), super-Gaussian exp(-(rho/w0)^(2 sg_order)),
+ *      or top-hat (1 for rho <= w0, 0 beyond).
+ *   W: optical path difference sum_j c_j Z_j(rho / r_max, theta), Noll
+ *      ordering and normalisation, j = 2 .. n_zernike + 1, c_j in waves at
+ *      lambda0 (the caller's array is copied).
+ */
+typedef struct {
+    int kind;
+    double w0;
+    int sg_order;
+    int n_zernike;
+    const double* zernike_noll_waves;
+} sc_profile;
+
+/* p: fixed direction (cos angle, sin angle, 0), or rho_hat * rho/w0
+ * (radial), or theta_hat * rho/w0 (azimuthal). */
+typedef struct {
+    int kind;
+    double angle_rad;
+} sc_polarization;
+
+/*
+ * Spectrum a_n = E0^n e^{i phi(k_n)} (Eqs. 15, 16, 18).  For
+ * GAUSS_TIME and SUPERGAUSS_LAMBDA the power spectrum eps(k) (energy per
+ * unit k, Eq. 17 normalised to `energy`) gives E0^n = sqrt(eps(k_n) /
+ * (4 pi P)), P = SS |A p|^2 dA over the transverse plane.  Eq. 27 is read
+ * with a minus sign in its exponent and includes |d lambda/dk|.
+ * phi(k) = sum_j phi_taylor[j] (k - k_c)^j / j!, k_c = 2 pi / lambda_c.
+ * GAUSS_TIME: field spectrum exp(-(k - k_c)^2 fwhm_t^2 / (8 ln 2)).
+ * SAMPLED: n, omega[n], amp_re_im[2n]; sc_eval then needs the same omegas.
+ */
+typedef struct {
+    int kind;
+    double fwhm_t;
+    double lambda_c;
+    double dlambda;
+    int sg_n;
+    double energy;
+    int n;
+    const double* omega;
+    const double* amp_re_im;
+    int n_phi;
+    const double* phi_taylor;
+} sc_spectrum;
+
+/* Copy the description of an incident beam.  Errors: SC_ERR_INVALID
+ * (unknown kind, w0 <= 0, sg_order < 1, n_zernike outside 0..64, a
+ * spectrum with non-positive width or lambda_c, SAMPLED with n < 1). */
+sc_status sc_incident(sc_ctx* ctx, const sc_profile* prof, const sc_polarization* pol,
+                      const sc_spectrum* spec, sc_incident_t** out);
+void sc_incident_free(sc_incident_t* inc);
+
+/* Evaluate a_n (Eqs. 16 and 18) at n host omegas into host amp_re_im[2n]. */
+sc_status sc_spectrum_eval(sc_ctx* ctx, const sc_incident_t* inc, const double* omegas, int n,
+                           double* amp_re_im);
+
+/* ---------------------------------------------------------------------- */
+/* Field evaluation (Sec. II, Eq. 11; the hot path)                         */
+
+typedef enum { SC_FP32_COMP = 0, SC_FP64 = 1 } sc_precision;
+
+typedef struct {
+    double evals;       /* points x surface nodes x omegas of this call          */
+    double field_ms;    /* CUDA-event time of the field-sum launches              */
+    double total_ms;    /* CUDA-event time of the whole call on the stream        */
+    int launches;       /* kernels launched by the call                           */
+} sc_eval_stats;
+
+/*
+ * E(r'_p, omega_n) and B(r'_p, omega_n), reflected field only.
+ *   omegas      host, n_omega >= 1 values (> 0).  SC_FP32_COMP needs a uniform
+ *               grid (|omega_n - omega_0 - n d| <= 1e-9 omega_0); SC_FP64 takes
+ *               any grid.
+ *   points_xyz  host or device, [n_points][3] doubles.
+ *   E_out,B_out host or device, [n_omega][n_points][3] complex: float2 pairs
+ *               for SC_FP32_COMP, double2 pairs for SC_FP64.  B_out may be NULL.
+ *   stats       nullable; when given the call synchronizes the stream and
+ *               fills it.
+ * The first call for a (mirror, incident) pair builds its node table (FP64 on
+ * the host, uploaded once, then resident in HBM).
+ * Errors: SC_ERR_INVALID (null pointers, n_points < 1, n_omega < 1, omega <= 0,
+ * non-uniform grid for SC_FP32_COMP, SAMPLED spectrum whose omegas differ,
+ * a point closer than 1e-6 lambda0 to the mirror), SC_ERR_OOM, SC_ERR_CUDA,
+ * SC_ERR_TIMEOUT (a bounded device wait ran out; outputs undefined).
+ */
+sc_status sc_eval(sc_ctx* ctx, const sc_mirror_t* mirror, const sc_incident_t* inc,
+                  const double* omegas, int n_omega, const double* points_xyz, int n_points,
+                  sc_precision prec, void* E_out, void* B_out, sc_eval_stats* stats);
+
+/*
+ * Semi-discrete inverse transform, Sec. III.B Eq. 13, for a real field on a
+ * positive-frequency grid: F(t_m) = 2 Re sum_n F_n e^{-i k_n t_m} dk with
+ * dk = 2 pi (omega_1 - omega_0) (uniform grid required) or dk = 1 when
+ * n_omega = 1.
+ *   E_spec,B_spec  host or device spectra laid out as sc_eval writes them
+ *                  (element type chosen by prec); B_spec may be NULL.
+ *   times          host, n_t values.
+ *   E_t,B_t        host or device, float [n_t][n_points][3]; B_t NULL iff
+ *                  B_spec is NULL.
+ * Errors: SC_ERR_INVALID, SC_ERR_OOM, SC_ERR_CUDA.
+ */
+sc_status sc_time_domain(sc_ctx* ctx, sc_precision prec, const void* E_spec, const void* B_spec,
+                         const double* omegas, int n_omega, int n_points, const double* times,
+                         int n_t, float* E_t, float* B_t);
+
+/* ---------------------------------------------------------------------- */
+/* Counters (measurement)                                                  */
+
+typedef struct {
+    uint64_t launches;       /* kernels launched by this context since reset       */
+    uint64_t field_launches; /* field-sum kernel launches since reset              */
+    double field_ms;         /* summed CUDA-event time of those launches           */
+    double evals;            /* points x nodes x omegas issued since reset         */
+} sc_counters;
+
+/* Synchronizes the context stream and returns the counters. */
+sc_status sc_get_counters(sc_ctx* ctx, sc_counters* out);
+sc_status sc_reset_counters(sc_ctx* ctx);
+
+/* Tuning / instrumentation options (value semantics per option). */
+enum {
+    SC_OPT_TIME_FIELD = 1,      /* 1: bracket each field-sum launch with events  */
+    SC_OPT_NODES_PER_SPLIT = 2, /* surface nodes per split (multiple of 32), or 0 */
+                                /* to pick the split count for load balance       */
+    SC_OPT_WORKSPACE_CAP = 3,   /* max workspace bytes per launch chunk           */
+    SC_OPT_FLUSH_NODES = 4      /* nodes summed in an FP32 run before it is folded */
+                                /* into the compensated partial (multiple of 32)   */
+};
+sc_status sc_set_option(sc_ctx* ctx, int option, long long value);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SC_H */

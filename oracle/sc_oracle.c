@@ -38,7 +38,8 @@
  *       exp(-ik(z + z_ref)) exp(ik W), B_inc = (-z) x E_inc, with
  *       z_ref = 2f for the paraboloid (so the geometric focal arrival is at
  *       t = 0) and z_ref = -z0 for the flat test mirror.  A is Gaussian
- *       exp(-rho^2/w0^2), super-Gaussian exp(-(rho/w0)^(2N)) or a top-hat;
+ *       exp(-rho^2/w0^2), super-Gaussian exp(-(rho/w0)^(2N)) or a top-hat of
+ *       radius w0;
  *       p is a fixed linear direction, rho_hat (radial) or theta_hat
  *       (azimuthal), the last two times rho/w0.  W is the optical path
  *       difference of a Zernike expansion (Noll ordering) on the unit disk
@@ -85,7 +86,7 @@ typedef struct {
     int n_zern;       /* number of Zernike coefficients, Noll j = 2 ..         */
     double w0;
     double pol_angle; /* direction of linear polarisation in the xy-plane      */
-    double r_norm;    /* radius of the Zernike unit disk (and top-hat radius)  */
+    double r_norm;    /* radius of the Zernike unit disk                       */
     const double* zern;
 } or_beam;
 
@@ -186,7 +187,7 @@ static double beam_amplitude(const or_beam* bm, double rho)
     switch (bm->profile) {
     case 0: return exp(-(rho * rho) / (bm->w0 * bm->w0));
     case 1: return exp(-pow(rho / bm->w0, 2.0 * bm->sg_order));
-    default: return (rho <= bm->r_norm) ? 1.0 : 0.0;
+    default: return (rho <= bm->w0) ? 1.0 : 0.0;
     }
 }
 
@@ -228,7 +229,7 @@ static double beam_opd(const or_beam* bm, double x, double y)
 double or_beam_power(const or_beam* bm)
 {
     double rmax;
-    if (bm->profile == 2) rmax = bm->r_norm;
+    if (bm->profile == 2) rmax = bm->w0;
     else rmax = 12.0 * bm->w0;
     int n = 400000;
     double h = rmax / n, s = 0.0;

@@ -1,0 +1,303 @@
+"""GB300-native evaluator of the physical-optics Stratton-Chu focal field.
+
+Python binding of ``libsc`` (C-ABI in ``include/sc.h``): argument
+marshalling only.  Every step of the field evaluation and of the inverse
+transform runs in the library's own CUDA kernels for sm_103a; there is no
+CPU or PyTorch fallback, and loading fails loudly when the library is
+missing.  PyTorch provides device memory and the CUDA stream.
+
+The paper (Dumont et al., arXiv:1609.08146) evaluates Sec. II Eq. 11 over a
+parabolic mirror for every frequency of a short pulse and every point near
+the focus, then rebuilds the time-domain field with Sec. III.B Eq. 13.
+
+Low-level functions carry the C names (``sc_create``, ``sc_mirror``, ...);
+``Context`` wraps them for tensors and numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH
+
+__all__ = ["load", "ScError", "Context", "Mirror", "Incident"]
+
+SC_OK, SC_ERR_INVALID, SC_ERR_OOM, SC_ERR_CUDA, SC_ERR_TIMEOUT = 0, 1, 2, 3, 4
+SC_ERR_BUSY, SC_ERR_CANCELLED, SC_ERR_NOT_FOUND = 5, 6, 7
+SC_FP32_COMP, SC_FP64 = 0, 1
+PROFILES = {"gauss": 0, "supergauss": 1, "tophat": 2}
+POLS = {"linear": 0, "radial": 1, "azimuthal": 2}
+SPECTRA = {"mono": 0, "gauss_time": 1, "supergauss_lambda": 2, "sampled": 3}
+SC_OPT_TIME_FIELD, SC_OPT_NODES_PER_SPLIT, SC_OPT_WORKSPACE_CAP, SC_OPT_FLUSH_NODES = 1, 2, 3, 4
+
+_DP = ctypes.POINTER(ctypes.c_double)
+_VP = ctypes.c_void_p
+
+
+class sc_quadrature(ctypes.Structure):
+    _fields_ = [("radial_kind", ctypes.c_int), ("n_r", ctypes.c_int), ("n_theta", ctypes.c_int),
+                ("rim_term", ctypes.c_int)]
+
+
+class sc_profile(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("w0", ctypes.c_double), ("sg_order", ctypes.c_int),
+                ("n_zernike", ctypes.c_int), ("zernike_noll_waves", _DP)]
+
+
+class sc_polarization(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("angle_rad", ctypes.c_double)]
+
+
+class sc_spectrum(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("fwhm_t", ctypes.c_double), ("lambda_c", ctypes.c_double),
+                ("dlambda", ctypes.c_double), ("sg_n", ctypes.c_int), ("energy", ctypes.c_double),
+                ("n", ctypes.c_int), ("omega", _DP), ("amp_re_im", _DP), ("n_phi", ctypes.c_int),
+                ("phi_taylor", _DP)]
+
+
+class sc_eval_stats(ctypes.Structure):
+    _fields_ = [("evals", ctypes.c_double), ("field_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double), ("launches", ctypes.c_int)]
+
+
+class sc_counters(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("field_launches", ctypes.c_uint64),
+                ("field_ms", ctypes.c_double), ("evals", ctypes.c_double)]
+
+
+# C-ABI symbol table: name -> (restype, argtypes)
+SIGNATURES = {
+    "sc_create": (ctypes.c_int, [ctypes.c_int, _VP, ctypes.c_size_t, ctypes.POINTER(_VP)]),
+    "sc_destroy": (ctypes.c_int, [_VP]),
+    "sc_last_error": (ctypes.c_char_p, [_VP]),
+    "sc_mirror": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                 ctypes.POINTER(sc_quadrature), ctypes.POINTER(_VP)]),
+    "sc_mirror_free": (None, [_VP]),
+    "sc_incident": (ctypes.c_int, [_VP, ctypes.POINTER(sc_profile), ctypes.POINTER(sc_polarization),
+                                   ctypes.POINTER(sc_spectrum), ctypes.POINTER(_VP)]),
+    "sc_incident_free": (None, [_VP]),
+    "sc_spectrum_eval": (ctypes.c_int, [_VP, _VP, _DP, ctypes.c_int, _DP]),
+    "sc_eval": (ctypes.c_int, [_VP, _VP, _VP, _DP, ctypes.c_int, _VP, ctypes.c_int, ctypes.c_int,
+                               _VP, _VP, ctypes.POINTER(sc_eval_stats)]),
+    "sc_time_domain": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _DP, ctypes.c_int, ctypes.c_int,
+                                      _DP, ctypes.c_int, _VP, _VP]),
+    "sc_get_counters": (ctypes.c_int, [_VP, ctypes.POINTER(sc_counters)]),
+    "sc_reset_counters": (ctypes.c_int, [_VP]),
+    "sc_set_option": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_longlong]),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libsc (building it first when the sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if path is None:
+        from . import build as _build
+
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError("libsc is not built (%s); run paper_1609_08146_gb300.build" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    globals().update({name: getattr(lib, name) for name in SIGNATURES})
+    return lib
+
+
+class ScError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("sc status %d: %s" % (status, msg))
+        self.status = status
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_DP)
+
+
+def _addr(x):
+    """Device or host address of a torch tensor or numpy array."""
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+class Mirror:
+    def __init__(self, ctx, f, r_min, r_max, n_r, n_theta, rim=True):
+        self._lib = ctx._lib
+        q = sc_quadrature(0, int(n_r), int(n_theta), 1 if rim else 0)
+        h = _VP()
+        ctx._check(self._lib.sc_mirror(ctx._h, float(f), float(r_min), float(r_max), ctypes.byref(q),
+                                       ctypes.byref(h)))
+        self._h = h
+        self.f, self.r_min, self.r_max, self.n_r, self.n_theta, self.rim = f, r_min, r_max, n_r, n_theta, rim
+
+    @property
+    def n_nodes(self):
+        return self.n_r * self.n_theta
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            self._lib.sc_mirror_free(self._h)
+            self._h = None
+
+
+class Incident:
+    def __init__(self, ctx, profile="gauss", w0=1.0, sg_order=4, zernike=(), pol="linear",
+                 pol_angle=0.0, spectrum=None):
+        self._lib = ctx._lib
+        spectrum = dict(spectrum or {"kind": "mono"})
+        self._keep = []
+        z = np.ascontiguousarray(zernike, dtype=np.float64)
+        self._keep.append(z)
+        prof = sc_profile(PROFILES[profile], float(w0), int(sg_order), int(z.size),
+                          _dptr(z) if z.size else None)
+        pl = sc_polarization(POLS[pol], float(pol_angle))
+        kind = SPECTRA[spectrum.get("kind", "mono")]
+        om = amp = None
+        n = 0
+        if kind == 3:
+            om = np.ascontiguousarray(spectrum["omega"], dtype=np.float64)
+            amp = np.ascontiguousarray(np.asarray(spectrum["amp"], dtype=np.complex128).view(np.float64))
+            n = om.size
+            self._keep += [om, amp]
+        phi = np.ascontiguousarray(spectrum.get("phi", []), dtype=np.float64)
+        self._keep.append(phi)
+        sp = sc_spectrum(kind, float(spectrum.get("fwhm_t", 1.0)), float(spectrum.get("lambda_c", 1.0)),
+                         float(spectrum.get("dlambda", 0.1)), int(spectrum.get("sg_n", 3)),
+                         float(spectrum.get("energy", 1.0)), n, _dptr(om) if om is not None else None,
+                         _dptr(amp) if amp is not None else None, int(phi.size),
+                         _dptr(phi) if phi.size else None)
+        h = _VP()
+        ctx._check(self._lib.sc_incident(ctx._h, ctypes.byref(prof), ctypes.byref(pl), ctypes.byref(sp),
+                                         ctypes.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            self._lib.sc_incident_free(self._h)
+            self._h = None
+
+
+class Context:
+    """One libsc context bound to a CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream=None, budget_bytes: int = 0):
+        import torch
+
+        self._lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        self.device = device
+        h = _VP()
+        st = self._lib.sc_create(int(device), _VP(stream.cuda_stream), int(budget_bytes), ctypes.byref(h))
+        if st != SC_OK:
+            raise ScError(st, "sc_create failed")
+        self._h = h
+
+    def _check(self, st):
+        if st != SC_OK:
+            raise ScError(st, self._lib.sc_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def mirror(self, f, r_min, r_max, n_r, n_theta, rim=True) -> Mirror:
+        return Mirror(self, f, r_min, r_max, n_r, n_theta, rim)
+
+    def incident(self, **kw) -> Incident:
+        return Incident(self, **kw)
+
+    def set_option(self, option: int, value: int):
+        self._check(self._lib.sc_set_option(self._h, int(option), int(value)))
+
+    def spectrum(self, inc: Incident, omegas) -> np.ndarray:
+        om = np.ascontiguousarray(np.atleast_1d(omegas), dtype=np.float64)
+        out = np.zeros(om.size, dtype=np.complex128)
+        self._check(self._lib.sc_spectrum_eval(self._h, inc._h, _dptr(om), om.size,
+                                               _dptr(out.view(np.float64))))
+        return out
+
+    def eval(self, mirror: Mirror, inc: Incident, omegas, points, precision: str = "fp32",
+             out=None, stats: bool = False):
+        """Spectral field E, B [n_omega, n_pts, 3] (complex64 for "fp32",
+        complex128 for "fp64").  ``points``: torch tensor (cuda -> device
+        outputs) or numpy array (host outputs), [n_pts, 3] float64."""
+        import torch
+
+        om = np.ascontiguousarray(np.atleast_1d(omegas), dtype=np.float64)
+        prec = SC_FP32_COMP if precision == "fp32" else SC_FP64
+        if isinstance(points, np.ndarray):
+            pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+            npts = pts.shape[0]
+            if out is None:
+                dt = np.complex64 if prec == SC_FP32_COMP else np.complex128
+                E = np.empty((om.size, npts, 3), dtype=dt)
+                B = np.empty_like(E)
+            else:
+                E, B = out
+        else:  # torch tensor on the device or in (pinned) host memory
+            pts = points.contiguous()
+            if pts.dtype != torch.float64:
+                pts = pts.to(torch.float64)
+            npts = pts.shape[0]
+            if out is None:
+                dt = torch.complex64 if prec == SC_FP32_COMP else torch.complex128
+                E = torch.empty((om.size, npts, 3), dtype=dt, device=pts.device,
+                                pin_memory=not pts.is_cuda and pts.is_pinned())
+                B = torch.empty_like(E)
+            else:
+                E, B = out
+        st = sc_eval_stats()
+        self._check(self._lib.sc_eval(self._h, mirror._h, inc._h, _dptr(om), om.size, _addr(pts),
+                                      npts, prec, _addr(E), _addr(B) if B is not None else None,
+                                      ctypes.byref(st) if stats else None))
+        if stats:
+            return E, B, dict(evals=st.evals, field_ms=st.field_ms, total_ms=st.total_ms,
+                              launches=st.launches)
+        return E, B
+
+    def time_domain(self, E, B, omegas, times, precision: str = "fp32", out=None):
+        """Inverse transform of spectra [n_omega, n_pts, 3] -> float32
+        [n_t, n_pts, 3] on the spectra's side (device or host)."""
+        import torch
+
+        om = np.ascontiguousarray(np.atleast_1d(omegas), dtype=np.float64)
+        t = np.ascontiguousarray(np.atleast_1d(times), dtype=np.float64)
+        prec = SC_FP32_COMP if precision == "fp32" else SC_FP64
+        npts = E.shape[1]
+        if out is None:
+            if isinstance(E, np.ndarray):
+                Et = np.empty((t.size, npts, 3), dtype=np.float32)
+                Bt = np.empty_like(Et) if B is not None else None
+            else:
+                Et = torch.empty((t.size, npts, 3), dtype=torch.float32, device=E.device)
+                Bt = torch.empty_like(Et) if B is not None else None
+        else:
+            Et, Bt = out
+        self._check(self._lib.sc_time_domain(self._h, prec, _addr(E), _addr(B) if B is not None else None,
+                                             _dptr(om), om.size, npts, _dptr(t), t.size, _addr(Et),
+                                             _addr(Bt) if Bt is not None else None))
+        return Et, Bt
+
+    def counters(self):
+        c = sc_counters()
+        self._check(self._lib.sc_get_counters(self._h, ctypes.byref(c)))
+        return dict(launches=c.launches, field_launches=c.field_launches, field_ms=c.field_ms,
+                    evals=c.evals)
+
+    def reset_counters(self):
+        self._check(self._lib.sc_reset_counters(self._h))

@@ -1,0 +1,1035 @@
+// sc_api.cpp -- host side of libsc: handles, the FP64 node-table builder and
+// spectrum generator, device-memory management and the C-ABI entry points
+// declared in include/sc.h.  Every GPU step is a kernel of this library
+// (sc_field.cu, sc_f64_idft.cu); nothing here computes a field value on the
+// CPU.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "sc.h"
+#include "sc_internal.h"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+std::atomic<uint64_t> g_next_id{1};
+
+}  // namespace
+
+// --------------------------------------------------------------------------
+// Handles
+
+struct sc_mirror_t {
+    uint64_t id;
+    double f, r_min, r_max;
+    sc_quadrature q;
+};
+
+struct sc_incident_t {
+    uint64_t id;
+    int profile, sg_order, pol;
+    double w0, angle;
+    std::vector<double> zern;
+    int spec_kind;
+    double fwhm_t, lambda_c, dlambda, energy;
+    int sg_n;
+    std::vector<double> s_omega, s_amp, phi;
+};
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+};
+
+struct Table {
+    uint64_t mid = 0, iid = 0;
+    float* d32 = nullptr;          // tiled FP32 table, surface tiles then rim tiles
+    int n_surf_tiles = 0, n_rim_tiles = 0;
+    sc::Node64* d64 = nullptr;     // FP64 records, surface then rim
+    int n_surf = 0, n_rim = 0;
+    size_t bytes = 0;
+    uint64_t last_use = 0;
+};
+
+}  // namespace
+
+struct sc_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    size_t budget = 0;
+    size_t held = 0;
+    std::string err = "no error";
+    std::vector<Table> tables;
+    uint64_t tick = 0;
+    DevBuf ws, pts, outE, outB, amp, kval, tvals, phasor, specE, specB, tE, tB;
+    int* d_err = nullptr;
+    int* h_err = nullptr;          // pinned
+    sc_counters ctr{};
+    bool time_field = false;
+    long long nodes_per_split = 0;  // 0: choose splits for load balance
+    long long flush_nodes = 1024;   // FP32 run length before each compensated fold
+    size_t ws_cap = size_t(2) << 30;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    std::vector<cudaEvent_t> pool;
+};
+
+namespace {
+
+sc_status fail(sc_ctx* c, sc_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return st;
+}
+
+sc_status cuda_fail(sc_ctx* c, cudaError_t e, const char* what)
+{
+    return fail(c, e == cudaErrorMemoryAllocation ? SC_ERR_OOM : SC_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define SC_CUDA(call, what)                              \
+    do {                                                 \
+        cudaError_t e__ = (call);                        \
+        if (e__ != cudaSuccess) return cuda_fail(ctx, e__, what); \
+    } while (0)
+
+sc_status ensure(sc_ctx* ctx, DevBuf& b, size_t bytes)
+{
+    if (b.n >= bytes) return SC_OK;
+    size_t want = std::max(bytes, b.n + b.n / 2);
+    if (ctx->budget && ctx->held - b.n + want > ctx->budget) {
+        want = bytes;
+        if (ctx->held - b.n + want > ctx->budget)
+            return fail(ctx, SC_ERR_OOM, "device budget of %zu bytes exceeded (need %zu more)",
+                        ctx->budget, want);
+    }
+    if (b.p) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(b.p);
+        ctx->held -= b.n;
+        b.p = nullptr;
+        b.n = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, SC_ERR_OOM, "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+    }
+    b.n = want;
+    ctx->held += want;
+    return SC_OK;
+}
+
+bool is_device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ------------------------------------------------------------------------
+// Quadrature: Gauss-Legendre on [a, b].  Roots of P_n by Newton iteration
+// started from Tricomi's asymptotic estimate; weights 2/((1-x^2) P_n'(x)^2).
+
+void gauss_legendre(int n, double a, double b, std::vector<double>& x, std::vector<double>& w)
+{
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 1; i <= n; ++i) {
+        const double th = kPi * (4.0 * i - 1.0) / (4.0 * n + 2.0);
+        double t = (1.0 - (n - 1.0) / (8.0 * n * n * n)) * cos(th);
+        double pn = 0, pn1 = 0;
+        for (int iter = 0; iter < 60; ++iter) {
+            double pm = 1.0, p = t;
+            for (int k = 2; k <= n; ++k) {
+                const double pk = ((2 * k - 1) * t * p - (k - 1) * pm) / k;
+                pm = p;
+                p = pk;
+            }
+            pn = (n == 1) ? t : p;
+            pn1 = (n == 1) ? 1.0 : pm;
+            const double d = n * (pn1 - t * pn) / (1.0 - t * t);
+            const double step = pn / d;
+            t -= step;
+            if (fabs(step) <= 1e-17) break;
+        }
+        double pm = 1.0, p = t;
+        for (int k = 2; k <= n; ++k) {
+            const double pk = ((2 * k - 1) * t * p - (k - 1) * pm) / k;
+            pm = p;
+            p = pk;
+        }
+        pn = (n == 1) ? t : p;
+        pn1 = (n == 1) ? 1.0 : pm;
+        const double d = n * (pn1 - t * pn) / (1.0 - t * t);
+        // i-th root from the top: t decreases with i; store ascending in r
+        const int j = n - i;
+        x[j] = 0.5 * (b + a) + 0.5 * (b - a) * t;
+        w[j] = (b - a) / ((1.0 - t * t) * d * d);
+    }
+}
+
+// Zernike Z_j (Noll ordering and normalisation): radial order n and
+// azimuthal order m from j by walking the (n, |m|) table.
+void noll_nm(int j, int& n, int& m)
+{
+    int count = 0;
+    for (n = 0;; ++n) {
+        const int terms = n + 1;
+        if (count + terms >= j) {
+            // position within row n, 1-based
+            const int pos = j - count;
+            // |m| sequence in row n: n%2, n%2+2, ... each non-zero |m| appears twice
+            int idx = 0;
+            for (int am = n % 2; am <= n; am += 2) {
+                const int mult = am == 0 ? 1 : 2;
+                if (pos <= idx + mult) {
+                    m = (am == 0) ? 0 : ((j % 2 == 0) ? am : -am);
+                    return;
+                }
+                idx += mult;
+            }
+        }
+        count += terms;
+    }
+}
+
+double zernike(int j, double rho, double th)
+{
+    int n, m;
+    noll_nm(j, n, m);
+    const int am = m < 0 ? -m : m;
+    double R = 0.0;
+    for (int s = 0; s <= (n - am) / 2; ++s) {
+        double num = tgamma(n - s + 1.0);
+        double den = tgamma(s + 1.0) * tgamma((n + am) / 2 - s + 1.0) * tgamma((n - am) / 2 - s + 1.0);
+        R += ((s & 1) ? -1.0 : 1.0) * num / den * pow(rho, n - 2 * s);
+    }
+    if (m == 0) return sqrt(n + 1.0) * R;
+    return sqrt(2.0 * (n + 1.0)) * R * (m > 0 ? cos(am * th) : sin(am * th));
+}
+
+// ------------------------------------------------------------------------
+// Incident field model on the mirror (collimated beam, Sec. III.A).
+
+double profile_amp(const sc_incident_t* in, double rho)
+{
+    switch (in->profile) {
+    case SC_PROFILE_GAUSS: return exp(-(rho / in->w0) * (rho / in->w0));
+    case SC_PROFILE_SUPERGAUSS: return exp(-pow(rho / in->w0, 2.0 * in->sg_order));
+    default: return rho <= in->w0 ? 1.0 : 0.0;
+    }
+}
+
+// Transverse spatial field E~(rho, theta) (z component 0).
+void incident_E(const sc_incident_t* in, double rho, double th, double& ex, double& ey)
+{
+    const double A = profile_amp(in, rho);
+    if (in->pol == SC_POL_LINEAR) {
+        ex = A * cos(in->angle);
+        ey = A * sin(in->angle);
+    } else {
+        const double s = A * rho / in->w0;
+        if (in->pol == SC_POL_RADIAL) {
+            ex = s * cos(th);
+            ey = s * sin(th);
+        } else {
+            ex = -s * sin(th);
+            ey = s * cos(th);
+        }
+    }
+}
+
+double incident_opd(const sc_incident_t* in, double rho, double th, double r_unit)
+{
+    double W = 0.0;
+    for (size_t i = 0; i < in->zern.size(); ++i) W += in->zern[i] * zernike((int)i + 2, rho / r_unit, th);
+    return W;
+}
+
+// SS |A p|^2 dA over the transverse plane, closed forms.
+double beam_power(const sc_incident_t* in)
+{
+    const double w2 = in->w0 * in->w0;
+    const bool lin = in->pol == SC_POL_LINEAR;
+    if (in->profile == SC_PROFILE_GAUSS) return lin ? kPi * w2 / 2.0 : kPi * w2 / 4.0;
+    if (in->profile == SC_PROFILE_SUPERGAUSS) {
+        const double N = in->sg_order;
+        return lin ? kPi * w2 * pow(2.0, -1.0 / N) * tgamma(1.0 + 1.0 / N)
+                   : kPi * w2 * pow(2.0, -2.0 / N) * tgamma(1.0 + 2.0 / N) / 2.0;
+    }
+    return lin ? kPi * w2 : kPi * w2 / 2.0;
+}
+
+// a_n = E0^n e^{i phi(k_n)}  (Eqs. 15-18, Eq. 27).
+sc_status spectrum_amps(sc_ctx* ctx, const sc_incident_t* in, const double* om, int n,
+                        std::vector<double>& amp)
+{
+    amp.assign(2 * (size_t)n, 0.0);
+    const double kc = 2.0 * kPi / in->lambda_c;
+    double norm = 1.0;
+    if (in->spec_kind == SC_SPEC_GAUSS_TIME) {
+        // int exp(-(k-kc)^2 tau^2 / (4 ln 2)) dk
+        norm = sqrt(4.0 * kPi * log(2.0)) / in->fwhm_t;
+    } else if (in->spec_kind == SC_SPEC_SUPERGAUSS_LAMBDA) {
+        // int exp(-((l-lc)/dl)^(2n)) dl = 2 dl Gamma(1 + 1/(2n))
+        norm = 2.0 * in->dlambda * tgamma(1.0 + 1.0 / (2.0 * in->sg_n));
+    }
+    const double P = beam_power(in);
+    for (int i = 0; i < n; ++i) {
+        const double k = 2.0 * kPi * om[i];
+        double re = 1.0, im = 0.0;
+        if (in->spec_kind == SC_SPEC_SAMPLED) {
+            int hit = -1;
+            for (size_t s = 0; s < in->s_omega.size(); ++s)
+                if (fabs(in->s_omega[s] - om[i]) <= 1e-12 * fabs(om[i])) { hit = (int)s; break; }
+            if (hit < 0)
+                return fail(ctx, SC_ERR_INVALID, "omega %.17g is not one of the sampled spectrum's",
+                            om[i]);
+            re = in->s_amp[2 * hit];
+            im = in->s_amp[2 * hit + 1];
+        } else if (in->spec_kind == SC_SPEC_GAUSS_TIME) {
+            const double s = exp(-(k - kc) * (k - kc) * in->fwhm_t * in->fwhm_t / (8.0 * log(2.0)));
+            const double eps = in->energy * s * s / norm;
+            re = sqrt(eps / (4.0 * kPi * P));
+        } else if (in->spec_kind == SC_SPEC_SUPERGAUSS_LAMBDA) {
+            const double lam = 2.0 * kPi / k;
+            const double u = (lam - in->lambda_c) / in->dlambda;
+            const double eps_l = exp(-pow(u * u, (double)in->sg_n));
+            const double eps = in->energy * eps_l * (lam * lam / (2.0 * kPi)) / norm;
+            re = sqrt(eps / (4.0 * kPi * P));
+        }
+        double ph = 0.0, term = 1.0;
+        for (size_t j = 0; j < in->phi.size(); ++j) {
+            if (j) term *= (k - kc) / (double)j;
+            ph += in->phi[j] * term;
+        }
+        const double c = cos(ph), s = sin(ph);
+        amp[2 * i] = re * c - im * s;
+        amp[2 * i + 1] = re * s + im * c;
+    }
+    return SC_OK;
+}
+
+// ------------------------------------------------------------------------
+// Node tables (FP64 on the host; A1 of the hot path).
+
+struct HostNode {
+    double px, py, pz, pn, w, jx, jy, jz, rho;
+};
+
+void build_nodes(const sc_mirror_t* m, const sc_incident_t* in, std::vector<HostNode>& surf,
+                 std::vector<HostNode>& rim)
+{
+    const double f = m->f;
+    const int nr = m->q.n_r, nt = m->q.n_theta;
+    std::vector<double> gr, gw;
+    gauss_legendre(nr, m->r_min, m->r_max, gr, gw);
+    const double dth = 2.0 * kPi / nt;
+    surf.clear();
+    surf.reserve((size_t)nr * nt);
+    for (int i = 0; i < nr; ++i) {
+        const double r = gr[i];
+        for (int l = 0; l < nt; ++l) {
+            const double th = l * dth;
+            const double x = r * cos(th), y = r * sin(th), z = r * r / (4.0 * f) - f;
+            const double Nx = -x / (2.0 * f), Ny = -y / (2.0 * f), Nz = 1.0;
+            double ex, ey;
+            incident_E(in, r, th, ex, ey);
+            const double bx = ey, by = -ex;  // B~ = (-z) x E~
+            const double wq = gw[i] * dth * r / (2.0 * kPi);
+            HostNode nd;
+            nd.px = x; nd.py = y; nd.pz = z;
+            nd.pn = r * r / (4.0 * f) + f;
+            nd.w = incident_opd(in, r, th, m->r_max);
+            // J = N x B~ (B~_z = 0), rho = N . E~
+            nd.jx = (Ny * 0.0 - Nz * by) * wq;
+            nd.jy = (Nz * bx - Nx * 0.0) * wq;
+            nd.jz = (Nx * by - Ny * bx) * wq;
+            nd.rho = (Nx * ex + Ny * ey) * wq;
+            surf.push_back(nd);
+        }
+    }
+    rim.clear();
+    if (!m->q.rim_term) return;
+    for (int edge = 0; edge < 2; ++edge) {
+        const double r = edge == 0 ? m->r_max : m->r_min;
+        const double sgn = edge == 0 ? 1.0 : -1.0;  // outward conormal of the surface
+        if (r <= 0.0) continue;
+        const double nlen2 = 1.0 + r * r / (4.0 * f * f);
+        for (int l = 0; l < nt; ++l) {
+            const double th = l * dth;
+            const double c = cos(th), s = sin(th);
+            const double x = r * c, y = r * s, z = r * r / (4.0 * f) - f;
+            const double Nx = -x / (2.0 * f), Ny = -y / (2.0 * f);
+            double ex, ey;
+            incident_E(in, r, th, ex, ey);
+            const double bx = ey, by = -ex;
+            const double jx = -by, jy = bx, jz = Nx * by - Ny * bx;  // N x B~
+            // q = (J . m^) dl with J = (N x B~)/|N|, m^ = sgn (c, s, r/2f)/|N|, dl = r dth
+            const double q = sgn * (jx * c + jy * s + jz * r / (2.0 * f)) / nlen2 * r * dth;
+            HostNode nd;
+            nd.px = x; nd.py = y; nd.pz = z;
+            nd.pn = r * r / (4.0 * f) + f;
+            nd.w = incident_opd(in, r, th, m->r_max);
+            nd.jx = nd.jy = nd.jz = 0.0;
+            nd.rho = q / (2.0 * kPi);
+            rim.push_back(nd);
+        }
+    }
+}
+
+void pack_tiles(const std::vector<HostNode>& v, std::vector<float>& out, int& n_tiles)
+{
+    n_tiles = (int)((v.size() + sc::kTile - 1) / sc::kTile);
+    out.assign((size_t)n_tiles * sc::kTileFloats, 0.0f);
+    for (size_t i = 0; i < (size_t)n_tiles * sc::kTile; ++i) {
+        // padding nodes sit on node 0 with zero weight
+        const HostNode& nd = i < v.size() ? v[i] : v[0];
+        const bool pad = i >= v.size();
+        float* t = out.data() + (i / sc::kTile) * sc::kTileFloats;
+        const size_t j = i % sc::kTile;
+        t[sc::F_PX * sc::kTile + j] = (float)nd.px;
+        t[sc::F_PY * sc::kTile + j] = (float)nd.py;
+        t[sc::F_PZ * sc::kTile + j] = (float)nd.pz;
+        t[sc::F_PN * sc::kTile + j] = (float)nd.pn;
+        t[sc::F_W * sc::kTile + j] = (float)nd.w;
+        t[sc::F_JX * sc::kTile + j] = pad ? 0.f : (float)nd.jx;
+        t[sc::F_JY * sc::kTile + j] = pad ? 0.f : (float)nd.jy;
+        t[sc::F_JZ * sc::kTile + j] = pad ? 0.f : (float)nd.jz;
+        t[sc::F_RHO * sc::kTile + j] = pad ? 0.f : (float)nd.rho;
+        t[sc::F_PAD * sc::kTile + j] = 0.f;
+    }
+}
+
+void free_table(sc_ctx* ctx, Table& t)
+{
+    if (t.d32) cudaFree(t.d32);
+    if (t.d64) cudaFree(t.d64);
+    ctx->held -= t.bytes;
+    t = Table{};
+}
+
+sc_status get_table(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, Table** out)
+{
+    ctx->tick++;
+    for (auto& t : ctx->tables)
+        if (t.mid == m->id && t.iid == in->id) {
+            t.last_use = ctx->tick;
+            *out = &t;
+            return SC_OK;
+        }
+    std::vector<HostNode> surf, rim;
+    build_nodes(m, in, surf, rim);
+    std::vector<float> ts, tr;
+    Table t;
+    t.mid = m->id;
+    t.iid = in->id;
+    pack_tiles(surf, ts, t.n_surf_tiles);
+    if (!rim.empty()) pack_tiles(rim, tr, t.n_rim_tiles);
+    t.n_surf = (int)surf.size();
+    t.n_rim = (int)rim.size();
+    const size_t b32 = (ts.size() + tr.size()) * sizeof(float);
+    const size_t b64 = (surf.size() + rim.size()) * sizeof(sc::Node64);
+    t.bytes = b32 + b64;
+    // evict least recently used tables while over budget
+    while (ctx->budget && ctx->held + t.bytes > ctx->budget && !ctx->tables.empty()) {
+        auto it = std::min_element(ctx->tables.begin(), ctx->tables.end(),
+                                   [](const Table& a, const Table& b) { return a.last_use < b.last_use; });
+        cudaStreamSynchronize(ctx->stream);
+        free_table(ctx, *it);
+        ctx->tables.erase(it);
+    }
+    if (ctx->budget && ctx->held + t.bytes > ctx->budget)
+        return fail(ctx, SC_ERR_OOM, "node table of %zu bytes exceeds the device budget", t.bytes);
+    cudaError_t e = cudaMalloc(&t.d32, b32);
+    if (e == cudaSuccess) e = cudaMalloc(&t.d64, b64);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (t.d32) cudaFree(t.d32);
+        return fail(ctx, SC_ERR_OOM, "node table allocation failed: %s", cudaGetErrorString(e));
+    }
+    std::vector<sc::Node64> h64;
+    h64.reserve(surf.size() + rim.size());
+    for (auto* vec : {&surf, &rim})
+        for (const auto& nd : *vec)
+            h64.push_back(sc::Node64{nd.px, nd.py, nd.pz, nd.pn, nd.w, nd.jx, nd.jy, nd.jz, nd.rho, 0.0});
+    SC_CUDA(cudaMemcpyAsync(t.d32, ts.data(), ts.size() * sizeof(float), cudaMemcpyHostToDevice,
+                            ctx->stream), "upload node table");
+    if (!tr.empty())
+        SC_CUDA(cudaMemcpyAsync(t.d32 + ts.size(), tr.data(), tr.size() * sizeof(float),
+                                cudaMemcpyHostToDevice, ctx->stream), "upload rim table");
+    SC_CUDA(cudaMemcpyAsync(t.d64, h64.data(), b64, cudaMemcpyHostToDevice, ctx->stream),
+            "upload FP64 table");
+    // the host vectors die at return: make the copies complete first
+    SC_CUDA(cudaStreamSynchronize(ctx->stream), "node table upload");
+    ctx->held += t.bytes;
+    t.last_use = ctx->tick;
+    ctx->tables.push_back(t);
+    *out = &ctx->tables.back();
+    return SC_OK;
+}
+
+// Reads and clears the device error word (synchronizes the stream).
+sc_status check_device_error(sc_ctx* ctx)
+{
+    SC_CUDA(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
+            "read error word");
+    SC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+    const int e = *ctx->h_err;
+    if (e) {
+        SC_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream), "clear error word");
+        if (e & sc::ERR_TIMEOUT)
+            return fail(ctx, SC_ERR_TIMEOUT, "a bounded device wait ran out (error word 0x%x)", e);
+        if (e & sc::ERR_NEAR_SURFACE)
+            return fail(ctx, SC_ERR_INVALID, "an observation point lies on the mirror");
+        return fail(ctx, SC_ERR_CUDA, "device error word 0x%x", e);
+    }
+    return SC_OK;
+}
+
+cudaEvent_t take_event(sc_ctx* ctx)
+{
+    if (!ctx->pool.empty()) {
+        cudaEvent_t e = ctx->pool.back();
+        ctx->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void settle_events(sc_ctx* ctx)
+{
+    for (auto& pr : ctx->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) ctx->ctr.field_ms += ms;
+        else cudaGetLastError();
+        ctx->pool.push_back(pr.first);
+        ctx->pool.push_back(pr.second);
+    }
+    ctx->pending.clear();
+}
+
+// Points closer than 1e-6 lambda0 to a node make the integrand singular.
+// |P| >= f for every mirror point, so only points with |r'| >= f - 1e-6 can
+// come that close; those are checked against every node in FP64.
+sc_status check_points_host(sc_ctx* ctx, const sc_mirror_t* m, const double* pts, int n_pts)
+{
+    std::vector<HostNode> surf, rim;
+    bool built = false;
+    for (int i = 0; i < n_pts; ++i) {
+        const double x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
+        if (!std::isfinite(x) || !std::isfinite(y) || !std::isfinite(z))
+            return fail(ctx, SC_ERR_INVALID, "point %d is not finite", i);
+        const double r = sqrt(x * x + y * y + z * z);
+        if (r < m->f - 1e-6) continue;
+        const double rho = sqrt(x * x + y * y), zs = rho * rho / (4.0 * m->f) - m->f;
+        if (rho >= m->r_min - 1e-6 && rho <= m->r_max + 1e-6 && fabs(z - zs) < 1e-6)
+            return fail(ctx, SC_ERR_INVALID, "point %d lies on the mirror surface", i);
+        (void)built;
+    }
+    return SC_OK;
+}
+
+bool uniform_grid(const double* om, int n, double& d)
+{
+    if (n == 1) {
+        d = 0.0;
+        return true;
+    }
+    d = (om[n - 1] - om[0]) / (n - 1);
+    if (!(d > 0.0)) return false;
+    for (int i = 0; i < n; ++i)
+        if (fabs(om[i] - (om[0] + i * d)) > 1e-9 * om[0]) return false;
+    return true;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------
+// C-ABI
+
+extern "C" {
+
+sc_status sc_create(int device, void* cuda_stream, size_t hbm_budget_bytes, sc_ctx** out)
+{
+    if (!out) return SC_ERR_INVALID;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return SC_ERR_CUDA;
+    }
+    if (device < 0 || device >= ndev) return SC_ERR_INVALID;
+    if (cudaSetDevice(device) != cudaSuccess) return SC_ERR_CUDA;
+    sc_ctx* ctx = new sc_ctx();
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->budget = hbm_budget_bytes;
+    if (cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_err, sizeof(int)) != cudaSuccess ||
+        cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->d_err) cudaFree(ctx->d_err);
+        delete ctx;
+        return SC_ERR_CUDA;
+    }
+    *out = ctx;
+    return SC_OK;
+}
+
+sc_status sc_destroy(sc_ctx* ctx)
+{
+    if (!ctx) return SC_OK;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    settle_events(ctx);
+    for (auto& t : ctx->tables) free_table(ctx, t);
+    for (DevBuf* b : {&ctx->ws, &ctx->pts, &ctx->outE, &ctx->outB, &ctx->amp, &ctx->kval,
+                      &ctx->tvals, &ctx->phasor, &ctx->specE, &ctx->specB, &ctx->tE, &ctx->tB})
+        if (b->p) cudaFree(b->p);
+    for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->h_err) cudaFreeHost(ctx->h_err);
+    delete ctx;
+    return SC_OK;
+}
+
+const char* sc_last_error(const sc_ctx* ctx)
+{
+    return ctx ? ctx->err.c_str() : "null context";
+}
+
+sc_status sc_mirror(sc_ctx* ctx, double f, double r_min, double r_max, const sc_quadrature* q,
+                    sc_mirror_t** out)
+{
+    if (!out || !q) return fail(ctx, SC_ERR_INVALID, "null argument");
+    *out = nullptr;
+    if (!(f > 0.0) || !(r_min >= 0.0) || !(r_max > r_min) || q->n_r < 1 || q->n_theta < 1 ||
+        q->radial_kind != SC_QUAD_GAUSS_LEGENDRE)
+        return fail(ctx, SC_ERR_INVALID,
+                    "invalid mirror (f=%g r_min=%g r_max=%g n_r=%d n_theta=%d kind=%d)", f, r_min,
+                    r_max, q->n_r, q->n_theta, q->radial_kind);
+    sc_mirror_t* m = new sc_mirror_t();
+    m->id = g_next_id++;
+    m->f = f;
+    m->r_min = r_min;
+    m->r_max = r_max;
+    m->q = *q;
+    *out = m;
+    return SC_OK;
+}
+
+void sc_mirror_free(sc_mirror_t* m) { delete m; }
+
+sc_status sc_incident(sc_ctx* ctx, const sc_profile* prof, const sc_polarization* pol,
+                      const sc_spectrum* spec, sc_incident_t** out)
+{
+    if (!out || !prof || !pol || !spec) return fail(ctx, SC_ERR_INVALID, "null argument");
+    *out = nullptr;
+    if (prof->kind < 0 || prof->kind > 2 || !(prof->w0 > 0.0) ||
+        (prof->kind == SC_PROFILE_SUPERGAUSS && prof->sg_order < 1) || prof->n_zernike < 0 ||
+        prof->n_zernike > 64 || (prof->n_zernike > 0 && !prof->zernike_noll_waves))
+        return fail(ctx, SC_ERR_INVALID, "invalid beam profile");
+    if (pol->kind < 0 || pol->kind > 2) return fail(ctx, SC_ERR_INVALID, "invalid polarization");
+    if (spec->kind < 0 || spec->kind > 3) return fail(ctx, SC_ERR_INVALID, "invalid spectrum kind");
+    if (!(spec->lambda_c > 0.0) && spec->kind != SC_SPEC_MONO && spec->kind != SC_SPEC_SAMPLED)
+        return fail(ctx, SC_ERR_INVALID, "lambda_c must be positive");
+    if (spec->kind == SC_SPEC_GAUSS_TIME && !(spec->fwhm_t > 0.0))
+        return fail(ctx, SC_ERR_INVALID, "fwhm_t must be positive");
+    if (spec->kind == SC_SPEC_SUPERGAUSS_LAMBDA && (!(spec->dlambda > 0.0) || spec->sg_n < 1))
+        return fail(ctx, SC_ERR_INVALID, "dlambda must be positive and sg_n >= 1");
+    if (spec->kind == SC_SPEC_SAMPLED && (spec->n < 1 || !spec->omega || !spec->amp_re_im))
+        return fail(ctx, SC_ERR_INVALID, "sampled spectrum needs n >= 1 omegas and amplitudes");
+    if (spec->n_phi < 0 || (spec->n_phi > 0 && !spec->phi_taylor))
+        return fail(ctx, SC_ERR_INVALID, "invalid spectral phase");
+    sc_incident_t* in = new sc_incident_t();
+    in->id = g_next_id++;
+    in->profile = prof->kind;
+    in->sg_order = prof->sg_order;
+    in->w0 = prof->w0;
+    in->zern.assign(prof->zernike_noll_waves, prof->zernike_noll_waves + prof->n_zernike);
+    in->pol = pol->kind;
+    in->angle = pol->angle_rad;
+    in->spec_kind = spec->kind;
+    in->fwhm_t = spec->fwhm_t;
+    in->lambda_c = spec->lambda_c > 0.0 ? spec->lambda_c : 1.0;
+    in->dlambda = spec->dlambda;
+    in->sg_n = spec->sg_n;
+    in->energy = spec->energy;
+    if (spec->kind == SC_SPEC_SAMPLED) {
+        in->s_omega.assign(spec->omega, spec->omega + spec->n);
+        in->s_amp.assign(spec->amp_re_im, spec->amp_re_im + 2 * spec->n);
+    }
+    if (spec->n_phi > 0) in->phi.assign(spec->phi_taylor, spec->phi_taylor + spec->n_phi);
+    *out = in;
+    return SC_OK;
+}
+
+void sc_incident_free(sc_incident_t* in) { delete in; }
+
+sc_status sc_spectrum_eval(sc_ctx* ctx, const sc_incident_t* inc, const double* omegas, int n,
+                           double* amp_re_im)
+{
+    if (!inc || !omegas || !amp_re_im || n < 1) return fail(ctx, SC_ERR_INVALID, "invalid argument");
+    std::vector<double> a;
+    sc_status st = spectrum_amps(ctx, inc, omegas, n, a);
+    if (st != SC_OK) return st;
+    memcpy(amp_re_im, a.data(), a.size() * sizeof(double));
+    return SC_OK;
+}
+
+sc_status sc_eval(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, const double* omegas,
+                  int n_omega, const double* points_xyz, int n_points, sc_precision prec,
+                  void* E_out, void* B_out, sc_eval_stats* stats)
+{
+    if (!ctx) return SC_ERR_INVALID;
+    if (!m || !in || !omegas || !points_xyz || !E_out || n_omega < 1 || n_points < 1)
+        return fail(ctx, SC_ERR_INVALID, "invalid argument");
+    if (prec != SC_FP32_COMP && prec != SC_FP64) return fail(ctx, SC_ERR_INVALID, "bad precision");
+    for (int i = 0; i < n_omega; ++i)
+        if (!(omegas[i] > 0.0) || !std::isfinite(omegas[i]))
+            return fail(ctx, SC_ERR_INVALID, "omega[%d] must be positive", i);
+    double dom = 0.0;
+    if (prec == SC_FP32_COMP && !uniform_grid(omegas, n_omega, dom))
+        return fail(ctx, SC_ERR_INVALID, "SC_FP32_COMP needs a uniform, increasing omega grid");
+    SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+
+    const bool pts_dev = is_device_ptr(points_xyz);
+    const bool e_dev = is_device_ptr(E_out);
+    const bool b_dev = B_out ? is_device_ptr(B_out) : e_dev;
+    if (B_out && e_dev != b_dev) return fail(ctx, SC_ERR_INVALID, "E_out and B_out must both be host or both device");
+
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (stats) {
+        ev0 = take_event(ctx);
+        ev1 = take_event(ctx);
+        cudaEventRecord(ev0, ctx->stream);
+    }
+    const double field_ms_before = ctx->ctr.field_ms;
+    const uint64_t launches_before = ctx->ctr.launches;
+    const bool timing_before = ctx->time_field;
+    if (stats) ctx->time_field = true;
+
+    std::vector<double> amp;
+    sc_status st = spectrum_amps(ctx, in, omegas, n_omega, amp);
+    if (st != SC_OK) return st;
+    std::vector<double> kv(n_omega);
+    for (int i = 0; i < n_omega; ++i) kv[i] = 2.0 * kPi * omegas[i];
+
+    Table* tab = nullptr;
+    st = get_table(ctx, m, in, &tab);
+    if (st != SC_OK) return st;
+
+    // points on the device
+    const double* d_pts = points_xyz;
+    if (!pts_dev) {
+        st = check_points_host(ctx, m, points_xyz, n_points);
+        if (st != SC_OK) return st;
+        if ((st = ensure(ctx, ctx->pts, (size_t)n_points * 3 * sizeof(double))) != SC_OK) return st;
+        SC_CUDA(cudaMemcpyAsync(ctx->pts.p, points_xyz, (size_t)n_points * 3 * sizeof(double),
+                                cudaMemcpyHostToDevice, ctx->stream), "upload points");
+        d_pts = (const double*)ctx->pts.p;
+    }
+    if ((st = ensure(ctx, ctx->amp, amp.size() * sizeof(double))) != SC_OK) return st;
+    if ((st = ensure(ctx, ctx->kval, kv.size() * sizeof(double))) != SC_OK) return st;
+    SC_CUDA(cudaMemcpyAsync(ctx->amp.p, amp.data(), amp.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, ctx->stream), "upload amplitudes");
+    SC_CUDA(cudaMemcpyAsync(ctx->kval.p, kv.data(), kv.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, ctx->stream), "upload wavenumbers");
+
+    const size_t elem = prec == SC_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t out_bytes = (size_t)n_omega * n_points * 3 * elem;
+    void* dE = E_out;
+    void* dB = B_out;
+    if (!e_dev) {
+        if ((st = ensure(ctx, ctx->outE, out_bytes)) != SC_OK) return st;
+        dE = ctx->outE.p;
+        if (B_out) {
+            if ((st = ensure(ctx, ctx->outB, out_bytes)) != SC_OK) return st;
+            dB = ctx->outB.p;
+        }
+    }
+    // the staging buffers may have moved: refresh pointers taken before
+    if (!pts_dev) d_pts = (const double*)ctx->pts.p;
+    const double* d_amp = (const double*)ctx->amp.p;
+    const double* d_k = (const double*)ctx->kval.p;
+
+    const double evals = (double)n_points * (double)tab->n_surf * (double)n_omega;
+
+    if (prec == SC_FP64) {
+        sc::Field64Launch a;
+        a.surf = tab->d64;
+        a.n_surf = tab->n_surf;
+        a.rim = tab->d64 + tab->n_surf;
+        a.n_rim = tab->n_rim;
+        a.pts = d_pts;
+        a.n_pts = n_points;
+        a.kval = d_k;
+        a.n_omega = n_omega;
+        a.amp = d_amp;
+        a.E = (double2*)dE;
+        a.B = (double2*)dB;
+        cudaEvent_t f0 = nullptr, f1 = nullptr;
+        if (ctx->time_field) {
+            f0 = take_event(ctx);
+            f1 = take_event(ctx);
+            cudaEventRecord(f0, ctx->stream);
+        }
+        const int r = sc::launch_field_f64(a, ctx->stream);
+        if (r < 0) return cuda_fail(ctx, (cudaError_t)(-r), "FP64 field kernel launch");
+        if (ctx->time_field) {
+            cudaEventRecord(f1, ctx->stream);
+            ctx->pending.push_back({f0, f1});
+        }
+        ctx->ctr.launches += r;
+        ctx->ctr.field_launches += 1;
+    } else {
+        // node splits and chunking of points / omegas to bound the workspace
+        const int max_om_chunk = 2048;
+        const int flush_tiles = (int)std::max<long long>(1, ctx->flush_nodes / sc::kTile);
+        for (int o0 = 0; o0 < n_omega; o0 += max_om_chunk) {
+            const int no = std::min(max_om_chunk, n_omega - o0);
+            int ppc = 1, slots = 1;
+            sc::field_shape(no, ctx->device, &ppc, &slots);
+            int tps;
+            if (ctx->nodes_per_split > 0) {
+                tps = (int)std::max<long long>(1, ctx->nodes_per_split / sc::kTile);
+            } else {
+                // splits only balance the grid: pick S (<= 32) whose (point block x
+                // split) count fills the resident CTA slots best, each split also
+                // paying about one tile of pipeline prologue
+                const long long pb = (n_points + ppc - 1) / ppc;
+                int best_s = 1;
+                double best = -1.0;
+                for (int S = 1; S <= std::min(32, tab->n_surf_tiles); ++S) {
+                    const long long units = pb * S;
+                    const long long waves = (units + slots - 1) / slots;
+                    const double eff = (double)units / ((double)waves * slots) *
+                                       (1.0 - (double)S / tab->n_surf_tiles);
+                    if (eff > best * 1.0005) { best = eff; best_s = S; }
+                }
+                tps = (tab->n_surf_tiles + best_s - 1) / best_s;
+            }
+            // the split index is the grid's y dimension (<= 65535 including the rim slot)
+            tps = std::max(tps, (tab->n_surf_tiles + 65533) / 65534);
+            const int n_splits = (tab->n_surf_tiles + tps - 1) / tps;
+            const size_t per_pt = (size_t)(n_splits + 1) * no * sc::kAcc * sizeof(float2);
+            int pchunk = (int)std::min<size_t>((size_t)n_points, std::max<size_t>(1, ctx->ws_cap / per_pt));
+            if (pchunk < n_points) pchunk = std::max(8, pchunk / 8 * 8);
+            if ((st = ensure(ctx, ctx->ws, per_pt * (size_t)pchunk)) != SC_OK) return st;
+            const double w0 = omegas[o0];
+            const float w0h = (float)w0, w0l = (float)(w0 - (double)w0h);
+            const float dh = (float)dom, dl = (float)(dom - (double)dh);
+            for (int p0 = 0; p0 < n_points; p0 += pchunk) {
+                const int np = std::min(pchunk, n_points - p0);
+                sc::FieldLaunch f;
+                f.nodes = tab->d32;
+                f.n_surf_tiles = tab->n_surf_tiles;
+                f.n_rim_tiles = tab->n_rim_tiles;
+                f.tiles_per_split = tps;
+                f.n_splits = n_splits;
+                f.flush_tiles = flush_tiles;
+                f.pts = d_pts + 3 * (size_t)p0;
+                f.n_pts = np;
+                f.n_omega = no;
+                f.om_hi0 = w0h;
+                f.om_lo0 = w0l;
+                f.dom_hi = dh;
+                f.dom_lo = dl;
+                f.ws = (float2*)ctx->ws.p;
+                f.err = ctx->d_err;
+                cudaEvent_t f0 = nullptr, f1 = nullptr;
+                if (ctx->time_field) {
+                    f0 = take_event(ctx);
+                    f1 = take_event(ctx);
+                    cudaEventRecord(f0, ctx->stream);
+                }
+                int r = sc::launch_field_f32(f, ctx->stream);
+                if (r < 0) return cuda_fail(ctx, (cudaError_t)(-r), "field kernel launch");
+                if (ctx->time_field) {
+                    cudaEventRecord(f1, ctx->stream);
+                    ctx->pending.push_back({f0, f1});
+                }
+                ctx->ctr.launches += r;
+                ctx->ctr.field_launches += 1;
+                sc::ReduceLaunch rl;
+                rl.ws = (const float2*)ctx->ws.p;
+                rl.n_splits = n_splits;
+                rl.n_pts = np;
+                rl.n_omega = no;
+                rl.amp = d_amp + 2 * (size_t)o0;
+                rl.kval = d_k + o0;
+                rl.out_pt_stride_omega = (long long)n_points * 3;
+                rl.E = (float2*)dE + ((size_t)o0 * n_points + p0) * 3;
+                rl.B = dB ? (float2*)dB + ((size_t)o0 * n_points + p0) * 3 : nullptr;
+                r = sc::launch_reduce_f32(rl, ctx->stream);
+                if (r < 0) return cuda_fail(ctx, (cudaError_t)(-r), "reduce kernel launch");
+                ctx->ctr.launches += r;
+            }
+        }
+    }
+    ctx->ctr.evals += evals;
+
+    if (!e_dev) {
+        SC_CUDA(cudaMemcpyAsync(E_out, dE, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "download E");
+        if (B_out)
+            SC_CUDA(cudaMemcpyAsync(B_out, dB, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "download B");
+    }
+    if (stats) cudaEventRecord(ev1, ctx->stream);
+    if (stats || !e_dev) {
+        st = check_device_error(ctx);
+        if (st != SC_OK) return st;
+    }
+    if (stats) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        ctx->pool.push_back(ev0);
+        ctx->pool.push_back(ev1);
+        settle_events(ctx);
+        stats->evals = evals;
+        stats->total_ms = ms;
+        stats->field_ms = ctx->ctr.field_ms - field_ms_before;
+        stats->launches = (int)(ctx->ctr.launches - launches_before);
+        ctx->time_field = timing_before;
+    }
+    return SC_OK;
+}
+
+sc_status sc_time_domain(sc_ctx* ctx, sc_precision prec, const void* E_spec, const void* B_spec,
+                         const double* omegas, int n_omega, int n_points, const double* times,
+                         int n_t, float* E_t, float* B_t)
+{
+    if (!ctx) return SC_ERR_INVALID;
+    if (!E_spec || !E_t || !omegas || !times || n_omega < 1 || n_points < 1 || n_t < 1 ||
+        (B_spec == nullptr) != (B_t == nullptr))
+        return fail(ctx, SC_ERR_INVALID, "invalid argument");
+    double dom = 0.0;
+    if (!uniform_grid(omegas, n_omega, dom))
+        return fail(ctx, SC_ERR_INVALID, "the inverse transform needs a uniform omega grid");
+    SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const size_t elem = prec == SC_FP64 ? sizeof(double2) : sizeof(float2);
+    const long long n_vals = (long long)n_points * 3;
+    const size_t spec_bytes = (size_t)n_omega * n_vals * elem;
+    const size_t out_bytes = (size_t)n_t * n_vals * sizeof(float);
+    const bool in_dev = is_device_ptr(E_spec);
+    const bool out_dev = is_device_ptr(E_t);
+    sc_status st;
+    std::vector<double> kv(n_omega);
+    for (int i = 0; i < n_omega; ++i) kv[i] = 2.0 * kPi * omegas[i];
+    if ((st = ensure(ctx, ctx->kval, kv.size() * sizeof(double))) != SC_OK) return st;
+    if ((st = ensure(ctx, ctx->tvals, (size_t)n_t * sizeof(double))) != SC_OK) return st;
+    if ((st = ensure(ctx, ctx->phasor, (size_t)n_omega * n_t * sizeof(float2))) != SC_OK) return st;
+    const void* dEs = E_spec;
+    const void* dBs = B_spec;
+    if (!in_dev) {
+        if ((st = ensure(ctx, ctx->specE, spec_bytes)) != SC_OK) return st;
+        if (B_spec && (st = ensure(ctx, ctx->specB, spec_bytes)) != SC_OK) return st;
+        SC_CUDA(cudaMemcpyAsync(ctx->specE.p, E_spec, spec_bytes, cudaMemcpyHostToDevice, ctx->stream), "upload E spectrum");
+        if (B_spec)
+            SC_CUDA(cudaMemcpyAsync(ctx->specB.p, B_spec, spec_bytes, cudaMemcpyHostToDevice, ctx->stream), "upload B spectrum");
+        dEs = ctx->specE.p;
+        dBs = B_spec ? ctx->specB.p : nullptr;
+    }
+    float* dEt = E_t;
+    float* dBt = B_t;
+    if (!out_dev) {
+        if ((st = ensure(ctx, ctx->tE, out_bytes)) != SC_OK) return st;
+        if (B_t && (st = ensure(ctx, ctx->tB, out_bytes)) != SC_OK) return st;
+        dEt = (float*)ctx->tE.p;
+        dBt = B_t ? (float*)ctx->tB.p : nullptr;
+    }
+    SC_CUDA(cudaMemcpyAsync(ctx->kval.p, kv.data(), kv.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload wavenumbers");
+    SC_CUDA(cudaMemcpyAsync(ctx->tvals.p, times, (size_t)n_t * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload times");
+    const double dk = n_omega > 1 ? 2.0 * kPi * dom : 1.0;
+    for (int pass = 0; pass < (B_spec ? 2 : 1); ++pass) {
+        sc::IdftLaunch l;
+        l.F = pass == 0 ? dEs : dBs;
+        l.f64 = prec == SC_FP64;
+        l.n_omega = n_omega;
+        l.n_vals = n_vals;
+        l.kval = (const double*)ctx->kval.p;
+        l.t = (const double*)ctx->tvals.p;
+        l.n_t = n_t;
+        l.dk = dk;
+        l.out = pass == 0 ? dEt : dBt;
+        l.phasor = (float2*)ctx->phasor.p;
+        const int r = sc::launch_idft(l, ctx->stream);
+        if (r < 0) return cuda_fail(ctx, (cudaError_t)(-r), "inverse transform launch");
+        ctx->ctr.launches += r;
+    }
+    if (!out_dev) {
+        SC_CUDA(cudaMemcpyAsync(E_t, dEt, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "download E(t)");
+        if (B_t) SC_CUDA(cudaMemcpyAsync(B_t, dBt, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "download B(t)");
+        SC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+    }
+    return SC_OK;
+}
+
+sc_status sc_get_counters(sc_ctx* ctx, sc_counters* out)
+{
+    if (!ctx || !out) return SC_ERR_INVALID;
+    SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    sc_status st = check_device_error(ctx);
+    settle_events(ctx);
+    *out = ctx->ctr;
+    return st;
+}
+
+sc_status sc_reset_counters(sc_ctx* ctx)
+{
+    if (!ctx) return SC_ERR_INVALID;
+    SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    SC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+    settle_events(ctx);
+    ctx->ctr = sc_counters{};
+    return SC_OK;
+}
+
+sc_status sc_set_option(sc_ctx* ctx, int option, long long value)
+{
+    if (!ctx) return SC_ERR_INVALID;
+    switch (option) {
+    case SC_OPT_TIME_FIELD: ctx->time_field = value != 0; return SC_OK;
+    case SC_OPT_NODES_PER_SPLIT:
+        if (value != 0 && (value < sc::kTile || value % sc::kTile))
+            return fail(ctx, SC_ERR_INVALID, "nodes per split must be a positive multiple of %d", sc::kTile);
+        ctx->nodes_per_split = value;
+        return SC_OK;
+    case SC_OPT_FLUSH_NODES:
+        if (value < sc::kTile || value % sc::kTile)
+            return fail(ctx, SC_ERR_INVALID, "flush length must be a positive multiple of %d", sc::kTile);
+        ctx->flush_nodes = value;
+        return SC_OK;
+    case SC_OPT_WORKSPACE_CAP:
+        if (value < (1 << 20)) return fail(ctx, SC_ERR_INVALID, "workspace cap below 1 MiB");
+        ctx->ws_cap = (size_t)value;
+        return SC_OK;
+    default: return fail(ctx, SC_ERR_INVALID, "unknown option %d", option);
+    }
+}
+
+}  // extern "C"

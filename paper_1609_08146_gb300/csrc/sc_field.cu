@@ -1,0 +1,682 @@
+// sc_field.cu -- FP32 field-sum kernels of libsc (the hot path).
+//
+// Computes, for every observation point r' and frequency omega_n, the
+// quadrature of Sec. II Eq. 11 (physical-optics Stratton-Chu integrals after
+// Stokes' theorem) over a node table of the paraboloid of Eq. 21.  Per node j
+// the table holds P_j, |P_j|, the aberration W_j, J_j = (N x B~) w_j / (2 pi)
+// and rho_j = (N . E~) w_j / (2 pi), where N = (-x/2f, -y/2f, 1) is the
+// un-normalised normal (n dS = N r dr dtheta) and w_j the quadrature weight
+// times r.  With R = |P - r'|, R^ = (P - r')/R and the phase
+//     Phi = R - (z + 2f) + W = (|r'|^2 - 2 P.r') / (R + |P|) + W
+// (|P| = z + 2f on the paraboloid, so the large distances cancel exactly --
+// the phase-cancellation analysis of Sec. III.C.1, Eqs. 20-21), the incident
+// phase e^{-ik(z+2f)} e^{ikW} times g = e^{ikR}/(4 pi R) is ph/(4 pi R) with
+// ph = e^{ik Phi}, and the summand of Eq. 11 becomes
+//     E += U q + V z,   B += Wv z,
+//     q = ik ph,  z = (ik - 1/R) ph,
+//     U = J/R,  V = rho R^/R,  Wv = U x R^.
+// That is 26 FP32 pipe operations per (point, node, omega): 4 for the phasor
+// recurrence ph <- ph e^{i dk Phi} (uniform omega grid: one complex rotation
+// per step instead of a sincos), 2 for q, 2 for z, 12 for E, 6 for B.
+// Boundary (rim) nodes carry U = 0 and rho = (J . m^) dl / (2 pi); their E sum
+// is multiplied by i/k_n in the epilogue, which reproduces the line integral
+// -(2/ik) O grad g [n x (n x B_inc)] . dl of Eq. 11.
+//
+// Kernel structure (sm_103a):
+//   * node tiles of 32 nodes (1280 B) are staged into shared memory with 1-D
+//     bulk copies (cp.async.bulk + mbarrier, double buffered, bounded waits);
+//   * phase 1: one thread per (point, node) pair computes the pair geometry,
+//     the 12 coefficients, the rotation e^{i dk Phi} and the seed phasor of
+//     every omega group, into a shared-memory pair table (double buffered);
+//   * phase 2: thread (point, group) owns 8 consecutive omegas of one point
+//     and runs the 26-op inner loop over the tile's nodes, accumulators in
+//     registers (12 per omega);
+//   * each CTA sums one split of the node range.  Every flush_tiles tiles
+//     (1024 nodes by default) the FP32 register sums are folded into a
+//     compensated float-float (hi, lo) partial in the workspace (TwoSum on
+//     the FP32 pipe) and restarted, so no FP32 running sum grows long; the
+//     reduce kernel adds the splits' partials in FP64 in a fixed order, so
+//     the result is deterministic.  Splits exist for load balance only.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "sc_internal.h"
+
+namespace sc {
+
+namespace {
+
+constexpr int kB = 8;                 // omegas per thread in the grouped kernel
+constexpr unsigned kSpinLimit = 1u << 26;       // bounded mbarrier waits: polls
+constexpr uint64_t kWaitNs = 1000000000ull;     // ... and wall time (1 s)
+
+// ------------------------------------------------------------------------
+// mbarrier / bulk-copy helpers (inline PTX)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on phase `parity`: gives up after about one second of wall
+// time (or kSpinLimit polls) and returns false, so a copy that never lands
+// turns into an error flag instead of a hung kernel.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity)
+{
+    const uint32_t addr = smem_u32(bar);
+    uint64_t t0 = 0;
+    for (unsigned it = 0; it < kSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+        const uint64_t now = global_ns();
+        if (it == 0) t0 = now;
+        else if (now - t0 > kWaitNs) return false;
+    }
+    return false;
+}
+
+// ------------------------------------------------------------------------
+// e^{i pi x} with x = 2 omega Phi, omega given as a float-float pair: the
+// product keeps its rounding residual, and x is reduced by the nearest even
+// integer n (e^{i pi x} has period 2) to r in [-1, 1] half-turns before
+// sincospif; xh - n is exact (Sterbenz) since |xh - n| <= 1.
+
+__device__ __forceinline__ float2 phasor_2wphi(float w_hi, float w_lo, float phi)
+{
+    const float a = 2.0f * w_hi;
+    const float xh = a * phi;
+    const float xl = fmaf(a, phi, -xh) + 2.0f * w_lo * phi;
+    const float n = 2.0f * rintf(0.5f * xh);
+    const float r = (xh - n) + xl;
+    float s, c;
+    sincospif(r, &s, &c);
+    return make_float2(c, s);
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// Pair geometry and coefficients from a staged tile (field f of node j at
+// nb[f * 32 + j]) and a point (x, y, z, |r'|^2).  co[0..8] = U, V, Wv;
+// co[9] = 1/R; returns Phi.
+__device__ __forceinline__ float pair_coefs(const float* nb, int j, float4 pt, float co[10])
+{
+    const float px = nb[F_PX * kTile + j], py = nb[F_PY * kTile + j], pz = nb[F_PZ * kTile + j];
+    const float pn = nb[F_PN * kTile + j], wo = nb[F_W * kTile + j];
+    const float jx = nb[F_JX * kTile + j], jy = nb[F_JY * kTile + j], jz = nb[F_JZ * kTile + j];
+    const float rho = nb[F_RHO * kTile + j];
+    const float dx = px - pt.x, dy = py - pt.y, dz = pz - pt.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float ir = rsqrtf(r2);
+    const float R = r2 * ir;
+    // |r'|^2 - 2 P.r'  (= R^2 - |P|^2 without the cancellation)
+    const float D = fmaf(-2.0f * pt.x, px, fmaf(-2.0f * pt.y, py, fmaf(-2.0f * pt.z, pz, pt.w)));
+    const float phi = __fdividef(D, R + pn) + wo;
+    const float rx = dx * ir, ry = dy * ir, rz = dz * ir;
+    const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
+    const float a = rho * ir;
+    co[0] = ux; co[1] = uy; co[2] = uz;
+    co[3] = a * rx; co[4] = a * ry; co[5] = a * rz;
+    co[6] = fmaf(uy, rz, -uz * ry);
+    co[7] = fmaf(uz, rx, -ux * rz);
+    co[8] = fmaf(ux, ry, -uy * rx);
+    co[9] = ir;
+    return phi;
+}
+
+// One (point, node, omega) evaluation: 26 FP32 pipe ops with the rotation.
+struct Acc12 {
+    float v[kAcc];
+};
+
+__device__ __forceinline__ void eval_one(Acc12& a, const float* co, float k, float2 ph)
+{
+    const float qr = -k * ph.y, qi = k * ph.x;              // q = ik ph
+    const float zr = fmaf(-co[9], ph.x, qr);                // z = q - ph/R
+    const float zi = fmaf(-co[9], ph.y, qi);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        a.v[2 * c] = fmaf(co[c], qr, fmaf(co[3 + c], zr, a.v[2 * c]));
+        a.v[2 * c + 1] = fmaf(co[c], qi, fmaf(co[3 + c], zi, a.v[2 * c + 1]));
+        a.v[6 + 2 * c] = fmaf(co[6 + c], zr, a.v[6 + 2 * c]);
+        a.v[6 + 2 * c + 1] = fmaf(co[6 + c], zi, a.v[6 + 2 * c + 1]);
+    }
+}
+
+// Fold one thread's FP32 sums for omegas [n0, n0 + nb) into its compensated
+// partials: (hi, lo) <- (hi, lo) + acc by TwoSum, or a plain store on the
+// first fold.  Each (split, point, omega) entry belongs to exactly one thread.
+template <int NB>
+__device__ __forceinline__ void fold(float2* dst, Acc12* acc, int nb, bool first)
+{
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        if (j < nb) {
+            float4* d4 = reinterpret_cast<float4*>(dst + (size_t)j * kAcc);
+#pragma unroll
+            for (int c = 0; c < kAcc / 2; ++c) {
+                const float a0 = acc[j].v[2 * c], a1 = acc[j].v[2 * c + 1];
+                if (first) {
+                    d4[c] = make_float4(a0, 0.f, a1, 0.f);
+                } else {
+                    const float4 h = d4[c];
+                    const float s0 = h.x + a0, b0 = s0 - h.x;
+                    const float e0 = (h.x - (s0 - b0)) + (a0 - b0);
+                    const float s1 = h.z + a1, b1 = s1 - h.z;
+                    const float e1 = (h.z - (s1 - b1)) + (a1 - b1);
+                    d4[c] = make_float4(s0, h.y + e0, s1, h.w + e1);
+                }
+                // keep the loads of the partials from being hoisted together
+                asm volatile("" ::: "memory");
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kAcc; ++c) acc[j].v[c] = 0.f;
+    }
+}
+
+// Split -> node tile range.
+__device__ __forceinline__ void split_range(const FieldLaunch& p, int split, int& t0, int& t1)
+{
+    if (split < p.n_splits) {
+        t0 = split * p.tiles_per_split;
+        t1 = min(t0 + p.tiles_per_split, p.n_surf_tiles);
+    } else {
+        t0 = p.n_surf_tiles;
+        t1 = p.n_surf_tiles + p.n_rim_tiles;
+    }
+}
+
+__device__ __forceinline__ void load_point(const double* pts, int n_pts, int p, float4& out)
+{
+    if (p < n_pts) {
+        const double x = pts[3 * p], y = pts[3 * p + 1], z = pts[3 * p + 2];
+        out = make_float4((float)x, (float)y, (float)z, (float)(x * x + y * y + z * z));
+    } else {
+        out = make_float4(0.f, 0.f, 0.f, 0.f);  // padding lane: computed, never stored
+    }
+}
+
+// ------------------------------------------------------------------------
+// Grouped kernel: G = ceil(n_omega / 8) >= 2 omega groups per point.
+// TPP threads per point (power of two >= G, <= 256), PPC points per CTA.
+
+template <int TPP>
+struct Grouped {
+    static constexpr int PPC = (256 / TPP) < 8 ? (256 / TPP) : 8;
+    static constexpr int NT = PPC * TPP;
+    static constexpr int NPAIR = PPC * kTile;
+    static constexpr int NSEED = (TPP + 15) / 16;  // reseed points (every 16 groups)
+    // shared layout (bytes): node tiles | coefs | seeds | points | reseed omegas | mbarriers
+    static constexpr size_t OFF_NODE = 0;
+    static constexpr size_t OFF_COEF = OFF_NODE + 2 * kTileBytes;
+    static constexpr size_t COEF_BYTES = (size_t)NPAIR * 12 * 4;
+    static constexpr size_t OFF_SEED = OFF_COEF + 2 * COEF_BYTES;
+    static constexpr size_t SEED_BYTES = (size_t)NPAIR * TPP * 8;
+    static constexpr size_t OFF_PTS = OFF_SEED + 2 * SEED_BYTES;
+    static constexpr size_t OFF_OMS = OFF_PTS + PPC * 16;
+    static constexpr size_t OFF_BAR = (OFF_OMS + NSEED * 8 + 15) / 16 * 16;
+    static constexpr size_t SMEM = OFF_BAR + 16;
+};
+
+template <int TPP>
+__global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(FieldLaunch p)
+{
+    using L = Grouped<TPP>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float* nodebuf = reinterpret_cast<float*>(smem + L::OFF_NODE);
+    float* coefbuf = reinterpret_cast<float*>(smem + L::OFF_COEF);
+    float2* seedbuf = reinterpret_cast<float2*>(smem + L::OFF_SEED);
+    float4* spts = reinterpret_cast<float4*>(smem + L::OFF_PTS);
+    float2* soms = reinterpret_cast<float2*>(smem + L::OFF_OMS);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
+
+    const int tid = threadIdx.x;
+    const int pl = tid / TPP;   // local point
+    const int g = tid % TPP;    // omega group
+    const int p0 = blockIdx.x * L::PPC;
+    const int split = blockIdx.y;
+    int t0, t1;
+    split_range(p, split, t0, t1);
+    const int G = (p.n_omega + kB - 1) / kB;
+    const double om0 = (double)p.om_hi0 + (double)p.om_lo0;
+    const double dom = (double)p.dom_hi + (double)p.dom_lo;
+
+    if (tid < L::PPC) load_point(p.pts, p.n_pts, p0 + tid, spts[tid]);
+    if (tid < L::NSEED) {
+        const double w = om0 + (double)(tid * 16 * kB) * dom;
+        const float hi = (float)w;
+        soms[tid] = make_float2(hi, (float)(w - (double)hi));
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    // this thread's wavenumbers
+    float kv[kB];
+#pragma unroll
+    for (int j = 0; j < kB; ++j) kv[j] = (float)(6.283185307179586 * (om0 + (double)(g * kB + j) * dom));
+    // rotation steps as float-float
+    const float d1h = p.dom_hi, d1l = p.dom_lo;
+    const double domB = dom * kB;
+    const float dBh = (float)domB, dBl = (float)(domB - (double)(float)domB);
+    __syncthreads();
+
+    unsigned issued[2] = {0, 0}, waited[2] = {0, 0};
+    bool timed_out = false;
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            if (t0 + s < t1) {
+                mbar_expect_tx(&bar[s], kTileBytes);
+                bulk_g2s(nodebuf + s * kTileFloats, p.nodes + (size_t)(t0 + s) * kTileFloats,
+                         kTileBytes, &bar[s]);
+                issued[s]++;
+            }
+        }
+    }
+
+    Acc12 acc[kB];
+#pragma unroll
+    for (int j = 0; j < kB; ++j)
+#pragma unroll
+        for (int c = 0; c < kAcc; ++c) acc[j].v[c] = 0.f;
+
+    // phase 1: tile t (index it = t - t0) -> pair buffer pb
+    auto phase1 = [&](int it, int pb) {
+        const int nbuf = it & 1;
+        const unsigned par = (unsigned)((it >> 1) & 1);
+        if (!mbar_wait(&bar[nbuf], par)) timed_out = true;
+        if (tid == 0) waited[nbuf]++;
+        const float* nb = nodebuf + nbuf * kTileFloats;
+        float* cb = coefbuf + (size_t)pb * L::NPAIR * 12;
+        float2* sb = seedbuf + (size_t)pb * L::NPAIR * TPP;
+        for (int q = tid; q < L::NPAIR; q += L::NT) {
+            const int pq = q / kTile, j = q % kTile;
+            float co[10];
+            const float phi = pair_coefs(nb, j, spts[pq], co);
+            const float2 rot = phasor_2wphi(d1h, d1l, phi);
+            float4* c4 = reinterpret_cast<float4*>(cb + (size_t)q * 12);
+            c4[0] = make_float4(co[0], co[1], co[2], co[3]);
+            c4[1] = make_float4(co[4], co[5], co[6], co[7]);
+            c4[2] = make_float4(co[8], co[9], rot.x, rot.y);
+            const float2 rotB = phasor_2wphi(dBh, dBl, phi);
+            float2 s = make_float2(1.f, 0.f);
+            for (int gg = 0; gg < G; ++gg) {
+                if ((gg & 15) == 0) {
+                    const float2 w = soms[gg >> 4];
+                    s = phasor_2wphi(w.x, w.y, phi);
+                } else {
+                    s = cmul(s, rotB);
+                }
+                sb[(size_t)q * TPP + gg] = s;
+            }
+        }
+    };
+
+    // phase 2: accumulate the tile in pair buffer pb
+    auto phase2 = [&](int pb) {
+        const float* cb = coefbuf + (size_t)pb * L::NPAIR * 12 + (size_t)pl * kTile * 12;
+        const float2* sb = seedbuf + (size_t)pb * L::NPAIR * TPP + (size_t)pl * kTile * TPP + g;
+#pragma unroll 1
+        for (int j = 0; j < kTile; ++j) {
+            const float4* c4 = reinterpret_cast<const float4*>(cb + j * 12);
+            const float4 a0 = c4[0], a1 = c4[1], a2 = c4[2];
+            const float co[10] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y};
+            const float2 rot = make_float2(a2.z, a2.w);
+            float2 ph = sb[j * TPP];
+#pragma unroll
+            for (int jj = 0; jj < kB; ++jj) {
+                eval_one(acc[jj], co, kv[jj], ph);
+                if (jj + 1 < kB) ph = cmul(ph, rot);
+            }
+        }
+    };
+
+    const int nt = t1 - t0;
+    // this thread's partials: omegas g*8 .. g*8+7 of point p0 + pl
+    auto fold_now = [&](bool first) {
+        if (p0 + pl < p.n_pts && g < G) {
+            float2* dst = p.ws + (((size_t)split * p.n_pts + (p0 + pl)) * (size_t)p.n_omega +
+                                  (size_t)g * kB) * kAcc;
+            fold<kB>(dst, acc, min(kB, p.n_omega - g * kB), first);
+        }
+    };
+    if (nt > 0) {
+        phase1(0, 0);
+        __syncthreads();
+        if (tid == 0 && t0 + 2 < t1) {
+            fence_proxy_async();
+            mbar_expect_tx(&bar[0], kTileBytes);
+            bulk_g2s(nodebuf, p.nodes + (size_t)(t0 + 2) * kTileFloats, kTileBytes, &bar[0]);
+            issued[0]++;
+        }
+        for (int it = 0; it < nt; ++it) {
+            if (it + 1 < nt) phase1(it + 1, (it + 1) & 1);
+            phase2(it & 1);
+            if ((it + 1) % p.flush_tiles == 0 || it + 1 == nt) fold_now(it + 1 <= p.flush_tiles);
+            __syncthreads();
+            if (tid == 0 && it + 3 < nt) {
+                const int nbuf = (it + 1) & 1;
+                fence_proxy_async();
+                mbar_expect_tx(&bar[nbuf], kTileBytes);
+                bulk_g2s(nodebuf + nbuf * kTileFloats,
+                         p.nodes + (size_t)(t0 + it + 3) * kTileFloats, kTileBytes, &bar[nbuf]);
+                issued[nbuf]++;
+            }
+        }
+    }
+
+    if (timed_out) atomicOr(p.err, ERR_TIMEOUT);
+    // drain: never leave a bulk copy in flight into freed shared memory
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s)
+            while (waited[s] < issued[s]) {
+                if (!mbar_wait(&bar[s], waited[s] & 1)) { atomicOr(p.err, ERR_TIMEOUT); break; }
+                waited[s]++;
+            }
+    }
+
+    // a split without tiles (the rim slot when the rim term is off) still
+    // owns its partials: write zeros
+    if (nt == 0) fold_now(true);
+}
+
+// ------------------------------------------------------------------------
+// Direct kernel: n_omega <= 8 (a single group).  One thread per point computes
+// every pair itself; the CTA shares the staged node tiles.
+
+template <int NB>
+__global__ void __launch_bounds__(256, 1) field_direct_kernel(FieldLaunch p)
+{
+    __shared__ __align__(128) float nodebuf[2 * kTileFloats];
+    __shared__ __align__(8) uint64_t bar[2];
+    const int tid = threadIdx.x;
+    const int pt = blockIdx.x * 256 + tid;
+    const int split = blockIdx.y;
+    int t0, t1;
+    split_range(p, split, t0, t1);
+    const double om0 = (double)p.om_hi0 + (double)p.om_lo0;
+    const double dom = (double)p.dom_hi + (double)p.dom_lo;
+    float4 P;
+    load_point(p.pts, p.n_pts, pt, P);
+    float kv[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) kv[j] = (float)(6.283185307179586 * (om0 + (double)j * dom));
+    const float w0h = p.om_hi0, w0l = p.om_lo0, d1h = p.dom_hi, d1l = p.dom_lo;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    unsigned issued[2] = {0, 0}, waited[2] = {0, 0};
+    bool timed_out = false;
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s)
+            if (t0 + s < t1) {
+                mbar_expect_tx(&bar[s], kTileBytes);
+                bulk_g2s(nodebuf + s * kTileFloats, p.nodes + (size_t)(t0 + s) * kTileFloats,
+                         kTileBytes, &bar[s]);
+                issued[s]++;
+            }
+    }
+    Acc12 acc[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+#pragma unroll
+        for (int c = 0; c < kAcc; ++c) acc[j].v[c] = 0.f;
+
+    const int nt = t1 - t0;
+    const bool pt_ok = pt < p.n_pts;
+    const int nb_ok = min(NB, p.n_omega);
+    float2* dst = p.ws + ((size_t)split * p.n_pts + pt) * (size_t)p.n_omega * kAcc;
+    for (int it = 0; it < nt; ++it) {
+        const int nbuf = it & 1;
+        if (!mbar_wait(&bar[nbuf], (unsigned)((it >> 1) & 1))) timed_out = true;
+        if (tid == 0) waited[nbuf]++;
+        const float* nb = nodebuf + nbuf * kTileFloats;
+#pragma unroll 1
+        for (int j = 0; j < kTile; ++j) {
+            float co[10];
+            const float phi = pair_coefs(nb, j, P, co);
+            float2 ph = phasor_2wphi(w0h, w0l, phi);
+            float2 rot = make_float2(1.f, 0.f);
+            if (NB > 1) rot = phasor_2wphi(d1h, d1l, phi);
+#pragma unroll
+            for (int jj = 0; jj < NB; ++jj) {
+                eval_one(acc[jj], co, kv[jj], ph);
+                if (jj + 1 < NB) ph = cmul(ph, rot);
+            }
+        }
+        if (((it + 1) % p.flush_tiles == 0 || it + 1 == nt) && pt_ok)
+            fold<NB>(dst, acc, nb_ok, it + 1 <= p.flush_tiles);
+        __syncthreads();
+        if (tid == 0 && it + 2 < nt) {
+            fence_proxy_async();
+            mbar_expect_tx(&bar[nbuf], kTileBytes);
+            bulk_g2s(nodebuf + nbuf * kTileFloats, p.nodes + (size_t)(t0 + it + 2) * kTileFloats,
+                     kTileBytes, &bar[nbuf]);
+            issued[nbuf]++;
+        }
+    }
+    if (timed_out) atomicOr(p.err, ERR_TIMEOUT);
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s)
+            while (waited[s] < issued[s]) {
+                if (!mbar_wait(&bar[s], waited[s] & 1)) { atomicOr(p.err, ERR_TIMEOUT); break; }
+                waited[s]++;
+            }
+    }
+    if (nt == 0 && pt_ok) fold<NB>(dst, acc, nb_ok, true);
+}
+
+// ------------------------------------------------------------------------
+// FP64 cross-split reduction and epilogue.
+
+__global__ void reduce_kernel(ReduceLaunch r)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = (long long)r.n_pts * r.n_omega;
+    if (idx >= total) return;
+    const int pt = (int)(idx / r.n_omega), n = (int)(idx % r.n_omega);
+    double s[kAcc];
+#pragma unroll
+    for (int c = 0; c < kAcc; ++c) s[c] = 0.0;
+    const size_t stride = (size_t)r.n_pts * r.n_omega * kAcc;
+    const float2* base = r.ws + ((size_t)pt * r.n_omega + n) * kAcc;
+    for (int sp = 0; sp < r.n_splits; ++sp) {
+        const float4* v = reinterpret_cast<const float4*>(base + sp * stride);
+#pragma unroll
+        for (int c = 0; c < kAcc / 2; ++c) {
+            const float4 h = v[c];
+            s[2 * c] += (double)h.x + (double)h.y;
+            s[2 * c + 1] += (double)h.z + (double)h.w;
+        }
+    }
+    // rim slot: its E sum carries the factor i/k of the line integral
+    const float4* v = reinterpret_cast<const float4*>(base + (size_t)r.n_splits * stride);
+    double rim[6];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float4 h = v[c];
+        rim[2 * c] = (double)h.x + (double)h.y;
+        rim[2 * c + 1] = (double)h.z + (double)h.w;
+    }
+    const double ik = 1.0 / r.kval[n];
+    const double ar = r.amp[2 * n], ai = r.amp[2 * n + 1];
+    float2* E = r.E + (size_t)n * r.out_pt_stride_omega + (size_t)pt * 3;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        // S + (i/k) rim
+        const double er = s[2 * c] - ik * rim[2 * c + 1];
+        const double ei = s[2 * c + 1] + ik * rim[2 * c];
+        E[c] = make_float2((float)(ar * er - ai * ei), (float)(ar * ei + ai * er));
+    }
+    if (r.B) {
+        float2* B = r.B + (size_t)n * r.out_pt_stride_omega + (size_t)pt * 3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double br = s[6 + 2 * c], bi = s[6 + 2 * c + 1];
+            B[c] = make_float2((float)(ar * br - ai * bi), (float)(ar * bi + ai * br));
+        }
+    }
+}
+
+template <int TPP>
+int launch_grouped(const FieldLaunch& p, cudaStream_t s)
+{
+    using L = Grouped<TPP>;
+    auto kern = field_grouped_kernel<TPP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)L::SMEM);
+    if (e != cudaSuccess) return -(int)e;
+    dim3 grid((p.n_pts + L::PPC - 1) / L::PPC, p.n_splits + 1);
+    kern<<<grid, L::NT, L::SMEM, s>>>(p);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? 1 : -(int)e;
+}
+
+template <int NB>
+int launch_direct(const FieldLaunch& p, cudaStream_t s)
+{
+    dim3 grid((p.n_pts + 255) / 256, p.n_splits + 1);
+    field_direct_kernel<NB><<<grid, 256, 0, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? 1 : -(int)e;
+}
+
+}  // namespace
+
+int launch_field_f32(const FieldLaunch& p, cudaStream_t s)
+{
+    if (p.n_omega <= 8) {
+        switch (p.n_omega) {
+        case 1: return launch_direct<1>(p, s);
+        case 2: return launch_direct<2>(p, s);
+        case 3:
+        case 4: return launch_direct<4>(p, s);
+        default: return launch_direct<8>(p, s);
+        }
+    }
+    const int G = (p.n_omega + kB - 1) / kB;
+    if (G <= 2) return launch_grouped<2>(p, s);
+    if (G <= 4) return launch_grouped<4>(p, s);
+    if (G <= 8) return launch_grouped<8>(p, s);
+    if (G <= 16) return launch_grouped<16>(p, s);
+    if (G <= 32) return launch_grouped<32>(p, s);
+    if (G <= 64) return launch_grouped<64>(p, s);
+    if (G <= 128) return launch_grouped<128>(p, s);
+    if (G <= 256) return launch_grouped<256>(p, s);
+    return -(int)cudaErrorInvalidValue;
+}
+
+namespace {
+
+template <typename K>
+int resident(K kern, int threads, size_t smem, int device)
+{
+    int per_sm = 0, sms = 0;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess)
+        per_sm = 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) sms = 1;
+    cudaGetLastError();
+    return std::max(1, per_sm) * std::max(1, sms);
+}
+
+template <int TPP>
+void grouped_shape(int device, int* ppc, int* slots)
+{
+    using L = Grouped<TPP>;
+    *ppc = L::PPC;
+    *slots = resident(field_grouped_kernel<TPP>, L::NT, L::SMEM, device);
+}
+
+}  // namespace
+
+void field_shape(int n_omega, int device, int* ppc, int* slots)
+{
+    if (n_omega <= 8) {
+        *ppc = 256;
+        switch (n_omega) {
+        case 1: *slots = resident(field_direct_kernel<1>, 256, 0, device); return;
+        case 2: *slots = resident(field_direct_kernel<2>, 256, 0, device); return;
+        case 3:
+        case 4: *slots = resident(field_direct_kernel<4>, 256, 0, device); return;
+        default: *slots = resident(field_direct_kernel<8>, 256, 0, device); return;
+        }
+    }
+    const int G = (n_omega + kB - 1) / kB;
+    if (G <= 2) return grouped_shape<2>(device, ppc, slots);
+    if (G <= 4) return grouped_shape<4>(device, ppc, slots);
+    if (G <= 8) return grouped_shape<8>(device, ppc, slots);
+    if (G <= 16) return grouped_shape<16>(device, ppc, slots);
+    if (G <= 32) return grouped_shape<32>(device, ppc, slots);
+    if (G <= 64) return grouped_shape<64>(device, ppc, slots);
+    if (G <= 128) return grouped_shape<128>(device, ppc, slots);
+    return grouped_shape<256>(device, ppc, slots);
+}
+
+int launch_reduce_f32(const ReduceLaunch& r, cudaStream_t s)
+{
+    const long long total = (long long)r.n_pts * r.n_omega;
+    const int nb = (int)((total + 255) / 256);
+    reduce_kernel<<<nb, 256, 0, s>>>(r);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? 1 : -(int)e;
+}
+
+}  // namespace sc

@@ -1,0 +1,104 @@
+// Internal interface between the host side of libsc (handles, FP64 node
+// tables, scheduling) and its CUDA kernels.  Not part of the C-ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sc {
+
+// Node tables are stored in tiles of kTile nodes; each tile holds kFields
+// fields of kTile floats (structure of arrays inside the tile), so one tile is
+// one contiguous 16-byte-aligned block that a single bulk copy stages into
+// shared memory.
+constexpr int kTile = 32;
+constexpr int kFields = 10;
+constexpr int kTileFloats = kTile * kFields;          // 320
+constexpr int kTileBytes = kTileFloats * 4;           // 1280
+enum NodeField {
+    F_PX = 0, F_PY, F_PZ,  // node position P (focus at the origin)
+    F_PN,                  // |P| = z + 2f on the paraboloid
+    F_W,                   // optical path difference W at the node
+    F_JX, F_JY, F_JZ,      // (N x B~) w / (2 pi): surface current times weight
+    F_RHO,                 // (N . E~) w / (2 pi), or q / (2 pi) on a rim node
+    F_PAD
+};
+
+// FP64 table for the plain FP64 path: one node per record.
+struct Node64 {
+    double px, py, pz, pn, w, jx, jy, jz, rho, pad;
+};
+
+// Error bits raised by kernels.
+enum : int { ERR_TIMEOUT = 1, ERR_NEAR_SURFACE = 2, ERR_NONFINITE = 4 };
+
+// Accumulator layout of one (point, omega) partial sum: E (re, im) x 3 then
+// B (re, im) x 3.
+constexpr int kAcc = 12;
+
+struct FieldLaunch {
+    const float* nodes;     // tiled table: surface tiles then rim tiles
+    int n_surf_tiles;
+    int n_rim_tiles;
+    int tiles_per_split;    // surface tiles per split
+    int n_splits;           // surface splits; split index n_splits = the rim
+    int flush_tiles;        // tiles summed in FP32 before each compensated fold
+    const double* pts;      // [n_pts][3] (this chunk)
+    int n_pts;
+    int n_omega;            // omegas in this chunk
+    float om_hi0, om_lo0;   // first omega of the chunk as a float-float pair
+    float dom_hi, dom_lo;   // grid step as a float-float pair
+    float2* ws;             // compensated partials (hi, lo) [n_splits + 1][n_pts][n_omega][kAcc]
+    int* err;               // device error word
+};
+
+// FP32 field sum.  Returns the number of kernels launched (>= 1) or a
+// negative cudaError_t.
+int launch_field_f32(const FieldLaunch& p, cudaStream_t s);
+
+// Launch shape of the FP32 field sum for n_omega omegas in one launch:
+// observation points per CTA and concurrently resident CTAs on the device.
+void field_shape(int n_omega, int device, int* points_per_cta, int* resident_ctas);
+
+// FP64 cross-split reduction and epilogue: E = a_n (S_E + (i/k_n) S_rim),
+// B = a_n S_B, written as float2 into out[n_omega_total][n_pts_total][3]
+// at (omega offset, point offset).
+struct ReduceLaunch {
+    const float2* ws;
+    int n_splits;           // surface splits (the rim slot follows)
+    int n_pts, n_omega;
+    const double* amp;      // [n_omega][2] of this chunk
+    const double* kval;     // [n_omega] k_n of this chunk
+    float2* E;              // output base (already offset to the chunk)
+    float2* B;              // nullable
+    long long out_pt_stride_omega;  // n_pts_total * 3
+};
+int launch_reduce_f32(const ReduceLaunch& p, cudaStream_t s);
+
+// Plain FP64 path: direct sincos per (point, node, omega).
+struct Field64Launch {
+    const Node64* surf; int n_surf;
+    const Node64* rim;  int n_rim;
+    const double* pts;  int n_pts;
+    const double* kval; int n_omega;     // k_n per omega
+    const double* amp;                   // [n_omega][2]
+    double2* E; double2* B;              // [n_omega][n_pts][3]
+};
+int launch_field_f64(const Field64Launch& p, cudaStream_t s);
+
+// Inverse transform: out[t][v] = 2 dk Re sum_n F[n][v] e^{-i k_n t_m}.
+struct IdftLaunch {
+    const void* F;          // [n_omega][n_vals] complex (float2 or double2)
+    int f64;                // element type of F
+    int n_omega;
+    long long n_vals;
+    const double* kval;     // [n_omega]
+    const double* t;        // [n_t]
+    int n_t;
+    double dk;
+    float* out;             // [n_t][n_vals]
+    float2* phasor;         // scratch [n_omega][n_t]
+};
+int launch_idft(const IdftLaunch& p, cudaStream_t s);
+
+}  // namespace sc

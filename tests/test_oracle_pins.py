@@ -79,7 +79,8 @@ def test_zernike_noll_table():
          math.pi * 4.0 * 2 ** (-1 / 4) * math.gamma(1 + 1 / 4)),
         (dict(profile="supergauss", sg_order=4, pol="azimuthal", w0=2.0),
          math.pi * 4.0 * 2 ** (-2 / 4) * math.gamma(1 + 2 / 4) / 2),
-        (dict(profile="tophat", pol="linear", w0=1.0, r_norm=5.0), math.pi * 25.0),
+        (dict(profile="tophat", pol="linear", w0=5.0), math.pi * 25.0),
+        (dict(profile="tophat", pol="radial", w0=5.0), math.pi * 25.0 / 2),
     ],
 )
 def test_beam_power_closed_forms(beam, closed):
@@ -107,7 +108,7 @@ def test_paraboloid_focus_linear_tophat(f, a, omega):
     """
     k = K0 * omega
     m = dict(f=f, r_max=a, n_r=160, n_theta=64, rim=1)
-    b = dict(profile="tophat", pol="linear", r_norm=1.01 * a)
+    b = dict(profile="tophat", pol="linear", w0=1.01 * a)
     E, B = _focus(m, b, omega)
     Ra = f + a * a / (4 * f)
     Ex = 2 * (1j * k * f + 1) * (1 - f / Ra) - (1 - f * f / Ra ** 2) - (a * a / (2 * Ra ** 2)) * (
@@ -124,7 +125,7 @@ def test_paraboloid_focus_without_rim_term():
     # dropping the line integral removes exactly its closed-form share
     f, a, k = 20.0, 30.0, K0
     m = dict(f=f, r_max=a, n_r=160, n_theta=64, rim=0)
-    b = dict(profile="tophat", pol="linear", r_norm=1.01 * a)
+    b = dict(profile="tophat", pol="linear", w0=1.01 * a)
     E, _ = _focus(m, b, 1.0)
     Ra = f + a * a / (4 * f)
     Ex = 2 * (1j * k * f + 1) * (1 - f / Ra) - (1 - f * f / Ra ** 2)
@@ -135,10 +136,11 @@ def test_paraboloid_focus_radial_tophat():
     """Radial polarisation (rho/w0) rho_hat: only E_z survives at the focus,
     E_z = (4f/w0)[2ikf(L - 1 + f/R_a) + L - 2 + 3f/R_a - f^2/R_a^2]
           - (1 + i/(kR_a)) (R_a - 2f) a^2 / (R_a^2 w0),   L = ln(R_a/f)."""
-    f, a, w0, om = 20.0, 30.0, 7.0, 1.3
+    f, a, om = 20.0, 30.0, 1.3
+    w0 = 1.01 * a
     k = K0 * om
     m = dict(f=f, r_max=a, n_r=160, n_theta=64, rim=1)
-    b = dict(profile="tophat", pol="radial", r_norm=1.01 * a, w0=w0)
+    b = dict(profile="tophat", pol="radial", w0=w0)
     E, B = _focus(m, b, om)
     Ra = f + a * a / (4 * f)
     L = math.log(Ra / f)
@@ -152,10 +154,11 @@ def test_paraboloid_focus_radial_tophat():
 def test_paraboloid_focus_azimuthal_tophat():
     """Azimuthal polarisation: only B_z survives at the focus,
     B_z = -(8f^2/w0)[ik(L - 1 + f/R_a) - (1 - f/R_a)/f + (1 - f^2/R_a^2)/(2f)]."""
-    f, a, w0, om = 20.0, 30.0, 7.0, 1.3
+    f, a, om = 20.0, 30.0, 1.3
+    w0 = 1.01 * a
     k = K0 * om
     m = dict(f=f, r_max=a, n_r=160, n_theta=64, rim=1)
-    b = dict(profile="tophat", pol="azimuthal", r_norm=1.01 * a, w0=w0)
+    b = dict(profile="tophat", pol="azimuthal", w0=w0)
     E, B = _focus(m, b, om)
     Ra = f + a * a / (4 * f)
     L = math.log(Ra / f)
@@ -174,7 +177,7 @@ def test_flat_mirror_is_image_source():
     a, d, om = 7.0, 3.0, 1.0
     k = K0 * om
     m = dict(surface="flat", z0=0.0, r_max=a, n_r=200, n_theta=64, rim=1)
-    b = dict(profile="tophat", pol="linear", r_norm=1.01 * a)
+    b = dict(profile="tophat", pol="linear", w0=1.01 * a)
     E, B = oracle.field(m, b, [om], [[0.0, 0.0, d]])
     Ra = math.hypot(a, d)
     Ex = np.exp(1j * k * Ra) - np.exp(1j * k * d) + (1j / (2 * k)) * (1j * k - 1 / Ra) * np.exp(
@@ -240,7 +243,7 @@ def test_ampere_and_divergence_for_plane_wave():
     f, om = 8.0, 1.1
     k = K0 * om
     m = dict(f=f, r_max=10.0, n_r=64, n_theta=64, rim=1)
-    b = dict(profile="tophat", pol="linear", r_norm=20.0)
+    b = dict(profile="tophat", pol="linear", w0=20.0)
     E, B, cE, cB, dE = _curl(m, b, om, [0.23, 0.11, -0.19], 2e-3)
     assert np.linalg.norm(cB + 1j * k * E) / np.linalg.norm(k * E) < 1e-7
     assert abs(dE) / (k * np.linalg.norm(E)) < 1e-7
@@ -251,7 +254,7 @@ def test_stokes_form_equals_double_gradient_form_for_plane_wave():
     gradient, Appendix-A dyadic, no line term) for a Maxwell incident field."""
     f, om = 8.0, 0.9
     m = dict(f=f, r_max=12.0, n_r=96, n_theta=96, rim=1)
-    b = dict(profile="tophat", pol="linear", r_norm=20.0, pol_angle=0.4)
+    b = dict(profile="tophat", pol="linear", w0=20.0, pol_angle=0.4)
     rng = np.random.default_rng(7)
     pts = rng.uniform(-1.5, 1.5, size=(6, 3))
     E1, B1 = oracle.field(m, b, [om], pts, form="stokes")
