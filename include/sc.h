@@ -226,6 +226,37 @@ sc_status sc_time_domain(sc_ctx* ctx, sc_precision prec, const void* E_spec, con
                          const double* omegas, int n_omega, int n_points, const double* times,
                          int n_t, float* E_t, float* B_t);
 
+/*
+ * Allocation-free variant of sc_eval for the SC_FP32_COMP path.  The paper
+ * has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc while they evaluate -- code running inside a global-mode stream
+ * capture, services that hand all device memory to their own pools up front,
+ * or real-time loops that forbid allocation.  It allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine.  Its split
+ * partials live in a fixed 64 MiB static device array of the library
+ * (SC_STATIC_SCRATCH_BYTES), which every GPU that loads the library holds
+ * until the process exits.
+ *   Preconditions: the node table of (mirror, inc) is already resident in
+ *   ctx, i.e. sc_eval ran once for this pair (that call may allocate).
+ *   omega_n = omega0 + n * domega, n < n_omega (<= 2048), omega0 > 0.
+ *   amp_re_im   host, [n_omega][2], e.g. from sc_spectrum_eval.
+ *   points_xyz  device, [n_points][3] doubles.
+ *   E_out,B_out device, [n_omega][n_points][3] float2 pairs; B_out may be NULL.
+ * The scratch needed is 2 x 96 x n_points x n_omega bytes plus 24 x n_omega;
+ * larger requests are rejected with SC_ERR_INVALID and a message giving the
+ * limit.  The first call on a device looks up the array's device address
+ * (which may load the module): make that first call before any stream
+ * capture.  Every call shares the array and leaves its contents behind; each
+ * call writes every partial before reading it, so nothing needs clearing,
+ * but calls whose GPU work overlaps (other streams, other contexts on the
+ * same device) race on it.  Asynchronous on the context stream.
+ * Errors: SC_ERR_INVALID, SC_ERR_CUDA.
+ */
+#define SC_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
+sc_status sc_eval_fp32_static(sc_ctx* ctx, const sc_mirror_t* mirror, const sc_incident_t* inc,
+                              double omega0, double domega, int n_omega, const double* amp_re_im,
+                              const double* points_xyz, int n_points, void* E_out, void* B_out);
+
 /* ---------------------------------------------------------------------- */
 /* Counters (measurement)                                                  */
 

@@ -83,6 +83,8 @@ SIGNATURES = {
                                _VP, _VP, ctypes.POINTER(sc_eval_stats)]),
     "sc_time_domain": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _DP, ctypes.c_int, ctypes.c_int,
                                       _DP, ctypes.c_int, _VP, _VP]),
+    "sc_eval_fp32_static": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_int, _DP, _VP, ctypes.c_int, _VP, _VP]),
     "sc_get_counters": (ctypes.c_int, [_VP, ctypes.POINTER(sc_counters)]),
     "sc_reset_counters": (ctypes.c_int, [_VP]),
     "sc_set_option": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_longlong]),

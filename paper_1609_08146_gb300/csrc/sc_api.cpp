@@ -20,6 +20,7 @@
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
+static_assert(SC_STATIC_SCRATCH_BYTES == sc::kStaticScratchBytes, "scratch size mismatch");
 
 std::atomic<uint64_t> g_next_id{1};
 
@@ -916,6 +917,88 @@ sc_status sc_eval(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, co
         stats->launches = (int)(ctx->ctr.launches - launches_before);
         ctx->time_field = timing_before;
     }
+    return SC_OK;
+}
+
+sc_status sc_eval_fp32_static(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in,
+                              double omega0, double domega, int n_omega, const double* amp_re_im,
+                              const double* points_xyz, int n_points, void* E_out, void* B_out)
+{
+    // No device allocation on this path: the table must already be resident,
+    // a_n and k_n travel through the static scratch, and so do the partials.
+    constexpr int kMaxOmega = 2048;
+    if (!ctx) return SC_ERR_INVALID;
+    if (!m || !in || !amp_re_im || !points_xyz || !E_out || n_points < 1 || n_omega < 1)
+        return fail(ctx, SC_ERR_INVALID, "invalid argument");
+    if (n_omega > kMaxOmega)
+        return fail(ctx, SC_ERR_INVALID, "n_omega %d exceeds %d for the static-scratch path", n_omega,
+                    kMaxOmega);
+    if (!(omega0 > 0.0) || !(domega >= 0.0) || (n_omega > 1 && !(domega > 0.0)))
+        return fail(ctx, SC_ERR_INVALID, "omega grid must be positive and increasing");
+    const size_t header = (size_t)n_omega * 3 * sizeof(double);   // a_n (2) and k_n (1)
+    const size_t header_al = (header + 255) / 256 * 256;
+    const size_t ws_bytes = (size_t)2 * n_points * n_omega * sc::kAcc * sizeof(float2);
+    if (header_al + ws_bytes > sc::kStaticScratchBytes)
+        return fail(ctx, SC_ERR_INVALID,
+                    "request needs %zu bytes of static scratch; the limit is %zu (points x omegas "
+                    "<= %zu)", header_al + ws_bytes, sc::kStaticScratchBytes,
+                    (sc::kStaticScratchBytes - header_al) / (2 * sc::kAcc * sizeof(float2)));
+    Table* tab = nullptr;
+    for (auto& t : ctx->tables)
+        if (t.mid == m->id && t.iid == in->id) tab = &t;
+    if (!tab)
+        return fail(ctx, SC_ERR_INVALID,
+                    "node table not resident: run sc_eval once for this mirror and incident first");
+    void* scratch = nullptr;
+    cudaError_t e = sc::static_scratch(ctx->device, &scratch);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "static scratch address");
+    SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    double hdr[3 * kMaxOmega];
+    for (int i = 0; i < n_omega; ++i) {
+        hdr[2 * i] = amp_re_im[2 * i];
+        hdr[2 * i + 1] = amp_re_im[2 * i + 1];
+        hdr[2 * n_omega + i] = 2.0 * kPi * (omega0 + i * domega);
+    }
+    double* d_amp = (double*)scratch;
+    double* d_k = d_amp + 2 * (size_t)n_omega;
+    // pageable source: the call returns once the bytes are staged
+    SC_CUDA(cudaMemcpyAsync(d_amp, hdr, header, cudaMemcpyHostToDevice, ctx->stream),
+            "upload a_n, k_n");
+    float2* ws = (float2*)((unsigned char*)scratch + header_al);
+    sc::FieldLaunch f;
+    f.nodes = tab->d32;
+    f.n_surf_tiles = tab->n_surf_tiles;
+    f.n_rim_tiles = tab->n_rim_tiles;
+    f.tiles_per_split = tab->n_surf_tiles;  // one surface split and the rim slot
+    f.n_splits = 1;
+    f.flush_tiles = (int)std::max<long long>(1, ctx->flush_nodes / sc::kTile);
+    f.pts = points_xyz;
+    f.n_pts = n_points;
+    f.n_omega = n_omega;
+    f.om_hi0 = (float)omega0;
+    f.om_lo0 = (float)(omega0 - (double)f.om_hi0);
+    f.dom_hi = (float)domega;
+    f.dom_lo = (float)(domega - (double)f.dom_hi);
+    f.ws = ws;
+    f.err = ctx->d_err;
+    int r = sc::launch_field_f32(f, ctx->stream);
+    if (r < 0) return cuda_fail(ctx, (cudaError_t)(-r), "field kernel launch");
+    ctx->ctr.launches += r;
+    ctx->ctr.field_launches += 1;
+    sc::ReduceLaunch rl;
+    rl.ws = ws;
+    rl.n_splits = 1;
+    rl.n_pts = n_points;
+    rl.n_omega = n_omega;
+    rl.amp = d_amp;
+    rl.kval = d_k;
+    rl.out_pt_stride_omega = (long long)n_points * 3;
+    rl.E = (float2*)E_out;
+    rl.B = (float2*)B_out;
+    r = sc::launch_reduce_f32(rl, ctx->stream);
+    if (r < 0) return cuda_fail(ctx, (cudaError_t)(-r), "reduce kernel launch");
+    ctx->ctr.launches += r;
+    ctx->ctr.evals += (double)n_points * tab->n_surf * n_omega;
     return SC_OK;
 }
 

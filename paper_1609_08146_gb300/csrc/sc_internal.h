@@ -101,4 +101,10 @@ struct IdftLaunch {
 };
 int launch_idft(const IdftLaunch& p, cudaStream_t s);
 
+// Fixed device scratch of the allocation-free entry point: 64 MiB of static
+// device memory per GPU.  static_scratch() returns its device address on
+// `device` (looked up once per device with that device current).
+constexpr size_t kStaticScratchBytes = size_t(64) << 20;
+cudaError_t static_scratch(int device, void** ptr);
+
 }  // namespace sc
