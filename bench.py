@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", default="broadband", choices=["broadband", "profile"],
+                    help="broadband: the benchmark workload; profile: the same kernel "
+                         "configuration at 128 x 128 nodes, for ncu captures")
     return ap.parse_args()
 
 
@@ -231,7 +234,7 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     ctx = sc.Context(local, stream=stream)
-    w = wl.broadband()
+    w = wl.broadband() if args.workload == "broadband" else wl.broadband(n_nodes=128)
     mc = w["mirror"]
     m = ctx.mirror(mc["f"], mc["r_min"], mc["r_max"], mc["n_r"], mc["n_theta"], rim=mc["rim"])
     inc = ctx.incident(profile=w["beam"]["profile"], w0=w["beam"]["w0"], pol=w["beam"]["pol"],

@@ -78,6 +78,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes)
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar)
 {
     asm volatile(
@@ -193,6 +198,58 @@ __device__ __forceinline__ void eval_one(Acc12& a, const float* co, float k, flo
     }
 }
 
+// Packed form of the same evaluation for the grouped kernel: accumulators as
+// (re, im) pairs and coefficients stored pre-duplicated as (c, c) pairs, so
+// the 18 accumulation FMAs issue as 9 FFMA2 and z as one more.  Lane-ops per
+// evaluation stay 26; issued instructions drop from 26 to 16.
+struct AccX2 {
+    float2 v[6];  // E_x, E_y, E_z, B_x, B_y, B_z as (re, im)
+};
+
+__device__ __forceinline__ void eval_x2(AccX2& a, const float2* cp, float k, float2 ph)
+{
+    const float2 q = make_float2(-k * ph.y, k * ph.x);  // q = ik ph
+    const float2 z = __ffma2_rn(cp[9], ph, q);           // z = q - ph/R  (cp[9] = (-1/R, -1/R))
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        a.v[c] = __ffma2_rn(cp[c], q, __ffma2_rn(cp[3 + c], z, a.v[c]));
+        a.v[3 + c] = __ffma2_rn(cp[6 + c], z, a.v[3 + c]);
+    }
+}
+
+template <int NB>
+__device__ __forceinline__ void fold(float2* dst, AccX2* acc, int nb, bool first)
+{
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        if (j < nb) {
+            float4* d4 = reinterpret_cast<float4*>(dst + (size_t)j * kAcc);
+            if (first) {
+#pragma unroll
+                for (int c = 0; c < kAcc / 2; ++c)
+                    d4[c] = make_float4(acc[j].v[c].x, 0.f, acc[j].v[c].y, 0.f);
+            } else {
+                float4 h[kAcc / 2];
+#pragma unroll
+                for (int c = 0; c < kAcc / 2; ++c) h[c] = d4[c];  // six loads in flight together
+#pragma unroll
+                for (int c = 0; c < kAcc / 2; ++c) {
+                    const float a0 = acc[j].v[c].x, a1 = acc[j].v[c].y;
+                    const float s0 = h[c].x + a0, b0 = s0 - h[c].x;
+                    const float e0 = (h[c].x - (s0 - b0)) + (a0 - b0);
+                    const float s1 = h[c].z + a1, b1 = s1 - h[c].z;
+                    const float e1 = (h[c].z - (s1 - b1)) + (a1 - b1);
+                    d4[c] = make_float4(s0, h[c].y + e0, s1, h[c].w + e1);
+                }
+            }
+            // one omega at a time: keeps the register footprint of the fold small
+            asm volatile("" ::: "memory");
+        }
+#pragma unroll
+        for (int c = 0; c < kAcc / 2; ++c) acc[j].v[c] = make_float2(0.f, 0.f);
+    }
+}
+
 // Fold one thread's FP32 sums for omegas [n0, n0 + nb) into its compensated
 // partials: (hi, lo) <- (hi, lo) + acc by TwoSum, or a plain store on the
 // first fold.  Each (split, point, omega) entry belongs to exactly one thread.
@@ -249,24 +306,45 @@ __device__ __forceinline__ void load_point(const double* pts, int n_pts, int p, 
 
 // ------------------------------------------------------------------------
 // Grouped kernel: G = ceil(n_omega / 8) >= 2 omega groups per point.
-// TPP threads per point (power of two >= G, <= 256), PPC points per CTA.
+// Warp-specialised, 384 threads:
+//   consumers  warps 0-7 (256 threads): thread (point pl, group g) owns 8
+//              consecutive omegas of one point and runs only the 26-op loop;
+//              PPC = 256 / TPP points per CTA, TPP = threads per point
+//              (power of two >= G, <= 256);
+//   producers  warps 8-11 (128 threads): stage node tiles with bulk copies and
+//              build the pair table of the next compute tile (geometry,
+//              coefficients, rotation, per-group seed phasors).
+// Pair tables are double buffered; `full` mbarriers (128 producer arrivals)
+// hand a table to the consumers and `empty` mbarriers (8 consumer-warp
+// arrivals) hand it back.  Every wait is bounded.  Each 32-node tile is
+// processed as CPT compute tiles of TC nodes so that two tables fit in
+// shared memory for every TPP.
 
 template <int TPP>
 struct Grouped {
-    static constexpr int PPC = (256 / TPP) < 8 ? (256 / TPP) : 8;
-    static constexpr int NT = PPC * TPP;
-    static constexpr int NPAIR = PPC * kTile;
-    static constexpr int NSEED = (TPP + 15) / 16;  // reseed points (every 16 groups)
-    // shared layout (bytes): node tiles | coefs | seeds | points | reseed omegas | mbarriers
+    static constexpr int NC = 256;                 // consumer threads
+    static constexpr int NPROD = 128;              // producer threads
+    static constexpr int NT = NC + NPROD;
+    static constexpr int PPC = NC / TPP;
+    static constexpr int TC = TPP == 2 ? 4 : (TPP == 4 ? 8 : (TPP <= 16 ? 16 : 32));
+    static constexpr int CPT = kTile / TC;
+    static constexpr int SEG = TPP >= 32 ? TPP / 32 : 1;  // seed segments of 32 groups per pair
+    static constexpr int NPAIR = PPC * TC;
+    static constexpr int NITEM = NPAIR * SEG;
+    static constexpr int COEF = 24;  // floats per pair: 10 duplicated pairs + rotation + pad
+    // shared layout (bytes): node tiles | coefs | seeds | points | segment omegas | mbarriers
     static constexpr size_t OFF_NODE = 0;
     static constexpr size_t OFF_COEF = OFF_NODE + 2 * kTileBytes;
-    static constexpr size_t COEF_BYTES = (size_t)NPAIR * 12 * 4;
+    static constexpr size_t COEF_BYTES = (size_t)NPAIR * COEF * 4;
     static constexpr size_t OFF_SEED = OFF_COEF + 2 * COEF_BYTES;
     static constexpr size_t SEED_BYTES = (size_t)NPAIR * TPP * 8;
     static constexpr size_t OFF_PTS = OFF_SEED + 2 * SEED_BYTES;
     static constexpr size_t OFF_OMS = OFF_PTS + PPC * 16;
-    static constexpr size_t OFF_BAR = (OFF_OMS + NSEED * 8 + 15) / 16 * 16;
-    static constexpr size_t SMEM = OFF_BAR + 16;
+    static constexpr size_t NOMS = (TPP + 15) / 16;  // reseed omegas, every 16 groups
+    static constexpr size_t OFF_BAR = (OFF_OMS + NOMS * 8 + 15) / 16 * 16;
+    static constexpr size_t SMEM = OFF_BAR + 6 * 8;  // node[2], full[2], empty[2]
+    static_assert(SMEM <= 227 * 1024, "shared memory");
+    static_assert(NC % TPP == 0 && kTile % TC == 0, "shape");
 };
 
 template <int TPP>
@@ -279,11 +357,11 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Fiel
     float2* seedbuf = reinterpret_cast<float2*>(smem + L::OFF_SEED);
     float4* spts = reinterpret_cast<float4*>(smem + L::OFF_PTS);
     float2* soms = reinterpret_cast<float2*>(smem + L::OFF_OMS);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
+    uint64_t* nbar = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
+    uint64_t* full = nbar + 2;
+    uint64_t* empty = nbar + 4;
 
     const int tid = threadIdx.x;
-    const int pl = tid / TPP;   // local point
-    const int g = tid % TPP;    // omega group
     const int p0 = blockIdx.x * L::PPC;
     const int split = blockIdx.y;
     int t0, t1;
@@ -291,145 +369,163 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Fiel
     const int G = (p.n_omega + kB - 1) / kB;
     const double om0 = (double)p.om_hi0 + (double)p.om_lo0;
     const double dom = (double)p.dom_hi + (double)p.dom_lo;
+    const int nt = t1 - t0;        // bulk-copied tiles
+    const int nct = nt * L::CPT;   // compute tiles
 
-    if (tid < L::PPC) load_point(p.pts, p.n_pts, p0 + tid, spts[tid]);
-    if (tid < L::NSEED) {
+    for (int i = tid; i < L::PPC; i += L::NT) load_point(p.pts, p.n_pts, p0 + i, spts[i]);
+    if (tid < (int)L::NOMS) {
         const double w = om0 + (double)(tid * 16 * kB) * dom;
         const float hi = (float)w;
         soms[tid] = make_float2(hi, (float)(w - (double)hi));
     }
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        mbar_init(&nbar[0], 1);
+        mbar_init(&nbar[1], 1);
+        mbar_init(&full[0], L::NPROD);
+        mbar_init(&full[1], L::NPROD);
+        mbar_init(&empty[0], L::NC / 32);
+        mbar_init(&empty[1], L::NC / 32);
         mbar_fence_init();
     }
-    // this thread's wavenumbers
-    float kv[kB];
-#pragma unroll
-    for (int j = 0; j < kB; ++j) kv[j] = (float)(6.283185307179586 * (om0 + (double)(g * kB + j) * dom));
-    // rotation steps as float-float
-    const float d1h = p.dom_hi, d1l = p.dom_lo;
-    const double domB = dom * kB;
-    const float dBh = (float)domB, dBl = (float)(domB - (double)(float)domB);
     __syncthreads();
 
-    unsigned issued[2] = {0, 0}, waited[2] = {0, 0};
     bool timed_out = false;
-    if (tid == 0) {
-        for (int s = 0; s < 2; ++s) {
-            if (t0 + s < t1) {
-                mbar_expect_tx(&bar[s], kTileBytes);
-                bulk_g2s(nodebuf + s * kTileFloats, p.nodes + (size_t)(t0 + s) * kTileFloats,
-                         kTileBytes, &bar[s]);
-                issued[s]++;
-            }
-        }
-    }
-
-    Acc12 acc[kB];
+    if (tid < L::NC) {
+        // ---------------- consumers ----------------
+        const int pl = tid / TPP;   // local point
+        const int g = tid % TPP;    // omega group
+        float kv[kB];
 #pragma unroll
-    for (int j = 0; j < kB; ++j)
+        for (int j = 0; j < kB; ++j)
+            kv[j] = (float)(6.283185307179586 * (om0 + (double)(g * kB + j) * dom));
+        AccX2 acc[kB];
 #pragma unroll
-        for (int c = 0; c < kAcc; ++c) acc[j].v[c] = 0.f;
-
-    // phase 1: tile t (index it = t - t0) -> pair buffer pb
-    auto phase1 = [&](int it, int pb) {
-        const int nbuf = it & 1;
-        const unsigned par = (unsigned)((it >> 1) & 1);
-        if (!mbar_wait(&bar[nbuf], par)) timed_out = true;
-        if (tid == 0) waited[nbuf]++;
-        const float* nb = nodebuf + nbuf * kTileFloats;
-        float* cb = coefbuf + (size_t)pb * L::NPAIR * 12;
-        float2* sb = seedbuf + (size_t)pb * L::NPAIR * TPP;
-        for (int q = tid; q < L::NPAIR; q += L::NT) {
-            const int pq = q / kTile, j = q % kTile;
-            float co[10];
-            const float phi = pair_coefs(nb, j, spts[pq], co);
-            const float2 rot = phasor_2wphi(d1h, d1l, phi);
-            float4* c4 = reinterpret_cast<float4*>(cb + (size_t)q * 12);
-            c4[0] = make_float4(co[0], co[1], co[2], co[3]);
-            c4[1] = make_float4(co[4], co[5], co[6], co[7]);
-            c4[2] = make_float4(co[8], co[9], rot.x, rot.y);
-            const float2 rotB = phasor_2wphi(dBh, dBl, phi);
-            float2 s = make_float2(1.f, 0.f);
-            for (int gg = 0; gg < G; ++gg) {
-                if ((gg & 15) == 0) {
-                    const float2 w = soms[gg >> 4];
-                    s = phasor_2wphi(w.x, w.y, phi);
-                } else {
-                    s = cmul(s, rotB);
-                }
-                sb[(size_t)q * TPP + gg] = s;
+        for (int j = 0; j < kB; ++j)
+#pragma unroll
+            for (int c = 0; c < kAcc / 2; ++c) acc[j].v[c] = make_float2(0.f, 0.f);
+        auto fold_now = [&](bool first) {
+            if (p0 + pl < p.n_pts && g < G) {
+                float2* dst = p.ws + (((size_t)split * p.n_pts + (p0 + pl)) * (size_t)p.n_omega +
+                                      (size_t)g * kB) * kAcc;
+                fold<kB>(dst, acc, min(kB, p.n_omega - g * kB), first);
             }
-        }
-    };
-
-    // phase 2: accumulate the tile in pair buffer pb
-    auto phase2 = [&](int pb) {
-        const float* cb = coefbuf + (size_t)pb * L::NPAIR * 12 + (size_t)pl * kTile * 12;
-        const float2* sb = seedbuf + (size_t)pb * L::NPAIR * TPP + (size_t)pl * kTile * TPP + g;
+        };
+        const int flush_ct = p.flush_tiles * L::CPT;
+        for (int c = 0; c < nct; ++c) {
+            const int pb = c & 1;
+            if (!mbar_wait(&full[pb], (unsigned)((c >> 1) & 1))) timed_out = true;
+            const float* cb = coefbuf + (size_t)pb * L::NPAIR * L::COEF + (size_t)pl * L::TC * L::COEF;
+            const float2* sb = seedbuf + (size_t)pb * L::NPAIR * TPP + (size_t)pl * L::TC * TPP + g;
 #pragma unroll 1
-        for (int j = 0; j < kTile; ++j) {
-            const float4* c4 = reinterpret_cast<const float4*>(cb + j * 12);
-            const float4 a0 = c4[0], a1 = c4[1], a2 = c4[2];
-            const float co[10] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y};
-            const float2 rot = make_float2(a2.z, a2.w);
-            float2 ph = sb[j * TPP];
+            for (int j = 0; j < L::TC; ++j) {
+                const float4* c4 = reinterpret_cast<const float4*>(cb + j * L::COEF);
+                float2 cp[10];
+                float2 rot;
+                {
+                    const float4 a0 = c4[0], a1 = c4[1], a2 = c4[2], a3 = c4[3], a4 = c4[4], a5 = c4[5];
+                    cp[0] = make_float2(a0.x, a0.y); cp[1] = make_float2(a0.z, a0.w);
+                    cp[2] = make_float2(a1.x, a1.y); cp[3] = make_float2(a1.z, a1.w);
+                    cp[4] = make_float2(a2.x, a2.y); cp[5] = make_float2(a2.z, a2.w);
+                    cp[6] = make_float2(a3.x, a3.y); cp[7] = make_float2(a3.z, a3.w);
+                    cp[8] = make_float2(a4.x, a4.y); cp[9] = make_float2(a4.z, a4.w);
+                    rot = make_float2(a5.x, a5.y);
+                }
+                float2 ph = sb[j * TPP];
 #pragma unroll
-            for (int jj = 0; jj < kB; ++jj) {
-                eval_one(acc[jj], co, kv[jj], ph);
-                if (jj + 1 < kB) ph = cmul(ph, rot);
+                for (int jj = 0; jj < kB; ++jj) {
+                    eval_x2(acc[jj], cp, kv[jj], ph);
+                    if (jj + 1 < kB) ph = cmul(ph, rot);
+                }
+            }
+            // hand the table back: one arrival per consumer warp, after the warp is done
+            __syncwarp();
+            if ((tid & 31) == 0) mbar_arrive(&empty[pb]);
+            if ((c + 1) % flush_ct == 0 || c + 1 == nct) fold_now(c + 1 <= flush_ct);
+        }
+        if (nct == 0) fold_now(true);  // e.g. the rim slot with the rim term off: zeros
+    } else {
+        // ---------------- producers ----------------
+        const int ptid = tid - L::NC;
+        const float d1h = p.dom_hi, d1l = p.dom_lo;
+        const double domB = dom * kB;
+        const float dBh = (float)domB, dBl = (float)(domB - (double)(float)domB);
+        unsigned issued[2] = {0, 0}, waited[2] = {0, 0};
+        if (ptid == 0) {
+            for (int s = 0; s < 2; ++s) {
+                if (s < nt) {
+                    mbar_expect_tx(&nbar[s], kTileBytes);
+                    bulk_g2s(nodebuf + s * kTileFloats, p.nodes + (size_t)(t0 + s) * kTileFloats,
+                             kTileBytes, &nbar[s]);
+                    issued[s]++;
+                }
             }
         }
-    };
-
-    const int nt = t1 - t0;
-    // this thread's partials: omegas g*8 .. g*8+7 of point p0 + pl
-    auto fold_now = [&](bool first) {
-        if (p0 + pl < p.n_pts && g < G) {
-            float2* dst = p.ws + (((size_t)split * p.n_pts + (p0 + pl)) * (size_t)p.n_omega +
-                                  (size_t)g * kB) * kAcc;
-            fold<kB>(dst, acc, min(kB, p.n_omega - g * kB), first);
-        }
-    };
-    if (nt > 0) {
-        phase1(0, 0);
-        __syncthreads();
-        if (tid == 0 && t0 + 2 < t1) {
-            fence_proxy_async();
-            mbar_expect_tx(&bar[0], kTileBytes);
-            bulk_g2s(nodebuf, p.nodes + (size_t)(t0 + 2) * kTileFloats, kTileBytes, &bar[0]);
-            issued[0]++;
-        }
-        for (int it = 0; it < nt; ++it) {
-            if (it + 1 < nt) phase1(it + 1, (it + 1) & 1);
-            phase2(it & 1);
-            if ((it + 1) % p.flush_tiles == 0 || it + 1 == nt) fold_now(it + 1 <= p.flush_tiles);
-            __syncthreads();
-            if (tid == 0 && it + 3 < nt) {
-                const int nbuf = (it + 1) & 1;
-                fence_proxy_async();
-                mbar_expect_tx(&bar[nbuf], kTileBytes);
-                bulk_g2s(nodebuf + nbuf * kTileFloats,
-                         p.nodes + (size_t)(t0 + it + 3) * kTileFloats, kTileBytes, &bar[nbuf]);
-                issued[nbuf]++;
+        for (int c = 0; c < nct; ++c) {
+            const int pb = c & 1;
+            const int it = c / L::CPT, sub = c % L::CPT;
+            const int nb_i = it & 1;
+            if (sub == 0) {
+                if (!mbar_wait(&nbar[nb_i], (unsigned)((it >> 1) & 1))) timed_out = true;
+                if (ptid == 0) waited[nb_i]++;
             }
+            // the table pb was last used for compute tile c - 2
+            if (c >= 2 && !mbar_wait(&empty[pb], (unsigned)(((c >> 1) - 1) & 1))) timed_out = true;
+            const float* nb = nodebuf + nb_i * kTileFloats;
+            float* cb = coefbuf + (size_t)pb * L::NPAIR * L::COEF;
+            float2* sb = seedbuf + (size_t)pb * L::NPAIR * TPP;
+            for (int i = ptid; i < L::NITEM; i += L::NPROD) {
+                const int q = i / L::SEG, seg = i % L::SEG;
+                const int pq = q / L::TC, j = q % L::TC;
+                float co[10];
+                const float phi = pair_coefs(nb, sub * L::TC + j, spts[pq], co);
+                if (seg == 0) {
+                    const float2 rot = phasor_2wphi(d1h, d1l, phi);
+                    float4* c4 = reinterpret_cast<float4*>(cb + (size_t)q * L::COEF);
+                    c4[0] = make_float4(co[0], co[0], co[1], co[1]);
+                    c4[1] = make_float4(co[2], co[2], co[3], co[3]);
+                    c4[2] = make_float4(co[4], co[4], co[5], co[5]);
+                    c4[3] = make_float4(co[6], co[6], co[7], co[7]);
+                    c4[4] = make_float4(co[8], co[8], -co[9], -co[9]);
+                    c4[5] = make_float4(rot.x, rot.y, 0.f, 0.f);
+                }
+                const int g0 = seg * 32, g1 = min(G, g0 + 32);
+                if (g0 < g1) {
+                    const float2 rotB = phasor_2wphi(dBh, dBl, phi);
+                    float2 sd = make_float2(1.f, 0.f);
+                    for (int gg = g0; gg < g1; ++gg) {
+                        if ((gg & 15) == 0) {
+                            const float2 w = soms[gg >> 4];
+                            sd = phasor_2wphi(w.x, w.y, phi);
+                        } else {
+                            sd = cmul(sd, rotB);
+                        }
+                        sb[(size_t)q * TPP + gg] = sd;
+                    }
+                }
+            }
+            mbar_arrive(&full[pb]);  // release: this thread's table entries are written
+            // node tile it fully read by all producers: refill its buffer with tile it + 2
+            if (sub == L::CPT - 1) {
+                asm volatile("bar.sync 1, %0;" ::"n"(L::NPROD) : "memory");
+                if (ptid == 0 && it + 2 < nt) {
+                    fence_proxy_async();
+                    mbar_expect_tx(&nbar[nb_i], kTileBytes);
+                    bulk_g2s(nodebuf + nb_i * kTileFloats, p.nodes + (size_t)(t0 + it + 2) * kTileFloats,
+                             kTileBytes, &nbar[nb_i]);
+                    issued[nb_i]++;
+                }
+            }
+        }
+        // drain: never leave a bulk copy in flight into freed shared memory
+        if (ptid == 0) {
+            for (int s = 0; s < 2; ++s)
+                while (waited[s] < issued[s]) {
+                    if (!mbar_wait(&nbar[s], waited[s] & 1)) { timed_out = true; break; }
+                    waited[s]++;
+                }
         }
     }
-
     if (timed_out) atomicOr(p.err, ERR_TIMEOUT);
-    // drain: never leave a bulk copy in flight into freed shared memory
-    if (tid == 0) {
-        for (int s = 0; s < 2; ++s)
-            while (waited[s] < issued[s]) {
-                if (!mbar_wait(&bar[s], waited[s] & 1)) { atomicOr(p.err, ERR_TIMEOUT); break; }
-                waited[s]++;
-            }
-    }
-
-    // a split without tiles (the rim slot when the rim term is off) still
-    // owns its partials: write zeros
-    if (nt == 0) fold_now(true);
 }
 
 // ------------------------------------------------------------------------
