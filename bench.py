@@ -153,9 +153,10 @@ def sum_over_ranks(pg, x: float) -> float:
     return float(t.item())
 
 
-def oracle_sample_rate(w, seconds: float):
+def oracle_sample_rate(w, seconds: float, amp=True):
     """FP64 oracle on the host cores over a bounded sample of the workload:
-    all nodes and omegas at a seeded subset of points, sized to ~seconds."""
+    all nodes and omegas at a seeded subset of points, sized to ~seconds.
+    Returns (evals/s, point indices, seconds, cores, E, B)."""
     import oracle
     from paper_1609_08146_gb300 import workloads as wl
 
@@ -164,17 +165,26 @@ def oracle_sample_rate(w, seconds: float):
     nodes = m["n_r"] * m["n_theta"]
     rng = np.random.Generator(np.random.PCG64(7))
     pts = w["points"]
+    a = oracle.spectrum(w["spectrum"], om, b) if amp else None
     # calibrate on one point
     t0 = time.perf_counter()
-    oracle.field(m, b, om, pts[:1])
+    oracle.field(m, b, om, pts[:1], amp=a)
     dt1 = time.perf_counter() - t0
     n = int(max(1, min(len(pts), seconds / max(dt1, 1e-6))))
-    idx = rng.choice(len(pts), size=n, replace=False)
+    idx = np.sort(rng.choice(len(pts), size=n, replace=False))
     t0 = time.perf_counter()
-    oracle.field(m, b, om, pts[idx])
+    E0, B0 = oracle.field(m, b, om, pts[idx], amp=a)
     dt = time.perf_counter() - t0
     evals = n * nodes * len(om)
-    return evals / dt, n, dt, os.cpu_count()
+    return evals / dt, idx, dt, os.cpu_count(), E0, B0
+
+
+def rel_l2(F, R):
+    """max over omega of sqrt(mean_points sum_c |F - R|^2) / max_points |R|."""
+    F = np.asarray(F, dtype=np.complex128)
+    num = np.sqrt(np.mean(np.sum(np.abs(F - R) ** 2, axis=2), axis=1))
+    den = np.max(np.sqrt(np.sum(np.abs(R) ** 2, axis=2)), axis=1)
+    return float(np.max(num / np.maximum(den, 1e-300)))
 
 
 def profile_traffic():
@@ -199,9 +209,9 @@ def run_reference(args, rank, world, pg):
     per_step = max(2.0, args.cpu_seconds / max(1, args.steps))
     rates = []
     for i in range(args.warmup + args.steps):
-        r, n, dt, cores = oracle_sample_rate(w, per_step)
+        r, idx, dt, cores, _, _ = oracle_sample_rate(w, per_step)
         if i >= args.warmup:
-            rates.append((r, n, dt, cores))
+            rates.append((r, len(idx), dt, cores))
     value = statistics.median([r[0] for r in rates])
     cores = rates[0][3]
     sample = "%d of %d points x all %d nodes x %d omegas per step (FP64 oracle, OpenMP)" % (
@@ -320,12 +330,35 @@ def main():
     if clk.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = achieved / (sms * 128 * clk["sm_mhz"] * 1e6 * 1e-12)
 
+    # ---- plain FP64 GPU form of the same sum, on a point subsample
+    sub = torch.tensor(w["points"][::65], device=dev)  # 64 points
+    ctx.eval(m, inc, om, sub[:2], precision="fp64")
+    e64 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with torch.cuda.stream(stream):
+        e64[0].record(stream)
+        E64, B64 = ctx.eval(m, inc, om, sub, precision="fp64")
+        e64[1].record(stream)
+    stream.synchronize()
+    fp64_rate = float(sub.shape[0]) * n_nodes * len(om) / (e64[0].elapsed_time(e64[1]) / 1000.0)
+    fp64 = {"value": fp64_rate, "unit": "evals/s", "sample": "%d points x all nodes x all omegas"
+            % sub.shape[0], "fp32_speedup": (value / world) / fp64_rate}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r, n, dt, cores = oracle_sample_rate(w, args.cpu_seconds)
+        r, idx, dt, cores, E0, B0 = oracle_sample_rate(w, args.cpu_seconds)
         cpu = {"value": r, "unit": "evals/s", "cores": cores, "kind": "oracle",
                "sample": "%d of %d points x all %d nodes x %d omegas (%.1f s, FP64 OpenMP)"
-               % (n, npts, n_nodes, len(om), dt)}
+               % (len(idx), npts, n_nodes, len(om), dt)}
+        # the oracle's sampled outputs also give the error of both GPU forms
+        ti = torch.tensor(idx, device=dev)
+        Eg = E.index_select(1, ti).cpu().numpy()
+        Bg = B.index_select(1, ti).cpu().numpy()
+        E6, B6 = ctx.eval(m, inc, om, P.index_select(0, ti), precision="fp64")
+        torch.cuda.synchronize()
+        cpu["fp32_rel_l2_err"] = max(rel_l2(Eg, E0), rel_l2(Bg, B0))
+        cpu["fp64_rel_l2_err"] = max(rel_l2(E6.cpu().numpy(), E0), rel_l2(B6.cpu().numpy(), B0))
+        fp64["fp32_rel_l2_err"] = cpu["fp32_rel_l2_err"]
+        fp64["fp64_rel_l2_err"] = cpu["fp64_rel_l2_err"]
 
     if rank == 0:
         line = {
@@ -343,6 +376,7 @@ def main():
             "gpu_launches": int(ctr["launches"]),
             "gpu_launches_per_step": launches_per_step,
             "roofline": roof,
+            "fp64_gpu": fp64,
             "cpu_baseline": cpu,
             "clocks": clk,
         }

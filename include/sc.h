@@ -257,6 +257,35 @@ sc_status sc_eval_fp32_static(sc_ctx* ctx, const sc_mirror_t* mirror, const sc_i
                               double omega0, double domega, int n_omega, const double* amp_re_im,
                               const double* points_xyz, int n_points, void* E_out, void* B_out);
 
+/*
+ * Batched evaluation (SC_FP32_COMP): many requests of uneven size -- each its
+ * own mirror, beam, uniform omega grid and point set -- in one scheduled
+ * pass.  Work items (request, omega chunk, point block, node split) of all
+ * requests are drained by one persistent kernel per kernel class from a
+ * device queue, the field launches are captured in a CUDA graph (replayed
+ * while the batch shape repeats), and one FP64 reduction finishes every
+ * request.  Each request's tiling depends only on its own shape, so its
+ * result is bitwise the same as sc_eval of that request alone.
+ * This is the batching pattern of the hot path; the paper computes one
+ * problem at a time with a domain decomposition over points (Sec. III.C.2).
+ *   omegas      host; points_xyz, E_out, B_out device (B_out may be NULL);
+ *               layouts as for sc_eval with SC_FP32_COMP.
+ * Asynchronous on the context stream unless stats is given.
+ * Errors: as sc_eval; SC_ERR_INVALID names the failing request.
+ */
+typedef struct {
+    const sc_mirror_t* mirror;
+    const sc_incident_t* incident;
+    const double* omegas;
+    int n_omega;
+    const double* points_xyz;
+    int n_points;
+    void* E_out;
+    void* B_out;
+} sc_request;
+
+sc_status sc_eval_batch(sc_ctx* ctx, const sc_request* reqs, int n_req, sc_eval_stats* stats);
+
 /* ---------------------------------------------------------------------- */
 /* Counters (measurement)                                                  */
 
@@ -265,6 +294,8 @@ typedef struct {
     uint64_t field_launches; /* field-sum kernel launches since reset              */
     double field_ms;         /* summed CUDA-event time of those launches           */
     double evals;            /* points x nodes x omegas issued since reset         */
+    uint64_t graph_captures; /* CUDA graphs captured for batched launches           */
+    uint64_t graph_replays;  /* launches that replayed a cached graph               */
 } sc_counters;
 
 /* Synchronizes the context stream and returns the counters. */
@@ -277,8 +308,11 @@ enum {
     SC_OPT_NODES_PER_SPLIT = 2, /* surface nodes per split (multiple of 32), or 0 */
                                 /* to pick the split count for load balance       */
     SC_OPT_WORKSPACE_CAP = 3,   /* max workspace bytes per launch chunk           */
-    SC_OPT_FLUSH_NODES = 4      /* nodes summed in an FP32 run before it is folded */
+    SC_OPT_FLUSH_NODES = 4,     /* nodes summed in an FP32 run before it is folded */
                                 /* into the compensated partial (multiple of 32)   */
+    SC_OPT_GRAPHS = 5,          /* 1 (default): capture/replay field launches       */
+    SC_OPT_AUTOTUNE = 6         /* 1 (default): time split-count candidates on the  */
+                                /* first request of each shape and cache the best   */
 };
 sc_status sc_set_option(sc_ctx* ctx, int option, long long value);
 

@@ -31,6 +31,7 @@ PROFILES = {"gauss": 0, "supergauss": 1, "tophat": 2}
 POLS = {"linear": 0, "radial": 1, "azimuthal": 2}
 SPECTRA = {"mono": 0, "gauss_time": 1, "supergauss_lambda": 2, "sampled": 3}
 SC_OPT_TIME_FIELD, SC_OPT_NODES_PER_SPLIT, SC_OPT_WORKSPACE_CAP, SC_OPT_FLUSH_NODES = 1, 2, 3, 4
+SC_OPT_GRAPHS, SC_OPT_AUTOTUNE = 5, 6
 
 _DP = ctypes.POINTER(ctypes.c_double)
 _VP = ctypes.c_void_p
@@ -64,7 +65,13 @@ class sc_eval_stats(ctypes.Structure):
 
 class sc_counters(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64), ("field_launches", ctypes.c_uint64),
-                ("field_ms", ctypes.c_double), ("evals", ctypes.c_double)]
+                ("field_ms", ctypes.c_double), ("evals", ctypes.c_double),
+                ("graph_captures", ctypes.c_uint64), ("graph_replays", ctypes.c_uint64)]
+
+
+class sc_request(ctypes.Structure):
+    _fields_ = [("mirror", _VP), ("incident", _VP), ("omegas", _DP), ("n_omega", ctypes.c_int),
+                ("points_xyz", _VP), ("n_points", ctypes.c_int), ("E_out", _VP), ("B_out", _VP)]
 
 
 # C-ABI symbol table: name -> (restype, argtypes)
@@ -85,6 +92,8 @@ SIGNATURES = {
                                       _DP, ctypes.c_int, _VP, _VP]),
     "sc_eval_fp32_static": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_int, _DP, _VP, ctypes.c_int, _VP, _VP]),
+    "sc_eval_batch": (ctypes.c_int, [_VP, ctypes.POINTER(sc_request), ctypes.c_int,
+                                     ctypes.POINTER(sc_eval_stats)]),
     "sc_get_counters": (ctypes.c_int, [_VP, ctypes.POINTER(sc_counters)]),
     "sc_reset_counters": (ctypes.c_int, [_VP]),
     "sc_set_option": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_longlong]),
@@ -295,11 +304,38 @@ class Context:
                                              _addr(Bt) if Bt is not None else None))
         return Et, Bt
 
+    def eval_batch(self, requests, stats: bool = False):
+        """Evaluate many requests in one scheduled pass (FP32 path).
+
+        requests: list of (mirror, incident, omegas, points) with points a
+        cuda float64 tensor [n, 3]; returns a list of (E, B) complex64
+        device tensors [n_omega, n, 3]."""
+        import torch
+
+        arr = (sc_request * len(requests))()
+        keep, outs = [], []
+        for i, (m, inc, om, pts) in enumerate(requests):
+            om = np.ascontiguousarray(np.atleast_1d(om), dtype=np.float64)
+            pts = pts.contiguous()
+            E = torch.empty((om.size, pts.shape[0], 3), dtype=torch.complex64, device=pts.device)
+            B = torch.empty_like(E)
+            keep += [om, pts]
+            outs.append((E, B))
+            arr[i] = sc_request(m._h, inc._h, _dptr(om), om.size, _VP(pts.data_ptr()), pts.shape[0],
+                                _VP(E.data_ptr()), _VP(B.data_ptr()))
+        st = sc_eval_stats()
+        self._check(self._lib.sc_eval_batch(self._h, arr, len(requests),
+                                            ctypes.byref(st) if stats else None))
+        if stats:
+            return outs, dict(evals=st.evals, field_ms=st.field_ms, total_ms=st.total_ms,
+                              launches=st.launches)
+        return outs
+
     def counters(self):
         c = sc_counters()
         self._check(self._lib.sc_get_counters(self._h, ctypes.byref(c)))
         return dict(launches=c.launches, field_launches=c.field_launches, field_ms=c.field_ms,
-                    evals=c.evals)
+                    evals=c.evals, graph_captures=c.graph_captures, graph_replays=c.graph_replays)
 
     def reset_counters(self):
         self._check(self._lib.sc_reset_counters(self._h))

@@ -11,7 +11,10 @@
 
 #include <algorithm>
 #include <atomic>
+#include <list>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "sc.h"
@@ -71,7 +74,7 @@ struct sc_ctx {
     size_t budget = 0;
     size_t held = 0;
     std::string err = "no error";
-    std::vector<Table> tables;
+    std::list<Table> tables;
     uint64_t tick = 0;
     DevBuf ws, pts, outE, outB, amp, kval, tvals, phasor, specE, specB, tE, tB;
     int* d_err = nullptr;
@@ -83,6 +86,20 @@ struct sc_ctx {
     size_t ws_cap = size_t(2) << 30;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
     std::vector<cudaEvent_t> pool;
+    // batched execution: descriptor arena, graph cache, split autotuner
+    DevBuf desc;
+    cudaStream_t cap_stream = nullptr;
+    bool use_graphs = true;
+    bool autotune = true;
+    struct GraphEntry {
+        std::vector<unsigned char> sig;
+        cudaGraphExec_t exec = nullptr;
+        uint64_t last = 0;
+    };
+    std::vector<GraphEntry> graphs;
+    uint64_t graph_tick = 0;
+    uint64_t graph_captures = 0, graph_replays = 0;
+    std::map<std::tuple<int, int, int, int, int>, int> tuned;  // shape -> split count
 };
 
 namespace {
@@ -432,9 +449,10 @@ void free_table(sc_ctx* ctx, Table& t)
     t = Table{};
 }
 
+// Look up or build the table of (m, in).  Public calls advance ctx->tick once;
+// tables touched by the current call carry that tick and are never evicted by it.
 sc_status get_table(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, Table** out)
 {
-    ctx->tick++;
     for (auto& t : ctx->tables)
         if (t.mid == m->id && t.iid == in->id) {
             t.last_use = ctx->tick;
@@ -456,8 +474,10 @@ sc_status get_table(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, 
     t.bytes = b32 + b64;
     // evict least recently used tables while over budget
     while (ctx->budget && ctx->held + t.bytes > ctx->budget && !ctx->tables.empty()) {
+        // evict the least recently used table that no call in flight on the host uses
         auto it = std::min_element(ctx->tables.begin(), ctx->tables.end(),
                                    [](const Table& a, const Table& b) { return a.last_use < b.last_use; });
+        if (it->last_use == ctx->tick) break;
         cudaStreamSynchronize(ctx->stream);
         free_table(ctx, *it);
         ctx->tables.erase(it);
@@ -568,6 +588,340 @@ bool uniform_grid(const double* om, int n, double& d)
     return true;
 }
 
+// ------------------------------------------------------------------------
+// Batched FP32 execution (A8): requests are cut into chunks (<= 2048 omegas,
+// points bounded by the workspace cap); chunks of one kernel class run in one
+// persistent launch whose CTAs take (chunk, point block, split) items from a
+// device queue; one batched FP64 reduce finishes every chunk.  The field
+// launches of a batch are captured into a CUDA graph and replayed while the
+// launch signature repeats.  Each chunk's split count comes from the
+// autotuner cache (or the heuristic), never from the rest of the batch, so a
+// request gives bitwise the same result alone or in a mix.
+
+struct Chunk {
+    sc::FieldLaunch f;      // ws assigned at execution
+    sc::ReduceLaunch rl;    // ws, off assigned at execution
+    int cls = 0, ppc = 1, pb = 1;
+    size_t ws_elems = 0;    // float2 elements
+};
+
+int heuristic_splits(int tiles, long long pb, int slots)
+{
+    // enough items for dynamic balance (about 16 per resident CTA), items of
+    // at least 32 node tiles, at most 64 splits
+    long long s = (16LL * slots + pb - 1) / pb;
+    s = std::min<long long>(s, std::max(1, tiles / 32));
+    return (int)std::max<long long>(1, std::min<long long>(64, s));
+}
+
+sc_status launch_chunks_direct(sc_ctx* ctx, std::vector<Chunk>& ch, float2* ws, size_t ws_n);
+
+// Time one chunk with split count S (the chunk's outputs are overwritten later).
+float time_chunk(sc_ctx* ctx, Chunk c, int S, const Table* tab, float2* ws)
+{
+    const int tps = (tab->n_surf_tiles + S - 1) / S;
+    c.f.tiles_per_split = tps;
+    c.f.n_splits = (tab->n_surf_tiles + tps - 1) / tps;
+    c.rl.n_splits = c.f.n_splits;
+    c.ws_elems = (size_t)(c.f.n_splits + 1) * c.f.n_pts * c.f.n_omega * sc::kAcc;
+    std::vector<Chunk> one{c};
+    cudaEvent_t a = take_event(ctx), b = take_event(ctx);
+    cudaEventRecord(a, ctx->stream);
+    sc_status st = launch_chunks_direct(ctx, one, ws, c.ws_elems);
+    cudaEventRecord(b, ctx->stream);
+    float ms = 1e30f;
+    if (st == SC_OK && cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+    cudaGetLastError();
+    ctx->pool.push_back(a);
+    ctx->pool.push_back(b);
+    return ms;
+}
+
+// Split count for a chunk shape: explicit option, tuned value, or heuristic
+// (tuned on first sight when the autotuner is on).
+sc_status choose_splits(sc_ctx* ctx, Chunk& c, const Table* tab, int slots, int* S_out)
+{
+    const int tiles = tab->n_surf_tiles;
+    if (ctx->nodes_per_split > 0) {
+        const int tps = (int)std::max<long long>(1, ctx->nodes_per_split / sc::kTile);
+        *S_out = (tiles + tps - 1) / tps;
+        return SC_OK;
+    }
+    const auto key = std::make_tuple(c.cls, tiles, tab->n_rim_tiles, c.f.n_pts, c.f.n_omega);
+    auto hit = ctx->tuned.find(key);
+    if (hit != ctx->tuned.end()) {
+        *S_out = hit->second;
+        return SC_OK;
+    }
+    const int s0 = heuristic_splits(tiles, c.pb, slots);
+    int best = s0;
+    if (ctx->autotune) {
+        // candidates around the heuristic, each timed once on the real chunk
+        std::vector<int> cand;
+        for (int s : {s0 / 2, s0, 2 * s0, 4 * s0})
+            if (s >= 1 && s <= std::min(64, tiles) &&
+                std::find(cand.begin(), cand.end(), s) == cand.end())
+                cand.push_back(s);
+        // only candidates whose whole-request workspace fits under the cap
+        size_t need = 0;
+        std::vector<int> fit;
+        for (int s : cand) {
+            const int tps = (tiles + s - 1) / s;
+            const int ns = (tiles + tps - 1) / tps;
+            const size_t n = (size_t)(ns + 1) * c.f.n_pts * c.f.n_omega * sc::kAcc;
+            if (n * sizeof(float2) <= ctx->ws_cap) {
+                fit.push_back(s);
+                need = std::max(need, n);
+            }
+        }
+        if (fit.size() > 1) {
+            sc_status st = ensure(ctx, ctx->ws, need * sizeof(float2));
+            if (st != SC_OK) return st;
+            float best_ms = 1e30f;
+            for (int s : fit) {
+                const float ms = time_chunk(ctx, c, s, tab, (float2*)ctx->ws.p);
+                if (ms < best_ms) { best_ms = ms; best = s; }
+            }
+        }
+    }
+    ctx->tuned[key] = best;
+    *S_out = best;
+    return SC_OK;
+}
+
+// Cut one request into chunks.  d_amp / d_k point at this request's a_n, k_n.
+sc_status plan_request(sc_ctx* ctx, const Table* tab, const double* omegas, int n_omega,
+                       double dom, const double* d_pts, int n_points, const double* d_amp,
+                       const double* d_k, float2* dE, float2* dB, std::vector<Chunk>& out)
+{
+    const int max_om_chunk = 2048;
+    const int flush_tiles = (int)std::max<long long>(1, ctx->flush_nodes / sc::kTile);
+    for (int o0 = 0; o0 < n_omega; o0 += max_om_chunk) {
+        const int no = std::min(max_om_chunk, n_omega - o0);
+        Chunk c;
+        c.cls = sc::field_class(no);
+        int slots = 1;
+        sc::field_shape(c.cls, ctx->device, &c.ppc, &slots);
+        const double w0 = omegas[o0];
+        c.f.nodes = tab->d32;
+        c.f.n_surf_tiles = tab->n_surf_tiles;
+        c.f.n_rim_tiles = tab->n_rim_tiles;
+        c.f.flush_tiles = flush_tiles;
+        c.f.n_omega = no;
+        c.f.om_hi0 = (float)w0;
+        c.f.om_lo0 = (float)(w0 - (double)c.f.om_hi0);
+        c.f.dom_hi = (float)dom;
+        c.f.dom_lo = (float)(dom - (double)c.f.dom_hi);
+        c.f.err = ctx->d_err;
+        c.f.ws = nullptr;
+        // the split count is chosen on the whole request's point count
+        c.f.pts = d_pts;
+        c.f.n_pts = n_points;
+        c.pb = (n_points + c.ppc - 1) / c.ppc;
+        c.rl.amp = d_amp + 2 * (size_t)o0;
+        c.rl.kval = d_k + o0;
+        c.rl.out_pt_stride_omega = (long long)n_points * 3;
+        c.rl.E = dE + (size_t)o0 * n_points * 3;
+        c.rl.B = dB ? dB + (size_t)o0 * n_points * 3 : nullptr;
+        c.rl.n_pts = n_points;
+        c.rl.n_omega = no;
+        int S = 1;
+        sc_status st = choose_splits(ctx, c, tab, slots, &S);
+        if (st != SC_OK) return st;
+        int tps = (tab->n_surf_tiles + S - 1) / S;
+        const int n_splits = (tab->n_surf_tiles + tps - 1) / tps;
+        c.f.tiles_per_split = tps;
+        c.f.n_splits = n_splits;
+        c.rl.n_splits = n_splits;
+        // point chunks bounded by the workspace cap
+        const size_t per_pt = (size_t)(n_splits + 1) * no * sc::kAcc;
+        long long pchunk = std::max<long long>(1, (long long)(ctx->ws_cap / sizeof(float2) / per_pt));
+        if (pchunk < n_points) pchunk = std::max<long long>(c.ppc, pchunk / c.ppc * c.ppc);
+        for (int p0 = 0; p0 < n_points; p0 += (int)pchunk) {
+            const int np = (int)std::min<long long>(pchunk, n_points - p0);
+            Chunk d = c;
+            d.f.pts = d_pts + 3 * (size_t)p0;
+            d.f.n_pts = np;
+            d.pb = (np + c.ppc - 1) / c.ppc;
+            d.rl.n_pts = np;
+            d.rl.E = c.rl.E + (size_t)p0 * 3;
+            d.rl.B = c.rl.B ? c.rl.B + (size_t)p0 * 3 : nullptr;
+            d.ws_elems = per_pt * np;
+            out.push_back(d);
+        }
+    }
+    return SC_OK;
+}
+
+// Launch a group of chunks whose workspaces fit in ws, with or without a
+// CUDA graph.  Field kernels (one persistent launch per class present) go
+// in the graph; the batched reduce follows on the stream.
+sc_status launch_chunks(sc_ctx* ctx, std::vector<Chunk>& ch, float2* ws, size_t ws_n, bool graph)
+{
+    // workspace offsets and reduce offsets
+    size_t off = 0;
+    long long roff = 0;
+    for (auto& c : ch) {
+        c.f.ws = ws + off;
+        c.rl.ws = ws + off;
+        c.rl.off = roff;
+        off += c.ws_elems;
+        roff += (long long)c.rl.n_pts * c.rl.n_omega;
+    }
+    if (off > ws_n) return fail(ctx, SC_ERR_OOM, "workspace plan exceeds its buffer");
+    // per-class descriptor arrays
+    constexpr int kClasses = 12;
+    std::vector<sc::WorkReq> reqs[kClasses];
+    long long items[kClasses] = {};
+    for (auto& c : ch) {
+        sc::WorkReq w;
+        w.f = c.f;
+        w.pb = c.pb;
+        w.cls = c.cls;
+        w.item0 = items[c.cls];
+        items[c.cls] += (long long)c.pb * (c.f.n_splits + 1);
+        reqs[c.cls].push_back(w);
+    }
+    std::vector<sc::ReduceLaunch> rls;
+    for (auto& c : ch) rls.push_back(c.rl);
+    // arena: queues (64 B each) | WorkReq arrays | ReduceLaunch array
+    size_t bytes = kClasses * 64;
+    size_t req_off[kClasses];
+    for (int k = 0; k < kClasses; ++k) {
+        req_off[k] = bytes;
+        bytes += (reqs[k].size() * sizeof(sc::WorkReq) + 255) / 256 * 256;
+    }
+    const size_t rl_off = bytes;
+    bytes += rls.size() * sizeof(sc::ReduceLaunch);
+    sc_status st = ensure(ctx, ctx->desc, bytes);
+    if (st != SC_OK) return st;
+    unsigned char* arena = (unsigned char*)ctx->desc.p;
+    for (int k = 0; k < kClasses; ++k)
+        if (!reqs[k].empty())
+            SC_CUDA(cudaMemcpyAsync(arena + req_off[k], reqs[k].data(), reqs[k].size() * sizeof(sc::WorkReq),
+                                    cudaMemcpyHostToDevice, ctx->stream), "upload work descriptors");
+    SC_CUDA(cudaMemcpyAsync(arena + rl_off, rls.data(), rls.size() * sizeof(sc::ReduceLaunch),
+                            cudaMemcpyHostToDevice, ctx->stream), "upload reduce descriptors");
+
+    struct L { int cls; sc::BatchLaunch b; int grid; };
+    std::vector<L> launches;
+    for (int k = 0; k < kClasses; ++k) {
+        if (reqs[k].empty()) continue;
+        int ppc = 1, slots = 1;
+        sc::field_shape(k, ctx->device, &ppc, &slots);
+        sc::BatchLaunch b{};
+        b.reqs = (const sc::WorkReq*)(arena + req_off[k]);
+        b.n_req = (int)reqs[k].size();
+        b.n_items = items[k];
+        b.queue = (int*)(arena + 64 * k);
+        b.err = ctx->d_err;
+        launches.push_back({k, b, (int)std::min<long long>(slots, items[k])});
+    }
+    auto issue = [&](cudaStream_t s) -> sc_status {
+        SC_CUDA(cudaMemsetAsync(arena, 0, kClasses * 64, s), "reset work queues");
+        for (auto& l : launches) {
+            const int r = sc::launch_field_batch(l.cls, l.b, l.grid, s);
+            if (r < 0) return cuda_fail(ctx, (cudaError_t)(-r), "field kernel launch");
+        }
+        return SC_OK;
+    };
+    cudaEvent_t f0 = nullptr, f1 = nullptr;
+    if (ctx->time_field) {
+        f0 = take_event(ctx);
+        f1 = take_event(ctx);
+        cudaEventRecord(f0, ctx->stream);
+    }
+    if (graph) {
+        // signature: everything the captured launches depend on
+        std::vector<unsigned char> sig;
+        auto put = [&](const void* p, size_t n) {
+            const unsigned char* q = (const unsigned char*)p;
+            sig.insert(sig.end(), q, q + n);
+        };
+        put(&arena, sizeof arena);
+        for (auto& l : launches) {
+            put(&l.cls, sizeof l.cls);
+            put(&l.grid, sizeof l.grid);
+            put(&l.b, sizeof l.b);
+        }
+        cudaGraphExec_t exec = nullptr;
+        for (auto& g : ctx->graphs)
+            if (g.sig == sig) {
+                exec = g.exec;
+                g.last = ++ctx->graph_tick;
+                ctx->graph_replays++;
+            }
+        if (!exec) {
+            if (!ctx->cap_stream)
+                SC_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking), "capture stream");
+            SC_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed), "begin capture");
+            st = issue(ctx->cap_stream);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+            if (st != SC_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+            e = cudaGraphInstantiate(&exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+            if (ctx->graphs.size() >= 8) {
+                auto it = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
+                                           [](const sc_ctx::GraphEntry& a, const sc_ctx::GraphEntry& b) {
+                                               return a.last < b.last;
+                                           });
+                cudaGraphExecDestroy(it->exec);
+                ctx->graphs.erase(it);
+            }
+            ctx->graphs.push_back({sig, exec, ++ctx->graph_tick});
+            ctx->graph_captures++;
+        }
+        SC_CUDA(cudaGraphLaunch(exec, ctx->stream), "graph launch");
+    } else {
+        st = issue(ctx->stream);
+        if (st != SC_OK) return st;
+    }
+    if (ctx->time_field) {
+        cudaEventRecord(f1, ctx->stream);
+        ctx->pending.push_back({f0, f1});
+    }
+    ctx->ctr.launches += launches.size();
+    ctx->ctr.field_launches += launches.size();
+    const int r = sc::launch_reduce_batch((const sc::ReduceLaunch*)(arena + rl_off), (int)rls.size(),
+                                          roff, ctx->stream);
+    if (r < 0) return cuda_fail(ctx, (cudaError_t)(-r), "reduce launch");
+    ctx->ctr.launches += r;
+    return SC_OK;
+}
+
+sc_status launch_chunks_direct(sc_ctx* ctx, std::vector<Chunk>& ch, float2* ws, size_t ws_n)
+{
+    const bool t = ctx->time_field;
+    ctx->time_field = false;
+    sc_status st = launch_chunks(ctx, ch, ws, ws_n, false);
+    ctx->time_field = t;
+    return st;
+}
+
+// Run chunks in groups whose workspace fits under the cap.
+sc_status run_chunks(sc_ctx* ctx, std::vector<Chunk>& ch)
+{
+    const size_t cap = std::max<size_t>(ctx->ws_cap / sizeof(float2), 1);
+    size_t i = 0;
+    while (i < ch.size()) {
+        size_t j = i, tot = 0;
+        while (j < ch.size() && (j == i || tot + ch[j].ws_elems <= cap)) tot += ch[j++].ws_elems;
+        sc_status st = ensure(ctx, ctx->ws, tot * sizeof(float2));
+        if (st != SC_OK) return st;
+        std::vector<Chunk> part(ch.begin() + i, ch.begin() + j);
+        st = launch_chunks(ctx, part, (float2*)ctx->ws.p, tot, ctx->use_graphs);
+        if (st != SC_OK) return st;
+        i = j;
+    }
+    return SC_OK;
+}
+
 }  // namespace
 
 // --------------------------------------------------------------------------
@@ -610,9 +964,12 @@ sc_status sc_destroy(sc_ctx* ctx)
     settle_events(ctx);
     for (auto& t : ctx->tables) free_table(ctx, t);
     for (DevBuf* b : {&ctx->ws, &ctx->pts, &ctx->outE, &ctx->outB, &ctx->amp, &ctx->kval,
-                      &ctx->tvals, &ctx->phasor, &ctx->specE, &ctx->specB, &ctx->tE, &ctx->tB})
+                      &ctx->tvals, &ctx->phasor, &ctx->specE, &ctx->specB, &ctx->tE, &ctx->tB,
+                      &ctx->desc})
         if (b->p) cudaFree(b->p);
     for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+    for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->h_err) cudaFreeHost(ctx->h_err);
     delete ctx;
@@ -718,6 +1075,7 @@ sc_status sc_eval(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, co
     if (prec == SC_FP32_COMP && !uniform_grid(omegas, n_omega, dom))
         return fail(ctx, SC_ERR_INVALID, "SC_FP32_COMP needs a uniform, increasing omega grid");
     SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    ctx->tick++;
 
     const bool pts_dev = is_device_ptr(points_xyz);
     const bool e_dev = is_device_ptr(E_out);
@@ -809,89 +1167,12 @@ sc_status sc_eval(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, co
         ctx->ctr.launches += r;
         ctx->ctr.field_launches += 1;
     } else {
-        // node splits and chunking of points / omegas to bound the workspace
-        const int max_om_chunk = 2048;
-        const int flush_tiles = (int)std::max<long long>(1, ctx->flush_nodes / sc::kTile);
-        for (int o0 = 0; o0 < n_omega; o0 += max_om_chunk) {
-            const int no = std::min(max_om_chunk, n_omega - o0);
-            int ppc = 1, slots = 1;
-            sc::field_shape(no, ctx->device, &ppc, &slots);
-            int tps;
-            if (ctx->nodes_per_split > 0) {
-                tps = (int)std::max<long long>(1, ctx->nodes_per_split / sc::kTile);
-            } else {
-                // splits only balance the grid: pick S (<= 32) whose (point block x
-                // split) count fills the resident CTA slots best, each split also
-                // paying about one tile of pipeline prologue
-                const long long pb = (n_points + ppc - 1) / ppc;
-                int best_s = 1;
-                double best = -1.0;
-                for (int S = 1; S <= std::min(32, tab->n_surf_tiles); ++S) {
-                    const long long units = pb * S;
-                    const long long waves = (units + slots - 1) / slots;
-                    const double eff = (double)units / ((double)waves * slots) *
-                                       (1.0 - (double)S / tab->n_surf_tiles);
-                    if (eff > best * 1.0005) { best = eff; best_s = S; }
-                }
-                tps = (tab->n_surf_tiles + best_s - 1) / best_s;
-            }
-            // the split index is the grid's y dimension (<= 65535 including the rim slot)
-            tps = std::max(tps, (tab->n_surf_tiles + 65533) / 65534);
-            const int n_splits = (tab->n_surf_tiles + tps - 1) / tps;
-            const size_t per_pt = (size_t)(n_splits + 1) * no * sc::kAcc * sizeof(float2);
-            int pchunk = (int)std::min<size_t>((size_t)n_points, std::max<size_t>(1, ctx->ws_cap / per_pt));
-            if (pchunk < n_points) pchunk = std::max(8, pchunk / 8 * 8);
-            if ((st = ensure(ctx, ctx->ws, per_pt * (size_t)pchunk)) != SC_OK) return st;
-            const double w0 = omegas[o0];
-            const float w0h = (float)w0, w0l = (float)(w0 - (double)w0h);
-            const float dh = (float)dom, dl = (float)(dom - (double)dh);
-            for (int p0 = 0; p0 < n_points; p0 += pchunk) {
-                const int np = std::min(pchunk, n_points - p0);
-                sc::FieldLaunch f;
-                f.nodes = tab->d32;
-                f.n_surf_tiles = tab->n_surf_tiles;
-                f.n_rim_tiles = tab->n_rim_tiles;
-                f.tiles_per_split = tps;
-                f.n_splits = n_splits;
-                f.flush_tiles = flush_tiles;
-                f.pts = d_pts + 3 * (size_t)p0;
-                f.n_pts = np;
-                f.n_omega = no;
-                f.om_hi0 = w0h;
-                f.om_lo0 = w0l;
-                f.dom_hi = dh;
-                f.dom_lo = dl;
-                f.ws = (float2*)ctx->ws.p;
-                f.err = ctx->d_err;
-                cudaEvent_t f0 = nullptr, f1 = nullptr;
-                if (ctx->time_field) {
-                    f0 = take_event(ctx);
-                    f1 = take_event(ctx);
-                    cudaEventRecord(f0, ctx->stream);
-                }
-                int r = sc::launch_field_f32(f, ctx->stream);
-                if (r < 0) return cuda_fail(ctx, (cudaError_t)(-r), "field kernel launch");
-                if (ctx->time_field) {
-                    cudaEventRecord(f1, ctx->stream);
-                    ctx->pending.push_back({f0, f1});
-                }
-                ctx->ctr.launches += r;
-                ctx->ctr.field_launches += 1;
-                sc::ReduceLaunch rl;
-                rl.ws = (const float2*)ctx->ws.p;
-                rl.n_splits = n_splits;
-                rl.n_pts = np;
-                rl.n_omega = no;
-                rl.amp = d_amp + 2 * (size_t)o0;
-                rl.kval = d_k + o0;
-                rl.out_pt_stride_omega = (long long)n_points * 3;
-                rl.E = (float2*)dE + ((size_t)o0 * n_points + p0) * 3;
-                rl.B = dB ? (float2*)dB + ((size_t)o0 * n_points + p0) * 3 : nullptr;
-                r = sc::launch_reduce_f32(rl, ctx->stream);
-                if (r < 0) return cuda_fail(ctx, (cudaError_t)(-r), "reduce kernel launch");
-                ctx->ctr.launches += r;
-            }
-        }
+        std::vector<Chunk> ch;
+        st = plan_request(ctx, tab, omegas, n_omega, dom, d_pts, n_points, d_amp, d_k, (float2*)dE,
+                          (float2*)dB, ch);
+        if (st != SC_OK) return st;
+        st = run_chunks(ctx, ch);
+        if (st != SC_OK) return st;
     }
     ctx->ctr.evals += evals;
 
@@ -916,6 +1197,95 @@ sc_status sc_eval(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, co
         stats->field_ms = ctx->ctr.field_ms - field_ms_before;
         stats->launches = (int)(ctx->ctr.launches - launches_before);
         ctx->time_field = timing_before;
+    }
+    return SC_OK;
+}
+
+sc_status sc_eval_batch(sc_ctx* ctx, const sc_request* reqs, int n_req, sc_eval_stats* stats)
+{
+    if (!ctx) return SC_ERR_INVALID;
+    if (!reqs || n_req < 1) return fail(ctx, SC_ERR_INVALID, "invalid argument");
+    std::vector<double> dom(n_req);
+    size_t n_om_total = 0;
+    for (int r = 0; r < n_req; ++r) {
+        const sc_request& q = reqs[r];
+        if (!q.mirror || !q.incident || !q.omegas || !q.points_xyz || !q.E_out || q.n_omega < 1 ||
+            q.n_points < 1)
+            return fail(ctx, SC_ERR_INVALID, "request %d: invalid argument", r);
+        for (int i = 0; i < q.n_omega; ++i)
+            if (!(q.omegas[i] > 0.0) || !std::isfinite(q.omegas[i]))
+                return fail(ctx, SC_ERR_INVALID, "request %d: omega[%d] must be positive", r, i);
+        if (!uniform_grid(q.omegas, q.n_omega, dom[r]))
+            return fail(ctx, SC_ERR_INVALID, "request %d: needs a uniform, increasing omega grid", r);
+        if (!is_device_ptr(q.points_xyz) || !is_device_ptr(q.E_out) ||
+            (q.B_out && !is_device_ptr(q.B_out)))
+            return fail(ctx, SC_ERR_INVALID, "request %d: points and outputs must be device buffers", r);
+        n_om_total += q.n_omega;
+    }
+    SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    ctx->tick++;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    const double field_ms_before = ctx->ctr.field_ms;
+    const uint64_t launches_before = ctx->ctr.launches;
+    const bool timing_before = ctx->time_field;
+    if (stats) {
+        ev0 = take_event(ctx);
+        ev1 = take_event(ctx);
+        cudaEventRecord(ev0, ctx->stream);
+        ctx->time_field = true;
+    }
+    // spectra and wavenumbers of all requests, one upload
+    std::vector<double> amp_all(2 * n_om_total), k_all(n_om_total);
+    std::vector<size_t> om_off(n_req);
+    size_t o = 0;
+    for (int r = 0; r < n_req; ++r) {
+        std::vector<double> a;
+        sc_status st = spectrum_amps(ctx, reqs[r].incident, reqs[r].omegas, reqs[r].n_omega, a);
+        if (st != SC_OK) return st;
+        om_off[r] = o;
+        std::copy(a.begin(), a.end(), amp_all.begin() + 2 * o);
+        for (int i = 0; i < reqs[r].n_omega; ++i) k_all[o + i] = 2.0 * kPi * reqs[r].omegas[i];
+        o += reqs[r].n_omega;
+    }
+    std::vector<Table*> tabs(n_req);
+    double evals = 0.0;
+    for (int r = 0; r < n_req; ++r) {
+        sc_status st = get_table(ctx, reqs[r].mirror, reqs[r].incident, &tabs[r]);
+        if (st != SC_OK) return st;
+        evals += (double)reqs[r].n_points * tabs[r]->n_surf * reqs[r].n_omega;
+    }
+    sc_status st;
+    if ((st = ensure(ctx, ctx->amp, amp_all.size() * sizeof(double))) != SC_OK) return st;
+    if ((st = ensure(ctx, ctx->kval, k_all.size() * sizeof(double))) != SC_OK) return st;
+    SC_CUDA(cudaMemcpyAsync(ctx->amp.p, amp_all.data(), amp_all.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, ctx->stream), "upload amplitudes");
+    SC_CUDA(cudaMemcpyAsync(ctx->kval.p, k_all.data(), k_all.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, ctx->stream), "upload wavenumbers");
+    std::vector<Chunk> ch;
+    for (int r = 0; r < n_req; ++r) {
+        const sc_request& q = reqs[r];
+        st = plan_request(ctx, tabs[r], q.omegas, q.n_omega, dom[r], q.points_xyz, q.n_points,
+                          (const double*)ctx->amp.p + 2 * om_off[r], (const double*)ctx->kval.p + om_off[r],
+                          (float2*)q.E_out, (float2*)q.B_out, ch);
+        if (st != SC_OK) return st;
+    }
+    st = run_chunks(ctx, ch);
+    if (st != SC_OK) return st;
+    ctx->ctr.evals += evals;
+    if (stats) {
+        cudaEventRecord(ev1, ctx->stream);
+        st = check_device_error(ctx);
+        ctx->time_field = timing_before;
+        if (st != SC_OK) return st;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        ctx->pool.push_back(ev0);
+        ctx->pool.push_back(ev1);
+        settle_events(ctx);
+        stats->evals = evals;
+        stats->total_ms = ms;
+        stats->field_ms = ctx->ctr.field_ms - field_ms_before;
+        stats->launches = (int)(ctx->ctr.launches - launches_before);
     }
     return SC_OK;
 }
@@ -949,6 +1319,7 @@ sc_status sc_eval_fp32_static(sc_ctx* ctx, const sc_mirror_t* m, const sc_incide
     if (!tab)
         return fail(ctx, SC_ERR_INVALID,
                     "node table not resident: run sc_eval once for this mirror and incident first");
+    ctx->tick++;
     void* scratch = nullptr;
     cudaError_t e = sc::static_scratch(ctx->device, &scratch);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "static scratch address");
@@ -1079,6 +1450,8 @@ sc_status sc_get_counters(sc_ctx* ctx, sc_counters* out)
     sc_status st = check_device_error(ctx);
     settle_events(ctx);
     *out = ctx->ctr;
+    out->graph_captures = ctx->graph_captures;
+    out->graph_replays = ctx->graph_replays;
     return st;
 }
 
@@ -1107,6 +1480,8 @@ sc_status sc_set_option(sc_ctx* ctx, int option, long long value)
             return fail(ctx, SC_ERR_INVALID, "flush length must be a positive multiple of %d", sc::kTile);
         ctx->flush_nodes = value;
         return SC_OK;
+    case SC_OPT_GRAPHS: ctx->use_graphs = value != 0; return SC_OK;
+    case SC_OPT_AUTOTUNE: ctx->autotune = value != 0; return SC_OK;
     case SC_OPT_WORKSPACE_CAP:
         if (value < (1 << 20)) return fail(ctx, SC_ERR_INVALID, "workspace cap below 1 MiB");
         ctx->ws_cap = (size_t)value;

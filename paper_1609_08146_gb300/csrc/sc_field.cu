@@ -51,6 +51,7 @@ namespace {
 constexpr int kB = 8;                 // omegas per thread in the grouped kernel
 constexpr unsigned kSpinLimit = 1u << 26;       // bounded mbarrier waits: polls
 constexpr uint64_t kWaitNs = 1000000000ull;     // ... and wall time (1 s)
+constexpr unsigned kSuspendNs = 20000;          // suspend-time hint per poll
 
 // ------------------------------------------------------------------------
 // mbarrier / bulk-copy helpers (inline PTX)
@@ -105,8 +106,11 @@ __device__ __forceinline__ uint64_t global_ns()
 }
 
 // Bounded wait on phase `parity`: gives up after about one second of wall
-// time (or kSpinLimit polls) and returns false, so a copy that never lands
-// turns into an error flag instead of a hung kernel.
+// time (or kSpinLimit polls) and returns false, so a copy or a hand-over that
+// never lands turns into an error flag instead of a hung kernel.  Each poll
+// may suspend the warp for up to kSuspendNs until the phase completes, and
+// the clock is read only every 64 polls, so waiting warps take few issue
+// slots from working ones.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity)
 {
     const uint32_t addr = smem_u32(bar);
@@ -115,15 +119,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity)
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
-            : "r"(addr), "r"(parity)
+            : "r"(addr), "r"(parity), "n"(kSuspendNs)
             : "memory");
         if (done) return true;
-        const uint64_t now = global_ns();
-        if (it == 0) t0 = now;
-        else if (now - t0 > kWaitNs) return false;
+        if ((it & 63) == 0) {
+            const uint64_t now = global_ns();
+            if (it == 0) t0 = now;
+            else if (now - t0 > kWaitNs) return false;
+        }
     }
     return false;
 }
@@ -305,20 +311,66 @@ __device__ __forceinline__ void load_point(const double* pts, int n_pts, int p, 
 }
 
 // ------------------------------------------------------------------------
+// Work items.  Every kernel below loops over work items (request, point
+// block, split): in grid mode the item is blockIdx.x of a single request, in
+// queue mode CTAs stay resident and take items from a device counter until
+// the batch is exhausted (persistent scheduling across requests of uneven
+// size).  Items of one request are numbered point block fastest, so CTAs that
+// run at the same time share node tiles in L2.  The arithmetic of an item
+// never depends on the other requests of a batch.
+
+struct Item {
+    const WorkReq* r;
+    int pbi, split;
+};
+
+__device__ __forceinline__ const WorkReq* find_req(const BatchLaunch& b, long long item)
+{
+    if (!b.reqs) return &b.one;
+    int lo = 0, hi = b.n_req - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.reqs[mid].item0 <= item) lo = mid; else hi = mid - 1;
+    }
+    return &b.reqs[lo];
+}
+
+// next item for the whole CTA (thread 0 takes it, everyone reads it)
+__device__ __forceinline__ long long next_item(const BatchLaunch& b, long long* slot, long long prev)
+{
+    __syncthreads();  // everyone is done with the previous item (and its slot value)
+    if (threadIdx.x == 0)
+        *slot = b.queue ? (long long)atomicAdd(b.queue, 1) : (prev < 0 ? (long long)blockIdx.x : b.n_items);
+    __syncthreads();
+    return *slot;
+}
+
+__device__ __forceinline__ Item decode(const BatchLaunch& b, long long item)
+{
+    Item it;
+    it.r = find_req(b, item);
+    const long long local = item - it.r->item0;
+    it.pbi = (int)(local % it.r->pb);
+    it.split = (int)(local / it.r->pb);
+    return it;
+}
+
+// ------------------------------------------------------------------------
 // Grouped kernel: G = ceil(n_omega / 8) >= 2 omega groups per point.
 // Warp-specialised, 384 threads:
 //   consumers  warps 0-7 (256 threads): thread (point pl, group g) owns 8
 //              consecutive omegas of one point and runs only the 26-op loop;
-//              PPC = 256 / TPP points per CTA, TPP = threads per point
+//              PPC = 256 / TPP points per item, TPP = threads per point
 //              (power of two >= G, <= 256);
 //   producers  warps 8-11 (128 threads): stage node tiles with bulk copies and
 //              build the pair table of the next compute tile (geometry,
 //              coefficients, rotation, per-group seed phasors).
 // Pair tables are double buffered; `full` mbarriers (128 producer arrivals)
 // hand a table to the consumers and `empty` mbarriers (8 consumer-warp
-// arrivals) hand it back.  Every wait is bounded.  Each 32-node tile is
-// processed as CPT compute tiles of TC nodes so that two tables fit in
-// shared memory for every TPP.
+// arrivals) hand it back.  Buffer indices and phase parities come from
+// counters that run on across items, so the barriers are initialised once.
+// Every wait is bounded.  Each 32-node tile is processed as CPT compute
+// tiles of TC nodes so that two tables fit in shared memory for every TPP.
 
 template <int TPP>
 struct Grouped {
@@ -332,7 +384,7 @@ struct Grouped {
     static constexpr int NPAIR = PPC * TC;
     static constexpr int NITEM = NPAIR * SEG;
     static constexpr int COEF = 24;  // floats per pair: 10 duplicated pairs + rotation + pad
-    // shared layout (bytes): node tiles | coefs | seeds | points | segment omegas | mbarriers
+    // shared layout (bytes): node tiles | coefs | seeds | points | segment omegas | mbarriers | item
     static constexpr size_t OFF_NODE = 0;
     static constexpr size_t OFF_COEF = OFF_NODE + 2 * kTileBytes;
     static constexpr size_t COEF_BYTES = (size_t)NPAIR * COEF * 4;
@@ -342,13 +394,13 @@ struct Grouped {
     static constexpr size_t OFF_OMS = OFF_PTS + PPC * 16;
     static constexpr size_t NOMS = (TPP + 15) / 16;  // reseed omegas, every 16 groups
     static constexpr size_t OFF_BAR = (OFF_OMS + NOMS * 8 + 15) / 16 * 16;
-    static constexpr size_t SMEM = OFF_BAR + 6 * 8;  // node[2], full[2], empty[2]
+    static constexpr size_t SMEM = OFF_BAR + 7 * 8;  // node[2], full[2], empty[2], item slot
     static_assert(SMEM <= 227 * 1024, "shared memory");
     static_assert(NC % TPP == 0 && kTile % TC == 0, "shape");
 };
 
 template <int TPP>
-__global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(FieldLaunch p)
+__global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(BatchLaunch b)
 {
     using L = Grouped<TPP>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -360,24 +412,9 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Fiel
     uint64_t* nbar = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
     uint64_t* full = nbar + 2;
     uint64_t* empty = nbar + 4;
+    long long* slot = reinterpret_cast<long long*>(nbar + 6);
 
     const int tid = threadIdx.x;
-    const int p0 = blockIdx.x * L::PPC;
-    const int split = blockIdx.y;
-    int t0, t1;
-    split_range(p, split, t0, t1);
-    const int G = (p.n_omega + kB - 1) / kB;
-    const double om0 = (double)p.om_hi0 + (double)p.om_lo0;
-    const double dom = (double)p.dom_hi + (double)p.dom_lo;
-    const int nt = t1 - t0;        // bulk-copied tiles
-    const int nct = nt * L::CPT;   // compute tiles
-
-    for (int i = tid; i < L::PPC; i += L::NT) load_point(p.pts, p.n_pts, p0 + i, spts[i]);
-    if (tid < (int)L::NOMS) {
-        const double w = om0 + (double)(tid * 16 * kB) * dom;
-        const float hi = (float)w;
-        soms[tid] = make_float2(hi, (float)(w - (double)hi));
-    }
     if (tid == 0) {
         mbar_init(&nbar[0], 1);
         mbar_init(&nbar[1], 1);
@@ -387,245 +424,282 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Fiel
         mbar_init(&empty[1], L::NC / 32);
         mbar_fence_init();
     }
-    __syncthreads();
-
     bool timed_out = false;
-    if (tid < L::NC) {
-        // ---------------- consumers ----------------
-        const int pl = tid / TPP;   // local point
-        const int g = tid % TPP;    // omega group
-        float kv[kB];
+    long long cbase = 0, tbase = 0;  // compute tiles and node tiles done by this CTA
+
+    for (long long item = next_item(b, slot, -1); item < b.n_items; item = next_item(b, slot, item)) {
+        const Item w = decode(b, item);
+        const FieldLaunch& p = w.r->f;
+        const int p0 = w.pbi * L::PPC;
+        const int split = w.split;
+        int t0, t1;
+        split_range(p, split, t0, t1);
+        const int G = (p.n_omega + kB - 1) / kB;
+        const double om0 = (double)p.om_hi0 + (double)p.om_lo0;
+        const double dom = (double)p.dom_hi + (double)p.dom_lo;
+        const int nt = t1 - t0;        // bulk-copied tiles
+        const int nct = nt * L::CPT;   // compute tiles
+
+        for (int i = tid; i < L::PPC; i += L::NT) load_point(p.pts, p.n_pts, p0 + i, spts[i]);
+        if (tid < (int)L::NOMS) {
+            const double wv = om0 + (double)(tid * 16 * kB) * dom;
+            const float hi = (float)wv;
+            soms[tid] = make_float2(hi, (float)(wv - (double)hi));
+        }
+        __syncthreads();
+
+        if (tid < L::NC) {
+            // ---------------- consumers ----------------
+            const int pl = tid / TPP;   // local point
+            const int g = tid % TPP;    // omega group
+            float kv[kB];
 #pragma unroll
-        for (int j = 0; j < kB; ++j)
-            kv[j] = (float)(6.283185307179586 * (om0 + (double)(g * kB + j) * dom));
-        AccX2 acc[kB];
+            for (int j = 0; j < kB; ++j)
+                kv[j] = (float)(6.283185307179586 * (om0 + (double)(g * kB + j) * dom));
+            AccX2 acc[kB];
 #pragma unroll
-        for (int j = 0; j < kB; ++j)
+            for (int j = 0; j < kB; ++j)
 #pragma unroll
-            for (int c = 0; c < kAcc / 2; ++c) acc[j].v[c] = make_float2(0.f, 0.f);
-        auto fold_now = [&](bool first) {
-            if (p0 + pl < p.n_pts && g < G) {
-                float2* dst = p.ws + (((size_t)split * p.n_pts + (p0 + pl)) * (size_t)p.n_omega +
-                                      (size_t)g * kB) * kAcc;
-                fold<kB>(dst, acc, min(kB, p.n_omega - g * kB), first);
-            }
-        };
-        const int flush_ct = p.flush_tiles * L::CPT;
-        for (int c = 0; c < nct; ++c) {
-            const int pb = c & 1;
-            if (!mbar_wait(&full[pb], (unsigned)((c >> 1) & 1))) timed_out = true;
-            const float* cb = coefbuf + (size_t)pb * L::NPAIR * L::COEF + (size_t)pl * L::TC * L::COEF;
-            const float2* sb = seedbuf + (size_t)pb * L::NPAIR * TPP + (size_t)pl * L::TC * TPP + g;
+                for (int c = 0; c < kAcc / 2; ++c) acc[j].v[c] = make_float2(0.f, 0.f);
+            auto fold_now = [&](bool first) {
+                if (p0 + pl < p.n_pts && g < G) {
+                    float2* dst = p.ws + (((size_t)split * p.n_pts + (p0 + pl)) * (size_t)p.n_omega +
+                                          (size_t)g * kB) * kAcc;
+                    fold<kB>(dst, acc, min(kB, p.n_omega - g * kB), first);
+                }
+            };
+            const int flush_ct = p.flush_tiles * L::CPT;
+            for (int c = 0; c < nct; ++c) {
+                const long long cg = cbase + c;
+                const int pb = (int)(cg & 1);
+                if (!mbar_wait(&full[pb], (unsigned)((cg >> 1) & 1))) timed_out = true;
+                const float* cb = coefbuf + (size_t)pb * L::NPAIR * L::COEF + (size_t)pl * L::TC * L::COEF;
+                const float2* sb = seedbuf + (size_t)pb * L::NPAIR * TPP + (size_t)pl * L::TC * TPP + g;
 #pragma unroll 1
-            for (int j = 0; j < L::TC; ++j) {
-                const float4* c4 = reinterpret_cast<const float4*>(cb + j * L::COEF);
-                float2 cp[10];
-                float2 rot;
-                {
-                    const float4 a0 = c4[0], a1 = c4[1], a2 = c4[2], a3 = c4[3], a4 = c4[4], a5 = c4[5];
-                    cp[0] = make_float2(a0.x, a0.y); cp[1] = make_float2(a0.z, a0.w);
-                    cp[2] = make_float2(a1.x, a1.y); cp[3] = make_float2(a1.z, a1.w);
-                    cp[4] = make_float2(a2.x, a2.y); cp[5] = make_float2(a2.z, a2.w);
-                    cp[6] = make_float2(a3.x, a3.y); cp[7] = make_float2(a3.z, a3.w);
-                    cp[8] = make_float2(a4.x, a4.y); cp[9] = make_float2(a4.z, a4.w);
-                    rot = make_float2(a5.x, a5.y);
-                }
-                float2 ph = sb[j * TPP];
+                for (int j = 0; j < L::TC; ++j) {
+                    const float4* c4 = reinterpret_cast<const float4*>(cb + j * L::COEF);
+                    float2 cp[10];
+                    float2 rot;
+                    {
+                        const float4 a0 = c4[0], a1 = c4[1], a2 = c4[2], a3 = c4[3], a4 = c4[4], a5 = c4[5];
+                        cp[0] = make_float2(a0.x, a0.y); cp[1] = make_float2(a0.z, a0.w);
+                        cp[2] = make_float2(a1.x, a1.y); cp[3] = make_float2(a1.z, a1.w);
+                        cp[4] = make_float2(a2.x, a2.y); cp[5] = make_float2(a2.z, a2.w);
+                        cp[6] = make_float2(a3.x, a3.y); cp[7] = make_float2(a3.z, a3.w);
+                        cp[8] = make_float2(a4.x, a4.y); cp[9] = make_float2(a4.z, a4.w);
+                        rot = make_float2(a5.x, a5.y);
+                    }
+                    float2 ph = sb[j * TPP];
 #pragma unroll
-                for (int jj = 0; jj < kB; ++jj) {
-                    eval_x2(acc[jj], cp, kv[jj], ph);
-                    if (jj + 1 < kB) ph = cmul(ph, rot);
+                    for (int jj = 0; jj < kB; ++jj) {
+                        eval_x2(acc[jj], cp, kv[jj], ph);
+                        if (jj + 1 < kB) ph = cmul(ph, rot);
+                    }
+                }
+                // hand the table back: one arrival per consumer warp, after the warp is done
+                __syncwarp();
+                if ((tid & 31) == 0) mbar_arrive(&empty[pb]);
+                if ((c + 1) % flush_ct == 0 || c + 1 == nct) fold_now(c + 1 <= flush_ct);
+            }
+            if (nct == 0) fold_now(true);  // e.g. the rim slot with the rim term off: zeros
+        } else {
+            // ---------------- producers ----------------
+            const int ptid = tid - L::NC;
+            const float d1h = p.dom_hi, d1l = p.dom_lo;
+            const double domB = dom * kB;
+            const float dBh = (float)domB, dBl = (float)(domB - (double)(float)domB);
+            unsigned issued[2] = {0, 0}, waited[2] = {0, 0};
+            if (ptid == 0) {
+                for (int s = 0; s < 2 && s < nt; ++s) {
+                    const int nbi = (int)((tbase + s) & 1);
+                    mbar_expect_tx(&nbar[nbi], kTileBytes);
+                    bulk_g2s(nodebuf + nbi * kTileFloats, p.nodes + (size_t)(t0 + s) * kTileFloats,
+                             kTileBytes, &nbar[nbi]);
+                    issued[nbi]++;
                 }
             }
-            // hand the table back: one arrival per consumer warp, after the warp is done
-            __syncwarp();
-            if ((tid & 31) == 0) mbar_arrive(&empty[pb]);
-            if ((c + 1) % flush_ct == 0 || c + 1 == nct) fold_now(c + 1 <= flush_ct);
-        }
-        if (nct == 0) fold_now(true);  // e.g. the rim slot with the rim term off: zeros
-    } else {
-        // ---------------- producers ----------------
-        const int ptid = tid - L::NC;
-        const float d1h = p.dom_hi, d1l = p.dom_lo;
-        const double domB = dom * kB;
-        const float dBh = (float)domB, dBl = (float)(domB - (double)(float)domB);
-        unsigned issued[2] = {0, 0}, waited[2] = {0, 0};
-        if (ptid == 0) {
-            for (int s = 0; s < 2; ++s) {
-                if (s < nt) {
-                    mbar_expect_tx(&nbar[s], kTileBytes);
-                    bulk_g2s(nodebuf + s * kTileFloats, p.nodes + (size_t)(t0 + s) * kTileFloats,
-                             kTileBytes, &nbar[s]);
-                    issued[s]++;
+            for (int c = 0; c < nct; ++c) {
+                const long long cg = cbase + c;
+                const int pb = (int)(cg & 1);
+                const int it = c / L::CPT, sub = c % L::CPT;
+                const long long tg = tbase + it;
+                const int nbi = (int)(tg & 1);
+                if (sub == 0) {
+                    if (!mbar_wait(&nbar[nbi], (unsigned)((tg >> 1) & 1))) timed_out = true;
+                    if (ptid == 0) waited[nbi]++;
                 }
-            }
-        }
-        for (int c = 0; c < nct; ++c) {
-            const int pb = c & 1;
-            const int it = c / L::CPT, sub = c % L::CPT;
-            const int nb_i = it & 1;
-            if (sub == 0) {
-                if (!mbar_wait(&nbar[nb_i], (unsigned)((it >> 1) & 1))) timed_out = true;
-                if (ptid == 0) waited[nb_i]++;
-            }
-            // the table pb was last used for compute tile c - 2
-            if (c >= 2 && !mbar_wait(&empty[pb], (unsigned)(((c >> 1) - 1) & 1))) timed_out = true;
-            const float* nb = nodebuf + nb_i * kTileFloats;
-            float* cb = coefbuf + (size_t)pb * L::NPAIR * L::COEF;
-            float2* sb = seedbuf + (size_t)pb * L::NPAIR * TPP;
-            for (int i = ptid; i < L::NITEM; i += L::NPROD) {
-                const int q = i / L::SEG, seg = i % L::SEG;
-                const int pq = q / L::TC, j = q % L::TC;
-                float co[10];
-                const float phi = pair_coefs(nb, sub * L::TC + j, spts[pq], co);
-                if (seg == 0) {
-                    const float2 rot = phasor_2wphi(d1h, d1l, phi);
-                    float4* c4 = reinterpret_cast<float4*>(cb + (size_t)q * L::COEF);
-                    c4[0] = make_float4(co[0], co[0], co[1], co[1]);
-                    c4[1] = make_float4(co[2], co[2], co[3], co[3]);
-                    c4[2] = make_float4(co[4], co[4], co[5], co[5]);
-                    c4[3] = make_float4(co[6], co[6], co[7], co[7]);
-                    c4[4] = make_float4(co[8], co[8], -co[9], -co[9]);
-                    c4[5] = make_float4(rot.x, rot.y, 0.f, 0.f);
-                }
-                const int g0 = seg * 32, g1 = min(G, g0 + 32);
-                if (g0 < g1) {
-                    const float2 rotB = phasor_2wphi(dBh, dBl, phi);
-                    float2 sd = make_float2(1.f, 0.f);
-                    for (int gg = g0; gg < g1; ++gg) {
-                        if ((gg & 15) == 0) {
-                            const float2 w = soms[gg >> 4];
-                            sd = phasor_2wphi(w.x, w.y, phi);
-                        } else {
-                            sd = cmul(sd, rotB);
+                // the table pb was last used for compute tile cg - 2
+                if (cg >= 2 && !mbar_wait(&empty[pb], (unsigned)(((cg >> 1) - 1) & 1))) timed_out = true;
+                const float* nb = nodebuf + nbi * kTileFloats;
+                float* cb = coefbuf + (size_t)pb * L::NPAIR * L::COEF;
+                float2* sb = seedbuf + (size_t)pb * L::NPAIR * TPP;
+                for (int i = ptid; i < L::NITEM; i += L::NPROD) {
+                    const int q = i / L::SEG, seg = i % L::SEG;
+                    const int pq = q / L::TC, j = q % L::TC;
+                    float co[10];
+                    const float phi = pair_coefs(nb, sub * L::TC + j, spts[pq], co);
+                    if (seg == 0) {
+                        const float2 rot = phasor_2wphi(d1h, d1l, phi);
+                        float4* c4 = reinterpret_cast<float4*>(cb + (size_t)q * L::COEF);
+                        c4[0] = make_float4(co[0], co[0], co[1], co[1]);
+                        c4[1] = make_float4(co[2], co[2], co[3], co[3]);
+                        c4[2] = make_float4(co[4], co[4], co[5], co[5]);
+                        c4[3] = make_float4(co[6], co[6], co[7], co[7]);
+                        c4[4] = make_float4(co[8], co[8], -co[9], -co[9]);
+                        c4[5] = make_float4(rot.x, rot.y, 0.f, 0.f);
+                    }
+                    const int g0 = seg * 32, g1 = min(G, g0 + 32);
+                    if (g0 < g1) {
+                        const float2 rotB = phasor_2wphi(dBh, dBl, phi);
+                        float2 sd = make_float2(1.f, 0.f);
+                        for (int gg = g0; gg < g1; ++gg) {
+                            if ((gg & 15) == 0) {
+                                const float2 wv = soms[gg >> 4];
+                                sd = phasor_2wphi(wv.x, wv.y, phi);
+                            } else {
+                                sd = cmul(sd, rotB);
+                            }
+                            sb[(size_t)q * TPP + gg] = sd;
                         }
-                        sb[(size_t)q * TPP + gg] = sd;
+                    }
+                }
+                mbar_arrive(&full[pb]);  // release: this thread's table entries are written
+                // node tile it fully read by all producers: refill its buffer with tile it + 2
+                if (sub == L::CPT - 1) {
+                    asm volatile("bar.sync 1, %0;" ::"n"(L::NPROD) : "memory");
+                    if (ptid == 0 && it + 2 < nt) {
+                        fence_proxy_async();
+                        mbar_expect_tx(&nbar[nbi], kTileBytes);
+                        bulk_g2s(nodebuf + nbi * kTileFloats, p.nodes + (size_t)(t0 + it + 2) * kTileFloats,
+                                 kTileBytes, &nbar[nbi]);
+                        issued[nbi]++;
                     }
                 }
             }
-            mbar_arrive(&full[pb]);  // release: this thread's table entries are written
-            // node tile it fully read by all producers: refill its buffer with tile it + 2
-            if (sub == L::CPT - 1) {
-                asm volatile("bar.sync 1, %0;" ::"n"(L::NPROD) : "memory");
-                if (ptid == 0 && it + 2 < nt) {
-                    fence_proxy_async();
-                    mbar_expect_tx(&nbar[nb_i], kTileBytes);
-                    bulk_g2s(nodebuf + nb_i * kTileFloats, p.nodes + (size_t)(t0 + it + 2) * kTileFloats,
-                             kTileBytes, &nbar[nb_i]);
-                    issued[nb_i]++;
-                }
+            // drain: never leave a bulk copy in flight into shared memory that is reused
+            if (ptid == 0) {
+                for (int s = 0; s < 2; ++s)
+                    while (waited[s] < issued[s]) {
+                        // the k-th tile of this item in buffer s has global index first + 2k
+                        const long long first = tbase + ((s - (int)(tbase & 1)) & 1);
+                        if (!mbar_wait(&nbar[s], (unsigned)(((first >> 1) + waited[s]) & 1))) {
+                            timed_out = true;
+                            break;
+                        }
+                        waited[s]++;
+                    }
             }
         }
-        // drain: never leave a bulk copy in flight into freed shared memory
-        if (ptid == 0) {
-            for (int s = 0; s < 2; ++s)
-                while (waited[s] < issued[s]) {
-                    if (!mbar_wait(&nbar[s], waited[s] & 1)) { timed_out = true; break; }
-                    waited[s]++;
-                }
-        }
+        cbase += nct;
+        tbase += nt;
     }
-    if (timed_out) atomicOr(p.err, ERR_TIMEOUT);
+    if (timed_out) atomicOr(b.err, ERR_TIMEOUT);
 }
 
 // ------------------------------------------------------------------------
 // Direct kernel: n_omega <= 8 (a single group).  One thread per point computes
-// every pair itself; the CTA shares the staged node tiles.
+// every pair itself; the CTA shares the staged node tiles.  256 points per item.
 
 template <int NB>
-__global__ void __launch_bounds__(256, 1) field_direct_kernel(FieldLaunch p)
+__global__ void __launch_bounds__(256, 1) field_direct_kernel(BatchLaunch b)
 {
     __shared__ __align__(128) float nodebuf[2 * kTileFloats];
     __shared__ __align__(8) uint64_t bar[2];
+    __shared__ long long slot;
     const int tid = threadIdx.x;
-    const int pt = blockIdx.x * 256 + tid;
-    const int split = blockIdx.y;
-    int t0, t1;
-    split_range(p, split, t0, t1);
-    const double om0 = (double)p.om_hi0 + (double)p.om_lo0;
-    const double dom = (double)p.dom_hi + (double)p.dom_lo;
-    float4 P;
-    load_point(p.pts, p.n_pts, pt, P);
-    float kv[NB];
-#pragma unroll
-    for (int j = 0; j < NB; ++j) kv[j] = (float)(6.283185307179586 * (om0 + (double)j * dom));
-    const float w0h = p.om_hi0, w0l = p.om_lo0, d1h = p.dom_hi, d1l = p.dom_lo;
-
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         mbar_fence_init();
     }
-    __syncthreads();
-    unsigned issued[2] = {0, 0}, waited[2] = {0, 0};
     bool timed_out = false;
-    if (tid == 0) {
-        for (int s = 0; s < 2; ++s)
-            if (t0 + s < t1) {
-                mbar_expect_tx(&bar[s], kTileBytes);
-                bulk_g2s(nodebuf + s * kTileFloats, p.nodes + (size_t)(t0 + s) * kTileFloats,
-                         kTileBytes, &bar[s]);
-                issued[s]++;
+    long long tbase = 0;
+    for (long long item = next_item(b, &slot, -1); item < b.n_items; item = next_item(b, &slot, item)) {
+        const Item w = decode(b, item);
+        const FieldLaunch& p = w.r->f;
+        const int pt = w.pbi * 256 + tid;
+        const int split = w.split;
+        int t0, t1;
+        split_range(p, split, t0, t1);
+        const double om0 = (double)p.om_hi0 + (double)p.om_lo0;
+        const double dom = (double)p.dom_hi + (double)p.dom_lo;
+        float4 P;
+        load_point(p.pts, p.n_pts, pt, P);
+        float kv[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) kv[j] = (float)(6.283185307179586 * (om0 + (double)j * dom));
+        const float w0h = p.om_hi0, w0l = p.om_lo0, d1h = p.dom_hi, d1l = p.dom_lo;
+        const int nt = t1 - t0;
+        unsigned issued[2] = {0, 0}, waited[2] = {0, 0};
+        if (tid == 0) {
+            for (int s = 0; s < 2 && s < nt; ++s) {
+                const int nbi = (int)((tbase + s) & 1);
+                mbar_expect_tx(&bar[nbi], kTileBytes);
+                bulk_g2s(nodebuf + nbi * kTileFloats, p.nodes + (size_t)(t0 + s) * kTileFloats,
+                         kTileBytes, &bar[nbi]);
+                issued[nbi]++;
             }
-    }
-    Acc12 acc[NB];
+        }
+        Acc12 acc[NB];
 #pragma unroll
-    for (int j = 0; j < NB; ++j)
+        for (int j = 0; j < NB; ++j)
 #pragma unroll
-        for (int c = 0; c < kAcc; ++c) acc[j].v[c] = 0.f;
-
-    const int nt = t1 - t0;
-    const bool pt_ok = pt < p.n_pts;
-    const int nb_ok = min(NB, p.n_omega);
-    float2* dst = p.ws + ((size_t)split * p.n_pts + pt) * (size_t)p.n_omega * kAcc;
-    for (int it = 0; it < nt; ++it) {
-        const int nbuf = it & 1;
-        if (!mbar_wait(&bar[nbuf], (unsigned)((it >> 1) & 1))) timed_out = true;
-        if (tid == 0) waited[nbuf]++;
-        const float* nb = nodebuf + nbuf * kTileFloats;
+            for (int c = 0; c < kAcc; ++c) acc[j].v[c] = 0.f;
+        const bool pt_ok = pt < p.n_pts;
+        const int nb_ok = min(NB, p.n_omega);
+        float2* dst = p.ws + ((size_t)split * p.n_pts + pt) * (size_t)p.n_omega * kAcc;
+        for (int it = 0; it < nt; ++it) {
+            const long long tg = tbase + it;
+            const int nbi = (int)(tg & 1);
+            if (!mbar_wait(&bar[nbi], (unsigned)((tg >> 1) & 1))) timed_out = true;
+            if (tid == 0) waited[nbi]++;
+            const float* nb = nodebuf + nbi * kTileFloats;
 #pragma unroll 1
-        for (int j = 0; j < kTile; ++j) {
-            float co[10];
-            const float phi = pair_coefs(nb, j, P, co);
-            float2 ph = phasor_2wphi(w0h, w0l, phi);
-            float2 rot = make_float2(1.f, 0.f);
-            if (NB > 1) rot = phasor_2wphi(d1h, d1l, phi);
+            for (int j = 0; j < kTile; ++j) {
+                float co[10];
+                const float phi = pair_coefs(nb, j, P, co);
+                float2 ph = phasor_2wphi(w0h, w0l, phi);
+                float2 rot = make_float2(1.f, 0.f);
+                if (NB > 1) rot = phasor_2wphi(d1h, d1l, phi);
 #pragma unroll
-            for (int jj = 0; jj < NB; ++jj) {
-                eval_one(acc[jj], co, kv[jj], ph);
-                if (jj + 1 < NB) ph = cmul(ph, rot);
+                for (int jj = 0; jj < NB; ++jj) {
+                    eval_one(acc[jj], co, kv[jj], ph);
+                    if (jj + 1 < NB) ph = cmul(ph, rot);
+                }
+            }
+            if (((it + 1) % p.flush_tiles == 0 || it + 1 == nt) && pt_ok)
+                fold<NB>(dst, acc, nb_ok, it + 1 <= p.flush_tiles);
+            __syncthreads();
+            if (tid == 0 && it + 2 < nt) {
+                fence_proxy_async();
+                mbar_expect_tx(&bar[nbi], kTileBytes);
+                bulk_g2s(nodebuf + nbi * kTileFloats, p.nodes + (size_t)(t0 + it + 2) * kTileFloats,
+                         kTileBytes, &bar[nbi]);
+                issued[nbi]++;
             }
         }
-        if (((it + 1) % p.flush_tiles == 0 || it + 1 == nt) && pt_ok)
-            fold<NB>(dst, acc, nb_ok, it + 1 <= p.flush_tiles);
-        __syncthreads();
-        if (tid == 0 && it + 2 < nt) {
-            fence_proxy_async();
-            mbar_expect_tx(&bar[nbuf], kTileBytes);
-            bulk_g2s(nodebuf + nbuf * kTileFloats, p.nodes + (size_t)(t0 + it + 2) * kTileFloats,
-                     kTileBytes, &bar[nbuf]);
-            issued[nbuf]++;
+        if (tid == 0) {
+            for (int s = 0; s < 2; ++s)
+                while (waited[s] < issued[s]) {
+                    const long long first = tbase + ((s - (int)(tbase & 1)) & 1);
+                    if (!mbar_wait(&bar[s], (unsigned)(((first >> 1) + waited[s]) & 1))) {
+                        timed_out = true;
+                        break;
+                    }
+                    waited[s]++;
+                }
         }
+        if (nt == 0 && pt_ok) fold<NB>(dst, acc, nb_ok, true);
+        tbase += nt;
     }
-    if (timed_out) atomicOr(p.err, ERR_TIMEOUT);
-    if (tid == 0) {
-        for (int s = 0; s < 2; ++s)
-            while (waited[s] < issued[s]) {
-                if (!mbar_wait(&bar[s], waited[s] & 1)) { atomicOr(p.err, ERR_TIMEOUT); break; }
-                waited[s]++;
-            }
-    }
-    if (nt == 0 && pt_ok) fold<NB>(dst, acc, nb_ok, true);
+    if (timed_out) atomicOr(b.err, ERR_TIMEOUT);
 }
 
 // ------------------------------------------------------------------------
 // FP64 cross-split reduction and epilogue.
 
-__global__ void reduce_kernel(ReduceLaunch r)
+__device__ __forceinline__ void reduce_one(const ReduceLaunch& r, long long idx)
 {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long total = (long long)r.n_pts * r.n_omega;
-    if (idx >= total) return;
     const int pt = (int)(idx / r.n_omega), n = (int)(idx % r.n_omega);
     double s[kAcc];
 #pragma unroll
@@ -670,55 +744,28 @@ __global__ void reduce_kernel(ReduceLaunch r)
     }
 }
 
-template <int TPP>
-int launch_grouped(const FieldLaunch& p, cudaStream_t s)
+__global__ void reduce_kernel(ReduceLaunch r)
 {
-    using L = Grouped<TPP>;
-    auto kern = field_grouped_kernel<TPP>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)L::SMEM);
-    if (e != cudaSuccess) return -(int)e;
-    dim3 grid((p.n_pts + L::PPC - 1) / L::PPC, p.n_splits + 1);
-    kern<<<grid, L::NT, L::SMEM, s>>>(p);
-    e = cudaGetLastError();
-    return e == cudaSuccess ? 1 : -(int)e;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)r.n_pts * r.n_omega) return;
+    reduce_one(r, idx);
 }
 
-template <int NB>
-int launch_direct(const FieldLaunch& p, cudaStream_t s)
+__global__ void reduce_batch_kernel(const ReduceLaunch* reqs, int n_req, long long total)
 {
-    dim3 grid((p.n_pts + 255) / 256, p.n_splits + 1);
-    field_direct_kernel<NB><<<grid, 256, 0, s>>>(p);
-    cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? 1 : -(int)e;
-}
-
-}  // namespace
-
-int launch_field_f32(const FieldLaunch& p, cudaStream_t s)
-{
-    if (p.n_omega <= 8) {
-        switch (p.n_omega) {
-        case 1: return launch_direct<1>(p, s);
-        case 2: return launch_direct<2>(p, s);
-        case 3:
-        case 4: return launch_direct<4>(p, s);
-        default: return launch_direct<8>(p, s);
-        }
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    int lo = 0, hi = n_req - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (reqs[mid].off <= idx) lo = mid; else hi = mid - 1;
     }
-    const int G = (p.n_omega + kB - 1) / kB;
-    if (G <= 2) return launch_grouped<2>(p, s);
-    if (G <= 4) return launch_grouped<4>(p, s);
-    if (G <= 8) return launch_grouped<8>(p, s);
-    if (G <= 16) return launch_grouped<16>(p, s);
-    if (G <= 32) return launch_grouped<32>(p, s);
-    if (G <= 64) return launch_grouped<64>(p, s);
-    if (G <= 128) return launch_grouped<128>(p, s);
-    if (G <= 256) return launch_grouped<256>(p, s);
-    return -(int)cudaErrorInvalidValue;
+    const ReduceLaunch& r = reqs[lo];
+    reduce_one(r, idx - r.off);
 }
 
-namespace {
+// ------------------------------------------------------------------------
+// Launchers and shapes
 
 template <typename K>
 int resident(K kern, int threads, size_t smem, int device)
@@ -734,6 +781,26 @@ int resident(K kern, int threads, size_t smem, int device)
 }
 
 template <int TPP>
+int launch_grouped(const BatchLaunch& b, int grid, cudaStream_t s)
+{
+    using L = Grouped<TPP>;
+    auto kern = field_grouped_kernel<TPP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::SMEM);
+    if (e != cudaSuccess) return -(int)e;
+    kern<<<grid, L::NT, L::SMEM, s>>>(b);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? 1 : -(int)e;
+}
+
+template <int NB>
+int launch_direct(const BatchLaunch& b, int grid, cudaStream_t s)
+{
+    field_direct_kernel<NB><<<grid, 256, 0, s>>>(b);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? 1 : -(int)e;
+}
+
+template <int TPP>
 void grouped_shape(int device, int* ppc, int* slots)
 {
     using L = Grouped<TPP>;
@@ -743,27 +810,74 @@ void grouped_shape(int device, int* ppc, int* slots)
 
 }  // namespace
 
-void field_shape(int n_omega, int device, int* ppc, int* slots)
+int field_class(int n_omega)
 {
-    if (n_omega <= 8) {
-        *ppc = 256;
-        switch (n_omega) {
-        case 1: *slots = resident(field_direct_kernel<1>, 256, 0, device); return;
-        case 2: *slots = resident(field_direct_kernel<2>, 256, 0, device); return;
-        case 3:
-        case 4: *slots = resident(field_direct_kernel<4>, 256, 0, device); return;
-        default: *slots = resident(field_direct_kernel<8>, 256, 0, device); return;
-        }
-    }
+    if (n_omega <= 1) return 0;
+    if (n_omega <= 2) return 1;
+    if (n_omega <= 4) return 2;
+    if (n_omega <= 8) return 3;
     const int G = (n_omega + kB - 1) / kB;
-    if (G <= 2) return grouped_shape<2>(device, ppc, slots);
-    if (G <= 4) return grouped_shape<4>(device, ppc, slots);
-    if (G <= 8) return grouped_shape<8>(device, ppc, slots);
-    if (G <= 16) return grouped_shape<16>(device, ppc, slots);
-    if (G <= 32) return grouped_shape<32>(device, ppc, slots);
-    if (G <= 64) return grouped_shape<64>(device, ppc, slots);
-    if (G <= 128) return grouped_shape<128>(device, ppc, slots);
-    return grouped_shape<256>(device, ppc, slots);
+    int cls = 4, tpp = 2;
+    while (tpp < G) { tpp *= 2; ++cls; }
+    return cls;  // 4: TPP 2 ... 11: TPP 256
+}
+
+void field_shape(int cls, int device, int* ppc, int* slots)
+{
+    switch (cls) {
+    case 0: *ppc = 256; *slots = resident(field_direct_kernel<1>, 256, 0, device); return;
+    case 1: *ppc = 256; *slots = resident(field_direct_kernel<2>, 256, 0, device); return;
+    case 2: *ppc = 256; *slots = resident(field_direct_kernel<4>, 256, 0, device); return;
+    case 3: *ppc = 256; *slots = resident(field_direct_kernel<8>, 256, 0, device); return;
+    case 4: return grouped_shape<2>(device, ppc, slots);
+    case 5: return grouped_shape<4>(device, ppc, slots);
+    case 6: return grouped_shape<8>(device, ppc, slots);
+    case 7: return grouped_shape<16>(device, ppc, slots);
+    case 8: return grouped_shape<32>(device, ppc, slots);
+    case 9: return grouped_shape<64>(device, ppc, slots);
+    case 10: return grouped_shape<128>(device, ppc, slots);
+    default: return grouped_shape<256>(device, ppc, slots);
+    }
+}
+
+int launch_field_batch(int cls, const BatchLaunch& b, int grid, cudaStream_t s)
+{
+    if (grid < 1) return 0;
+    switch (cls) {
+    case 0: return launch_direct<1>(b, grid, s);
+    case 1: return launch_direct<2>(b, grid, s);
+    case 2: return launch_direct<4>(b, grid, s);
+    case 3: return launch_direct<8>(b, grid, s);
+    case 4: return launch_grouped<2>(b, grid, s);
+    case 5: return launch_grouped<4>(b, grid, s);
+    case 6: return launch_grouped<8>(b, grid, s);
+    case 7: return launch_grouped<16>(b, grid, s);
+    case 8: return launch_grouped<32>(b, grid, s);
+    case 9: return launch_grouped<64>(b, grid, s);
+    case 10: return launch_grouped<128>(b, grid, s);
+    case 11: return launch_grouped<256>(b, grid, s);
+    default: return -(int)cudaErrorInvalidValue;
+    }
+}
+
+int launch_field_f32(const FieldLaunch& p, cudaStream_t s)
+{
+    const int cls = field_class(p.n_omega);
+    int ppc = 1, slots = 1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    field_shape(cls, dev, &ppc, &slots);
+    BatchLaunch b{};
+    b.reqs = nullptr;
+    b.one.f = p;
+    b.one.pb = (p.n_pts + ppc - 1) / ppc;
+    b.one.cls = cls;
+    b.one.item0 = 0;
+    b.n_req = 1;
+    b.n_items = (long long)b.one.pb * (p.n_splits + 1);
+    b.queue = nullptr;
+    b.err = p.err;
+    return launch_field_batch(cls, b, (int)b.n_items, s);
 }
 
 int launch_reduce_f32(const ReduceLaunch& r, cudaStream_t s)
@@ -771,6 +885,14 @@ int launch_reduce_f32(const ReduceLaunch& r, cudaStream_t s)
     const long long total = (long long)r.n_pts * r.n_omega;
     const int nb = (int)((total + 255) / 256);
     reduce_kernel<<<nb, 256, 0, s>>>(r);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? 1 : -(int)e;
+}
+
+int launch_reduce_batch(const ReduceLaunch* reqs, int n_req, long long total, cudaStream_t s)
+{
+    if (total <= 0) return 0;
+    reduce_batch_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(reqs, n_req, total);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? 1 : -(int)e;
 }

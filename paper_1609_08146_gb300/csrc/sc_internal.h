@@ -52,13 +52,41 @@ struct FieldLaunch {
     int* err;               // device error word
 };
 
-// FP32 field sum.  Returns the number of kernels launched (>= 1) or a
-// negative cudaError_t.
-int launch_field_f32(const FieldLaunch& p, cudaStream_t s);
+// One request (or one chunk of a request) of a batched field-sum launch:
+// work items are (point block, split) pairs, point blocks fastest, numbered
+// from item0.
+struct WorkReq {
+    FieldLaunch f;
+    int pb;                 // point blocks of f.n_pts
+    int cls;                // kernel class (field_class)
+    long long item0;        // first global item of this request
+};
 
-// Launch shape of the FP32 field sum for n_omega omegas in one launch:
-// observation points per CTA and concurrently resident CTAs on the device.
-void field_shape(int n_omega, int device, int* points_per_cta, int* resident_ctas);
+// A launch over many requests of one kernel class.  Queue mode: reqs is a
+// device array sorted by item0 and CTAs take items from *queue (reset to 0
+// before the launch).  Grid mode (reqs == nullptr): the single request `one`,
+// item = blockIdx.x, grid = n_items.
+struct BatchLaunch {
+    const WorkReq* reqs;
+    WorkReq one;
+    int n_req;
+    long long n_items;
+    int* queue;
+    int* err;
+};
+
+// Kernel class for a chunk of n_omega (<= 2048) omegas: 0..3 direct kernel
+// with 1, 2, 4, 8 omegas per thread; 4 + log2(TPP/2) grouped kernel.
+int field_class(int n_omega);
+// Observation points per work item and resident CTAs on the device.
+void field_shape(int cls, int device, int* points_per_item, int* resident_ctas);
+// Launch one class; grid = CTAs (queue mode: resident slots; grid mode:
+// n_items).  Returns kernels launched (1) or a negative cudaError_t.
+int launch_field_batch(int cls, const BatchLaunch& b, int grid, cudaStream_t s);
+
+// Single-request FP32 field sum in grid mode (no device descriptor, no
+// queue).  Returns kernels launched or a negative cudaError_t.
+int launch_field_f32(const FieldLaunch& p, cudaStream_t s);
 
 // FP64 cross-split reduction and epilogue: E = a_n (S_E + (i/k_n) S_rim),
 // B = a_n S_B, written as float2 into out[n_omega_total][n_pts_total][3]
@@ -72,8 +100,12 @@ struct ReduceLaunch {
     float2* E;              // output base (already offset to the chunk)
     float2* B;              // nullable
     long long out_pt_stride_omega;  // n_pts_total * 3
+    long long off;          // prefix of n_pts * n_omega over a batch
 };
 int launch_reduce_f32(const ReduceLaunch& p, cudaStream_t s);
+// Reduction of many requests in one launch: reqs is a device array sorted
+// by off, total = sum of n_pts * n_omega.
+int launch_reduce_batch(const ReduceLaunch* reqs, int n_req, long long total, cudaStream_t s);
 
 // Plain FP64 path: direct sincos per (point, node, omega).
 struct Field64Launch {
