@@ -287,6 +287,44 @@ typedef struct {
 sc_status sc_eval_batch(sc_ctx* ctx, const sc_request* reqs, int n_req, sc_eval_stats* stats);
 
 /* ---------------------------------------------------------------------- */
+/* Serving: continuous batching of submitted requests                       */
+/*
+ * A server thread (started by the first sc_submit) admits queued requests in
+ * arrival order while the device memory they need fits the context's HBM
+ * budget (staged points and, for requests without outputs, the outputs the
+ * server allocates), batches up to 64 of them and runs each batch as
+ * sc_eval_batch does on one of two lanes (streams with their own buffers), so
+ * a batch starts while the previous one is still on the GPU.  Node tables
+ * stay resident between requests.  The paper has one problem per run; this
+ * is the serving pattern of the hot path.
+ *
+ * sc_submit   req->points_xyz host (copied) or device (kept by reference);
+ *             req->E_out/B_out NULL: server-owned outputs, read them with
+ *             sc_fetch; else caller-owned device outputs (float2 layout of
+ *             sc_eval).  Caller-owned buffers must stay valid until done.
+ *             SC_ERR_BUSY: the request alone exceeds the budget.
+ * sc_poll     *done = 1 once finished, failed or cancelled (the status says
+ *             which: SC_OK, the failure, or SC_ERR_CANCELLED).
+ * sc_wait     blocks up to timeout_s; SC_ERR_TIMEOUT if still running.
+ * sc_cancel   drops a queued request, or discards a running one's result.
+ * sc_fetch    copies a finished request's E, B (host or device dst, either
+ *             nullable) and synchronizes.
+ * sc_release  frees the ticket and its server-owned memory (SC_ERR_BUSY
+ *             while its batch runs); memory returns to the admission budget.
+ * sc_ticket_times  seconds since the server started: submitted, started on
+ *             the GPU, observed finished (latency = t_done - t_submit).
+ * Errors: SC_ERR_NOT_FOUND for unknown tickets; others as sc_eval.
+ */
+sc_status sc_submit(sc_ctx* ctx, const sc_request* req, uint64_t* ticket);
+sc_status sc_poll(sc_ctx* ctx, uint64_t ticket, int* done);
+sc_status sc_wait(sc_ctx* ctx, uint64_t ticket, double timeout_s);
+sc_status sc_cancel(sc_ctx* ctx, uint64_t ticket);
+sc_status sc_fetch(sc_ctx* ctx, uint64_t ticket, void* E_dst, void* B_dst);
+sc_status sc_release(sc_ctx* ctx, uint64_t ticket);
+sc_status sc_ticket_times(sc_ctx* ctx, uint64_t ticket, double* t_submit, double* t_start,
+                          double* t_done);
+
+/* ---------------------------------------------------------------------- */
 /* Counters (measurement)                                                  */
 
 typedef struct {

@@ -94,6 +94,13 @@ SIGNATURES = {
                                            ctypes.c_int, _DP, _VP, ctypes.c_int, _VP, _VP]),
     "sc_eval_batch": (ctypes.c_int, [_VP, ctypes.POINTER(sc_request), ctypes.c_int,
                                      ctypes.POINTER(sc_eval_stats)]),
+    "sc_submit": (ctypes.c_int, [_VP, ctypes.POINTER(sc_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "sc_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
+    "sc_wait": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_double]),
+    "sc_cancel": (ctypes.c_int, [_VP, ctypes.c_uint64]),
+    "sc_fetch": (ctypes.c_int, [_VP, ctypes.c_uint64, _VP, _VP]),
+    "sc_release": (ctypes.c_int, [_VP, ctypes.c_uint64]),
+    "sc_ticket_times": (ctypes.c_int, [_VP, ctypes.c_uint64, _DP, _DP, _DP]),
     "sc_get_counters": (ctypes.c_int, [_VP, ctypes.POINTER(sc_counters)]),
     "sc_reset_counters": (ctypes.c_int, [_VP]),
     "sc_set_option": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_longlong]),
@@ -330,6 +337,61 @@ class Context:
             return outs, dict(evals=st.evals, field_ms=st.field_ms, total_ms=st.total_ms,
                               launches=st.launches)
         return outs
+
+    # ---- serving
+    def submit(self, mirror, inc, omegas, points, out=None):
+        """Queue one request; returns its ticket.  points: numpy (host,
+        copied) or cuda tensor (kept by reference); out: optional (E, B)
+        caller-owned complex64 cuda tensors, else server-owned outputs."""
+        om = np.ascontiguousarray(np.atleast_1d(omegas), dtype=np.float64)
+        if isinstance(points, np.ndarray):
+            pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+            paddr, n = pts.ctypes.data, pts.shape[0]
+        else:
+            pts = points.contiguous()
+            paddr, n = pts.data_ptr(), pts.shape[0]
+        E = B = None
+        if out is not None:
+            E, B = out
+        req = sc_request(mirror._h, inc._h, _dptr(om), om.size, _VP(paddr), n,
+                         _VP(E.data_ptr()) if E is not None else None,
+                         _VP(B.data_ptr()) if B is not None else None)
+        t = ctypes.c_uint64()
+        self._check(self._lib.sc_submit(self._h, ctypes.byref(req), ctypes.byref(t)))
+        self._serving_keep = getattr(self, "_serving_keep", {})
+        self._serving_keep[t.value] = (om, pts, E, B, n)
+        return t.value
+
+    def poll(self, ticket) -> bool:
+        d = ctypes.c_int()
+        self._check(self._lib.sc_poll(self._h, ticket, ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket, timeout_s: float = 60.0):
+        self._check(self._lib.sc_wait(self._h, ticket, float(timeout_s)))
+
+    def cancel(self, ticket):
+        self._check(self._lib.sc_cancel(self._h, ticket))
+
+    def fetch(self, ticket, device="cuda"):
+        """Results of a finished request as complex64 tensors [n_omega, n, 3]."""
+        import torch
+
+        om, _, _, _, n = self._serving_keep[ticket]
+        E = torch.empty((om.size, n, 3), dtype=torch.complex64, device=device)
+        B = torch.empty_like(E)
+        self._check(self._lib.sc_fetch(self._h, ticket, _VP(E.data_ptr()), _VP(B.data_ptr())))
+        return E, B
+
+    def release(self, ticket):
+        self._check(self._lib.sc_release(self._h, ticket))
+        getattr(self, "_serving_keep", {}).pop(ticket, None)
+
+    def ticket_times(self, ticket):
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.sc_ticket_times(self._h, ticket, ctypes.byref(a), ctypes.byref(b),
+                                              ctypes.byref(c)))
+        return a.value, b.value, c.value
 
     def counters(self):
         c = sc_counters()

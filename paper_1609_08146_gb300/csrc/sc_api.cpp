@@ -11,7 +11,12 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
 #include <list>
+#include <mutex>
+#include <thread>
 #include <map>
 #include <string>
 #include <tuple>
@@ -64,7 +69,28 @@ struct Table {
     int n_surf = 0, n_rim = 0;
     size_t bytes = 0;
     uint64_t last_use = 0;
+    int inflight = 0;              // serving batches on the GPU that read this table
 };
+
+struct GraphEntry {
+    std::vector<unsigned char> sig;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t last = 0;
+};
+
+// An execution lane of the FP32 path: a stream and the device buffers and
+// graph cache that one batch in flight needs.  The context's own calls use
+// lane `main` (on the caller's stream); the serving loop owns more lanes so
+// that batches overlap on the GPU.
+struct Lane {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    DevBuf ws, desc, amp, kval;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<GraphEntry> graphs;
+};
+
+struct Server;
 
 }  // namespace
 
@@ -76,7 +102,7 @@ struct sc_ctx {
     std::string err = "no error";
     std::list<Table> tables;
     uint64_t tick = 0;
-    DevBuf ws, pts, outE, outB, amp, kval, tvals, phasor, specE, specB, tE, tB;
+    DevBuf pts, outE, outB, tkval, tvals, phasor, specE, specB, tE, tB;
     int* d_err = nullptr;
     int* h_err = nullptr;          // pinned
     sc_counters ctr{};
@@ -86,20 +112,15 @@ struct sc_ctx {
     size_t ws_cap = size_t(2) << 30;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
     std::vector<cudaEvent_t> pool;
-    // batched execution: descriptor arena, graph cache, split autotuner
-    DevBuf desc;
-    cudaStream_t cap_stream = nullptr;
+    // batched execution: lanes, graph counters, split autotuner, serving
+    Lane main;
     bool use_graphs = true;
     bool autotune = true;
-    struct GraphEntry {
-        std::vector<unsigned char> sig;
-        cudaGraphExec_t exec = nullptr;
-        uint64_t last = 0;
-    };
-    std::vector<GraphEntry> graphs;
     uint64_t graph_tick = 0;
     uint64_t graph_captures = 0, graph_replays = 0;
     std::map<std::tuple<int, int, int, int, int>, int> tuned;  // shape -> split count
+    std::mutex mu;                                              // guards all of the above
+    Server* server = nullptr;
 };
 
 namespace {
@@ -127,7 +148,14 @@ sc_status cuda_fail(sc_ctx* c, cudaError_t e, const char* what)
         if (e__ != cudaSuccess) return cuda_fail(ctx, e__, what); \
     } while (0)
 
+sc_status ensure(sc_ctx* ctx, DevBuf& b, size_t bytes, cudaStream_t sync_stream);
+
 sc_status ensure(sc_ctx* ctx, DevBuf& b, size_t bytes)
+{
+    return ensure(ctx, b, bytes, ctx->stream);
+}
+
+sc_status ensure(sc_ctx* ctx, DevBuf& b, size_t bytes, cudaStream_t sync_stream)
 {
     if (b.n >= bytes) return SC_OK;
     size_t want = std::max(bytes, b.n + b.n / 2);
@@ -138,7 +166,7 @@ sc_status ensure(sc_ctx* ctx, DevBuf& b, size_t bytes)
                         ctx->budget, want);
     }
     if (b.p) {
-        cudaStreamSynchronize(ctx->stream);
+        cudaStreamSynchronize(sync_stream);
         cudaFree(b.p);
         ctx->held -= b.n;
         b.p = nullptr;
@@ -451,7 +479,8 @@ void free_table(sc_ctx* ctx, Table& t)
 
 // Look up or build the table of (m, in).  Public calls advance ctx->tick once;
 // tables touched by the current call carry that tick and are never evicted by it.
-sc_status get_table(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, Table** out)
+sc_status get_table(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, Table** out,
+                    cudaStream_t stream)
 {
     for (auto& t : ctx->tables)
         if (t.mid == m->id && t.iid == in->id) {
@@ -475,10 +504,13 @@ sc_status get_table(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, 
     // evict least recently used tables while over budget
     while (ctx->budget && ctx->held + t.bytes > ctx->budget && !ctx->tables.empty()) {
         // evict the least recently used table that no call in flight on the host uses
-        auto it = std::min_element(ctx->tables.begin(), ctx->tables.end(),
-                                   [](const Table& a, const Table& b) { return a.last_use < b.last_use; });
-        if (it->last_use == ctx->tick) break;
-        cudaStreamSynchronize(ctx->stream);
+        auto it = ctx->tables.end();
+        for (auto jt = ctx->tables.begin(); jt != ctx->tables.end(); ++jt)
+            if (jt->inflight == 0 && jt->last_use != ctx->tick &&
+                (it == ctx->tables.end() || jt->last_use < it->last_use))
+                it = jt;
+        if (it == ctx->tables.end()) break;
+        cudaDeviceSynchronize();
         free_table(ctx, *it);
         ctx->tables.erase(it);
     }
@@ -497,14 +529,14 @@ sc_status get_table(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, 
         for (const auto& nd : *vec)
             h64.push_back(sc::Node64{nd.px, nd.py, nd.pz, nd.pn, nd.w, nd.jx, nd.jy, nd.jz, nd.rho, 0.0});
     SC_CUDA(cudaMemcpyAsync(t.d32, ts.data(), ts.size() * sizeof(float), cudaMemcpyHostToDevice,
-                            ctx->stream), "upload node table");
+                            stream), "upload node table");
     if (!tr.empty())
         SC_CUDA(cudaMemcpyAsync(t.d32 + ts.size(), tr.data(), tr.size() * sizeof(float),
-                                cudaMemcpyHostToDevice, ctx->stream), "upload rim table");
-    SC_CUDA(cudaMemcpyAsync(t.d64, h64.data(), b64, cudaMemcpyHostToDevice, ctx->stream),
+                                cudaMemcpyHostToDevice, stream), "upload rim table");
+    SC_CUDA(cudaMemcpyAsync(t.d64, h64.data(), b64, cudaMemcpyHostToDevice, stream),
             "upload FP64 table");
     // the host vectors die at return: make the copies complete first
-    SC_CUDA(cudaStreamSynchronize(ctx->stream), "node table upload");
+    SC_CUDA(cudaStreamSynchronize(stream), "node table upload");
     ctx->held += t.bytes;
     t.last_use = ctx->tick;
     ctx->tables.push_back(t);
@@ -614,10 +646,10 @@ int heuristic_splits(int tiles, long long pb, int slots)
     return (int)std::max<long long>(1, std::min<long long>(64, s));
 }
 
-sc_status launch_chunks_direct(sc_ctx* ctx, std::vector<Chunk>& ch, float2* ws, size_t ws_n);
+sc_status launch_chunks_direct(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch, float2* ws, size_t ws_n);
 
 // Time one chunk with split count S (the chunk's outputs are overwritten later).
-float time_chunk(sc_ctx* ctx, Chunk c, int S, const Table* tab, float2* ws)
+float time_chunk(sc_ctx* ctx, Lane& ln, Chunk c, int S, const Table* tab, float2* ws)
 {
     const int tps = (tab->n_surf_tiles + S - 1) / S;
     c.f.tiles_per_split = tps;
@@ -626,9 +658,9 @@ float time_chunk(sc_ctx* ctx, Chunk c, int S, const Table* tab, float2* ws)
     c.ws_elems = (size_t)(c.f.n_splits + 1) * c.f.n_pts * c.f.n_omega * sc::kAcc;
     std::vector<Chunk> one{c};
     cudaEvent_t a = take_event(ctx), b = take_event(ctx);
-    cudaEventRecord(a, ctx->stream);
-    sc_status st = launch_chunks_direct(ctx, one, ws, c.ws_elems);
-    cudaEventRecord(b, ctx->stream);
+    cudaEventRecord(a, ln.stream);
+    sc_status st = launch_chunks_direct(ctx, ln, one, ws, c.ws_elems);
+    cudaEventRecord(b, ln.stream);
     float ms = 1e30f;
     if (st == SC_OK && cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
     cudaGetLastError();
@@ -639,7 +671,7 @@ float time_chunk(sc_ctx* ctx, Chunk c, int S, const Table* tab, float2* ws)
 
 // Split count for a chunk shape: explicit option, tuned value, or heuristic
 // (tuned on first sight when the autotuner is on).
-sc_status choose_splits(sc_ctx* ctx, Chunk& c, const Table* tab, int slots, int* S_out)
+sc_status choose_splits(sc_ctx* ctx, Lane& ln, Chunk& c, const Table* tab, int slots, int* S_out)
 {
     const int tiles = tab->n_surf_tiles;
     if (ctx->nodes_per_split > 0) {
@@ -675,11 +707,11 @@ sc_status choose_splits(sc_ctx* ctx, Chunk& c, const Table* tab, int slots, int*
             }
         }
         if (fit.size() > 1) {
-            sc_status st = ensure(ctx, ctx->ws, need * sizeof(float2));
+            sc_status st = ensure(ctx, ln.ws, need * sizeof(float2), ln.stream);
             if (st != SC_OK) return st;
             float best_ms = 1e30f;
             for (int s : fit) {
-                const float ms = time_chunk(ctx, c, s, tab, (float2*)ctx->ws.p);
+                const float ms = time_chunk(ctx, ln, c, s, tab, (float2*)ln.ws.p);
                 if (ms < best_ms) { best_ms = ms; best = s; }
             }
         }
@@ -690,7 +722,7 @@ sc_status choose_splits(sc_ctx* ctx, Chunk& c, const Table* tab, int slots, int*
 }
 
 // Cut one request into chunks.  d_amp / d_k point at this request's a_n, k_n.
-sc_status plan_request(sc_ctx* ctx, const Table* tab, const double* omegas, int n_omega,
+sc_status plan_request(sc_ctx* ctx, Lane& ln, const Table* tab, const double* omegas, int n_omega,
                        double dom, const double* d_pts, int n_points, const double* d_amp,
                        const double* d_k, float2* dE, float2* dB, std::vector<Chunk>& out)
 {
@@ -726,7 +758,7 @@ sc_status plan_request(sc_ctx* ctx, const Table* tab, const double* omegas, int 
         c.rl.n_pts = n_points;
         c.rl.n_omega = no;
         int S = 1;
-        sc_status st = choose_splits(ctx, c, tab, slots, &S);
+        sc_status st = choose_splits(ctx, ln, c, tab, slots, &S);
         if (st != SC_OK) return st;
         int tps = (tab->n_surf_tiles + S - 1) / S;
         const int n_splits = (tab->n_surf_tiles + tps - 1) / tps;
@@ -756,7 +788,7 @@ sc_status plan_request(sc_ctx* ctx, const Table* tab, const double* omegas, int 
 // Launch a group of chunks whose workspaces fit in ws, with or without a
 // CUDA graph.  Field kernels (one persistent launch per class present) go
 // in the graph; the batched reduce follows on the stream.
-sc_status launch_chunks(sc_ctx* ctx, std::vector<Chunk>& ch, float2* ws, size_t ws_n, bool graph)
+sc_status launch_chunks(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch, float2* ws, size_t ws_n, bool graph)
 {
     // workspace offsets and reduce offsets
     size_t off = 0;
@@ -793,15 +825,15 @@ sc_status launch_chunks(sc_ctx* ctx, std::vector<Chunk>& ch, float2* ws, size_t 
     }
     const size_t rl_off = bytes;
     bytes += rls.size() * sizeof(sc::ReduceLaunch);
-    sc_status st = ensure(ctx, ctx->desc, bytes);
+    sc_status st = ensure(ctx, ln.desc, bytes, ln.stream);
     if (st != SC_OK) return st;
-    unsigned char* arena = (unsigned char*)ctx->desc.p;
+    unsigned char* arena = (unsigned char*)ln.desc.p;
     for (int k = 0; k < kClasses; ++k)
         if (!reqs[k].empty())
             SC_CUDA(cudaMemcpyAsync(arena + req_off[k], reqs[k].data(), reqs[k].size() * sizeof(sc::WorkReq),
-                                    cudaMemcpyHostToDevice, ctx->stream), "upload work descriptors");
+                                    cudaMemcpyHostToDevice, ln.stream), "upload work descriptors");
     SC_CUDA(cudaMemcpyAsync(arena + rl_off, rls.data(), rls.size() * sizeof(sc::ReduceLaunch),
-                            cudaMemcpyHostToDevice, ctx->stream), "upload reduce descriptors");
+                            cudaMemcpyHostToDevice, ln.stream), "upload reduce descriptors");
 
     struct L { int cls; sc::BatchLaunch b; int grid; };
     std::vector<L> launches;
@@ -829,7 +861,7 @@ sc_status launch_chunks(sc_ctx* ctx, std::vector<Chunk>& ch, float2* ws, size_t 
     if (ctx->time_field) {
         f0 = take_event(ctx);
         f1 = take_event(ctx);
-        cudaEventRecord(f0, ctx->stream);
+        cudaEventRecord(f0, ln.stream);
     }
     if (graph) {
         // signature: everything the captured launches depend on
@@ -845,19 +877,19 @@ sc_status launch_chunks(sc_ctx* ctx, std::vector<Chunk>& ch, float2* ws, size_t 
             put(&l.b, sizeof l.b);
         }
         cudaGraphExec_t exec = nullptr;
-        for (auto& g : ctx->graphs)
+        for (auto& g : ln.graphs)
             if (g.sig == sig) {
                 exec = g.exec;
                 g.last = ++ctx->graph_tick;
                 ctx->graph_replays++;
             }
         if (!exec) {
-            if (!ctx->cap_stream)
-                SC_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking), "capture stream");
-            SC_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed), "begin capture");
-            st = issue(ctx->cap_stream);
+            if (!ln.cap_stream)
+                SC_CUDA(cudaStreamCreateWithFlags(&ln.cap_stream, cudaStreamNonBlocking), "capture stream");
+            SC_CUDA(cudaStreamBeginCapture(ln.cap_stream, cudaStreamCaptureModeRelaxed), "begin capture");
+            st = issue(ln.cap_stream);
             cudaGraph_t g = nullptr;
-            cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+            cudaError_t e = cudaStreamEndCapture(ln.cap_stream, &g);
             if (st != SC_OK) {
                 if (g) cudaGraphDestroy(g);
                 return st;
@@ -866,60 +898,328 @@ sc_status launch_chunks(sc_ctx* ctx, std::vector<Chunk>& ch, float2* ws, size_t 
             e = cudaGraphInstantiate(&exec, g, 0);
             cudaGraphDestroy(g);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
-            if (ctx->graphs.size() >= 8) {
-                auto it = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
-                                           [](const sc_ctx::GraphEntry& a, const sc_ctx::GraphEntry& b) {
+            if (ln.graphs.size() >= 8) {
+                auto it = std::min_element(ln.graphs.begin(), ln.graphs.end(),
+                                           [](const GraphEntry& a, const GraphEntry& b) {
                                                return a.last < b.last;
                                            });
                 cudaGraphExecDestroy(it->exec);
-                ctx->graphs.erase(it);
+                ln.graphs.erase(it);
             }
-            ctx->graphs.push_back({sig, exec, ++ctx->graph_tick});
+            ln.graphs.push_back({sig, exec, ++ctx->graph_tick});
             ctx->graph_captures++;
         }
-        SC_CUDA(cudaGraphLaunch(exec, ctx->stream), "graph launch");
+        SC_CUDA(cudaGraphLaunch(exec, ln.stream), "graph launch");
     } else {
-        st = issue(ctx->stream);
+        st = issue(ln.stream);
         if (st != SC_OK) return st;
     }
     if (ctx->time_field) {
-        cudaEventRecord(f1, ctx->stream);
+        cudaEventRecord(f1, ln.stream);
         ctx->pending.push_back({f0, f1});
     }
     ctx->ctr.launches += launches.size();
     ctx->ctr.field_launches += launches.size();
     const int r = sc::launch_reduce_batch((const sc::ReduceLaunch*)(arena + rl_off), (int)rls.size(),
-                                          roff, ctx->stream);
+                                          roff, ln.stream);
     if (r < 0) return cuda_fail(ctx, (cudaError_t)(-r), "reduce launch");
     ctx->ctr.launches += r;
     return SC_OK;
 }
 
-sc_status launch_chunks_direct(sc_ctx* ctx, std::vector<Chunk>& ch, float2* ws, size_t ws_n)
+sc_status launch_chunks_direct(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch, float2* ws, size_t ws_n)
 {
     const bool t = ctx->time_field;
     ctx->time_field = false;
-    sc_status st = launch_chunks(ctx, ch, ws, ws_n, false);
+    sc_status st = launch_chunks(ctx, ln, ch, ws, ws_n, false);
     ctx->time_field = t;
     return st;
 }
 
 // Run chunks in groups whose workspace fits under the cap.
-sc_status run_chunks(sc_ctx* ctx, std::vector<Chunk>& ch)
+sc_status run_chunks(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch)
 {
     const size_t cap = std::max<size_t>(ctx->ws_cap / sizeof(float2), 1);
     size_t i = 0;
     while (i < ch.size()) {
         size_t j = i, tot = 0;
         while (j < ch.size() && (j == i || tot + ch[j].ws_elems <= cap)) tot += ch[j++].ws_elems;
-        sc_status st = ensure(ctx, ctx->ws, tot * sizeof(float2));
+        sc_status st = ensure(ctx, ln.ws, tot * sizeof(float2), ln.stream);
         if (st != SC_OK) return st;
         std::vector<Chunk> part(ch.begin() + i, ch.begin() + j);
-        st = launch_chunks(ctx, part, (float2*)ctx->ws.p, tot, ctx->use_graphs);
+        st = launch_chunks(ctx, ln, part, (float2*)ln.ws.p, tot, ctx->use_graphs);
         if (st != SC_OK) return st;
         i = j;
     }
     return SC_OK;
+}
+
+void free_lane(Lane& ln)
+{
+    if (ln.stream) cudaStreamSynchronize(ln.stream);
+    for (DevBuf* b : {&ln.ws, &ln.desc, &ln.amp, &ln.kval})
+        if (b->p) {
+            cudaFree(b->p);
+            b->p = nullptr;
+            b->n = 0;
+        }
+    for (auto& g : ln.graphs) cudaGraphExecDestroy(g.exec);
+    ln.graphs.clear();
+    if (ln.cap_stream) cudaStreamDestroy(ln.cap_stream);
+    ln.cap_stream = nullptr;
+    if (ln.own_stream && ln.stream) cudaStreamDestroy(ln.stream);
+    ln.stream = nullptr;
+}
+
+// ------------------------------------------------------------------------
+// Serving (A9): continuous batching of submitted requests.  A server thread
+// admits queued requests in arrival order while their device memory (staged
+// points and server-owned outputs) fits the context's HBM budget, batches up
+// to max_batch of them and runs the batch on a free lane; with two lanes a
+// new batch starts while the previous one is still on the GPU, so requests
+// that arrive meanwhile overlap with it.  Completion is observed through an
+// event per lane; memory returns to the budget when the caller releases the
+// ticket.
+
+struct Ticket {
+    const sc_mirror_t* mirror = nullptr;
+    const sc_incident_t* incident = nullptr;
+    std::vector<double> omegas, host_pts;
+    const double* user_pts = nullptr;   // caller's device points (or null)
+    int n_points = 0, n_omega = 0;
+    double dom = 0.0;
+    void* E_user = nullptr;             // caller-owned device outputs (or null)
+    void* B_user = nullptr;
+    void* E = nullptr;                  // outputs in use
+    void* B = nullptr;
+    double* pts = nullptr;              // device points in use
+    bool own_out = false, own_pts = false;
+    size_t bytes = 0;                   // device bytes this ticket holds
+    int state = 0;                      // 0 queued, 1 running, 2 done, 3 failed, 4 cancelled
+    bool cancel = false;
+    sc_status status = SC_OK;
+    double t_submit = 0, t_start = 0, t_done = 0;
+    int lane = -1;
+    Table* tab = nullptr;
+};
+
+struct Server {
+    static constexpr int kLanes = 2;
+    std::thread th;
+    bool stop = false;
+    std::condition_variable cv;
+    std::deque<uint64_t> queue;
+    std::map<uint64_t, Ticket> tickets;
+    Lane lanes[kLanes];
+    cudaEvent_t done_ev[kLanes] = {};
+    std::vector<uint64_t> batch[kLanes];
+    bool busy[kLanes] = {};
+    size_t held = 0;                    // bytes of admitted tickets not yet released
+    uint64_t next_id = 1;
+    int max_batch = 64;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    double now() const
+    {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+size_t ticket_bytes(const Ticket& t)
+{
+    size_t b = 0;
+    if (t.own_pts) b += (size_t)t.n_points * 3 * sizeof(double);
+    if (t.own_out) b += (size_t)2 * t.n_omega * t.n_points * 3 * sizeof(float2);
+    return b;
+}
+
+// Run one batch of admitted tickets on lane L (ctx->mu held).
+sc_status launch_batch(sc_ctx* ctx, Server* srv, int L, const std::vector<uint64_t>& ids)
+{
+    Lane& ln = srv->lanes[L];
+    ctx->tick++;
+    std::vector<double> amp_all, k_all;
+    std::vector<size_t> om_off;
+    for (uint64_t id : ids) {
+        Ticket& t = srv->tickets[id];
+        t.state = 1;
+        t.lane = L;
+        t.t_start = srv->now();
+        sc_status st = get_table(ctx, t.mirror, t.incident, &t.tab, ln.stream);
+        if (st != SC_OK) return st;
+        t.tab->inflight++;
+        if (t.own_pts) {
+            SC_CUDA(cudaMallocAsync((void**)&t.pts, (size_t)t.n_points * 3 * sizeof(double), ln.stream),
+                    "serving points");
+            SC_CUDA(cudaMemcpyAsync(t.pts, t.host_pts.data(), (size_t)t.n_points * 3 * sizeof(double),
+                                    cudaMemcpyHostToDevice, ln.stream), "stage points");
+        } else {
+            t.pts = (double*)t.user_pts;
+        }
+        if (t.own_out) {
+            const size_t ob = (size_t)t.n_omega * t.n_points * 3 * sizeof(float2);
+            SC_CUDA(cudaMallocAsync(&t.E, ob, ln.stream), "serving outputs");
+            SC_CUDA(cudaMallocAsync(&t.B, ob, ln.stream), "serving outputs");
+        } else {
+            t.E = t.E_user;
+            t.B = t.B_user;
+        }
+        std::vector<double> a;
+        st = spectrum_amps(ctx, t.incident, t.omegas.data(), t.n_omega, a);
+        if (st != SC_OK) return st;
+        om_off.push_back(k_all.size());
+        amp_all.insert(amp_all.end(), a.begin(), a.end());
+        for (double w : t.omegas) k_all.push_back(2.0 * kPi * w);
+    }
+    sc_status st;
+    if ((st = ensure(ctx, ln.amp, amp_all.size() * sizeof(double), ln.stream)) != SC_OK) return st;
+    if ((st = ensure(ctx, ln.kval, k_all.size() * sizeof(double), ln.stream)) != SC_OK) return st;
+    SC_CUDA(cudaMemcpyAsync(ln.amp.p, amp_all.data(), amp_all.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, ln.stream), "upload amplitudes");
+    SC_CUDA(cudaMemcpyAsync(ln.kval.p, k_all.data(), k_all.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, ln.stream), "upload wavenumbers");
+    std::vector<Chunk> ch;
+    for (size_t i = 0; i < ids.size(); ++i) {
+        Ticket& t = srv->tickets[ids[i]];
+        st = plan_request(ctx, ln, t.tab, t.omegas.data(), t.n_omega, t.dom, t.pts, t.n_points,
+                          (const double*)ln.amp.p + 2 * om_off[i], (const double*)ln.kval.p + om_off[i],
+                          (float2*)t.E, (float2*)t.B, ch);
+        if (st != SC_OK) return st;
+        ctx->ctr.evals += (double)t.n_points * t.tab->n_surf * t.n_omega;
+    }
+    st = run_chunks(ctx, ln, ch);
+    if (st != SC_OK) return st;
+    SC_CUDA(cudaEventRecord(srv->done_ev[L], ln.stream), "completion event");
+    return SC_OK;
+}
+
+void serve(sc_ctx* ctx)
+{
+    Server* srv = ctx->server;
+    cudaSetDevice(ctx->device);
+    std::unique_lock<std::mutex> lk(ctx->mu);
+    while (!srv->stop) {
+        bool changed = false;
+        // completions
+        for (int L = 0; L < Server::kLanes; ++L) {
+            if (!srv->busy[L]) continue;
+            const cudaError_t q = cudaEventQuery(srv->done_ev[L]);
+            if (q == cudaErrorNotReady) continue;
+            const double t = srv->now();
+            for (uint64_t id : srv->batch[L]) {
+                auto it = srv->tickets.find(id);
+                if (it == srv->tickets.end()) continue;
+                Ticket& tk = it->second;
+                if (tk.tab) tk.tab->inflight--;
+                tk.tab = nullptr;
+                tk.t_done = t;
+                if (q != cudaSuccess) {
+                    tk.state = 3;
+                    tk.status = SC_ERR_CUDA;
+                } else {
+                    tk.state = tk.cancel ? 4 : 2;
+                }
+            }
+            if (q != cudaSuccess) cudaGetLastError();
+            srv->batch[L].clear();
+            srv->busy[L] = false;
+            changed = true;
+        }
+        // admission and launch on free lanes
+        for (int L = 0; L < Server::kLanes && !srv->queue.empty(); ++L) {
+            if (srv->busy[L]) continue;
+            // workspace the lanes may still grow into (bounded by the cap)
+            size_t reserve = size_t(16) << 20;
+            for (int M = 0; M < Server::kLanes; ++M)
+                if (srv->lanes[M].ws.n < ctx->ws_cap) reserve += ctx->ws_cap - srv->lanes[M].ws.n;
+            std::vector<uint64_t> ids;
+            while (!srv->queue.empty() && (int)ids.size() < srv->max_batch) {
+                Ticket& t = srv->tickets[srv->queue.front()];
+                const size_t b = ticket_bytes(t);
+                // admit only what fits next to every lane's full workspace; the
+                // first request of an idle server is always admitted
+                const bool idle = srv->held == 0 && ids.empty();
+                if (ctx->budget && !idle && ctx->held + srv->held + b + reserve > ctx->budget) break;
+                t.bytes = b;
+                srv->held += b;
+                ids.push_back(srv->queue.front());
+                srv->queue.pop_front();
+            }
+            if (ids.empty()) break;
+            const sc_status st = launch_batch(ctx, srv, L, ids);
+            if (st != SC_OK) {
+                cudaStreamSynchronize(srv->lanes[L].stream);
+                for (uint64_t id : ids) {
+                    Ticket& t = srv->tickets[id];
+                    if (t.tab) t.tab->inflight--;
+                    t.tab = nullptr;
+                    t.state = 3;
+                    t.status = st;
+                    t.t_done = srv->now();
+                }
+            } else {
+                srv->batch[L] = ids;
+                srv->busy[L] = true;
+            }
+            changed = true;
+        }
+        if (changed) srv->cv.notify_all();
+        srv->cv.wait_for(lk, std::chrono::microseconds(100));
+    }
+}
+
+sc_status start_server(sc_ctx* ctx)
+{
+    if (ctx->server) return SC_OK;
+    Server* srv = new Server();
+    for (int L = 0; L < Server::kLanes; ++L) {
+        if (cudaStreamCreateWithFlags(&srv->lanes[L].stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&srv->done_ev[L], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            delete srv;
+            return fail(ctx, SC_ERR_CUDA, "serving lane set-up failed");
+        }
+        srv->lanes[L].own_stream = true;
+    }
+    ctx->server = srv;
+    srv->th = std::thread(serve, ctx);
+    return SC_OK;
+}
+
+void free_ticket_memory(Server* srv, Ticket& t)
+{
+    cudaStream_t s = t.lane >= 0 ? srv->lanes[t.lane].stream : nullptr;
+    if (t.own_pts && t.pts) cudaFreeAsync(t.pts, s);
+    if (t.own_out && t.E) cudaFreeAsync(t.E, s);
+    if (t.own_out && t.B) cudaFreeAsync(t.B, s);
+    t.pts = nullptr;
+    t.E = t.B = nullptr;
+    srv->held -= t.bytes;
+    t.bytes = 0;
+}
+
+void stop_server(sc_ctx* ctx)
+{
+    Server* srv = ctx->server;
+    if (!srv) return;
+    {
+        std::lock_guard<std::mutex> lock(ctx->mu);
+        srv->stop = true;
+    }
+    srv->cv.notify_all();
+    srv->th.join();
+    cudaSetDevice(ctx->device);
+    for (int L = 0; L < Server::kLanes; ++L) cudaStreamSynchronize(srv->lanes[L].stream);
+    for (auto& kv : srv->tickets) {
+        if (kv.second.tab) kv.second.tab->inflight--;
+        free_ticket_memory(srv, kv.second);
+    }
+    for (int L = 0; L < Server::kLanes; ++L) {
+        cudaStreamSynchronize(srv->lanes[L].stream);
+        free_lane(srv->lanes[L]);
+        if (srv->done_ev[L]) cudaEventDestroy(srv->done_ev[L]);
+    }
+    delete srv;
+    ctx->server = nullptr;
 }
 
 }  // namespace
@@ -943,6 +1243,7 @@ sc_status sc_create(int device, void* cuda_stream, size_t hbm_budget_bytes, sc_c
     sc_ctx* ctx = new sc_ctx();
     ctx->device = device;
     ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->main.stream = ctx->stream;
     ctx->budget = hbm_budget_bytes;
     if (cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_err, sizeof(int)) != cudaSuccess ||
@@ -959,17 +1260,16 @@ sc_status sc_create(int device, void* cuda_stream, size_t hbm_budget_bytes, sc_c
 sc_status sc_destroy(sc_ctx* ctx)
 {
     if (!ctx) return SC_OK;
+    stop_server(ctx);
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     settle_events(ctx);
     for (auto& t : ctx->tables) free_table(ctx, t);
-    for (DevBuf* b : {&ctx->ws, &ctx->pts, &ctx->outE, &ctx->outB, &ctx->amp, &ctx->kval,
-                      &ctx->tvals, &ctx->phasor, &ctx->specE, &ctx->specB, &ctx->tE, &ctx->tB,
-                      &ctx->desc})
+    for (DevBuf* b : {&ctx->pts, &ctx->outE, &ctx->outB, &ctx->tkval, &ctx->tvals, &ctx->phasor,
+                      &ctx->specE, &ctx->specB, &ctx->tE, &ctx->tB})
         if (b->p) cudaFree(b->p);
+    free_lane(ctx->main);
     for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
-    for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
-    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->h_err) cudaFreeHost(ctx->h_err);
     delete ctx;
@@ -1074,6 +1374,7 @@ sc_status sc_eval(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, co
     double dom = 0.0;
     if (prec == SC_FP32_COMP && !uniform_grid(omegas, n_omega, dom))
         return fail(ctx, SC_ERR_INVALID, "SC_FP32_COMP needs a uniform, increasing omega grid");
+    std::lock_guard<std::mutex> lock(ctx->mu);
     SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
     ctx->tick++;
 
@@ -1100,7 +1401,7 @@ sc_status sc_eval(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, co
     for (int i = 0; i < n_omega; ++i) kv[i] = 2.0 * kPi * omegas[i];
 
     Table* tab = nullptr;
-    st = get_table(ctx, m, in, &tab);
+    st = get_table(ctx, m, in, &tab, ctx->stream);
     if (st != SC_OK) return st;
 
     // points on the device
@@ -1113,11 +1414,11 @@ sc_status sc_eval(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, co
                                 cudaMemcpyHostToDevice, ctx->stream), "upload points");
         d_pts = (const double*)ctx->pts.p;
     }
-    if ((st = ensure(ctx, ctx->amp, amp.size() * sizeof(double))) != SC_OK) return st;
-    if ((st = ensure(ctx, ctx->kval, kv.size() * sizeof(double))) != SC_OK) return st;
-    SC_CUDA(cudaMemcpyAsync(ctx->amp.p, amp.data(), amp.size() * sizeof(double),
+    if ((st = ensure(ctx, ctx->main.amp, amp.size() * sizeof(double))) != SC_OK) return st;
+    if ((st = ensure(ctx, ctx->main.kval, kv.size() * sizeof(double))) != SC_OK) return st;
+    SC_CUDA(cudaMemcpyAsync(ctx->main.amp.p, amp.data(), amp.size() * sizeof(double),
                             cudaMemcpyHostToDevice, ctx->stream), "upload amplitudes");
-    SC_CUDA(cudaMemcpyAsync(ctx->kval.p, kv.data(), kv.size() * sizeof(double),
+    SC_CUDA(cudaMemcpyAsync(ctx->main.kval.p, kv.data(), kv.size() * sizeof(double),
                             cudaMemcpyHostToDevice, ctx->stream), "upload wavenumbers");
 
     const size_t elem = prec == SC_FP64 ? sizeof(double2) : sizeof(float2);
@@ -1134,8 +1435,8 @@ sc_status sc_eval(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, co
     }
     // the staging buffers may have moved: refresh pointers taken before
     if (!pts_dev) d_pts = (const double*)ctx->pts.p;
-    const double* d_amp = (const double*)ctx->amp.p;
-    const double* d_k = (const double*)ctx->kval.p;
+    const double* d_amp = (const double*)ctx->main.amp.p;
+    const double* d_k = (const double*)ctx->main.kval.p;
 
     const double evals = (double)n_points * (double)tab->n_surf * (double)n_omega;
 
@@ -1168,10 +1469,10 @@ sc_status sc_eval(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, co
         ctx->ctr.field_launches += 1;
     } else {
         std::vector<Chunk> ch;
-        st = plan_request(ctx, tab, omegas, n_omega, dom, d_pts, n_points, d_amp, d_k, (float2*)dE,
-                          (float2*)dB, ch);
+        st = plan_request(ctx, ctx->main, tab, omegas, n_omega, dom, d_pts, n_points, d_amp, d_k,
+                          (float2*)dE, (float2*)dB, ch);
         if (st != SC_OK) return st;
-        st = run_chunks(ctx, ch);
+        st = run_chunks(ctx, ctx->main, ch);
         if (st != SC_OK) return st;
     }
     ctx->ctr.evals += evals;
@@ -1222,6 +1523,7 @@ sc_status sc_eval_batch(sc_ctx* ctx, const sc_request* reqs, int n_req, sc_eval_
             return fail(ctx, SC_ERR_INVALID, "request %d: points and outputs must be device buffers", r);
         n_om_total += q.n_omega;
     }
+    std::lock_guard<std::mutex> lock(ctx->mu);
     SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
     ctx->tick++;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -1250,26 +1552,27 @@ sc_status sc_eval_batch(sc_ctx* ctx, const sc_request* reqs, int n_req, sc_eval_
     std::vector<Table*> tabs(n_req);
     double evals = 0.0;
     for (int r = 0; r < n_req; ++r) {
-        sc_status st = get_table(ctx, reqs[r].mirror, reqs[r].incident, &tabs[r]);
+        sc_status st = get_table(ctx, reqs[r].mirror, reqs[r].incident, &tabs[r], ctx->main.stream);
         if (st != SC_OK) return st;
         evals += (double)reqs[r].n_points * tabs[r]->n_surf * reqs[r].n_omega;
     }
     sc_status st;
-    if ((st = ensure(ctx, ctx->amp, amp_all.size() * sizeof(double))) != SC_OK) return st;
-    if ((st = ensure(ctx, ctx->kval, k_all.size() * sizeof(double))) != SC_OK) return st;
-    SC_CUDA(cudaMemcpyAsync(ctx->amp.p, amp_all.data(), amp_all.size() * sizeof(double),
-                            cudaMemcpyHostToDevice, ctx->stream), "upload amplitudes");
-    SC_CUDA(cudaMemcpyAsync(ctx->kval.p, k_all.data(), k_all.size() * sizeof(double),
-                            cudaMemcpyHostToDevice, ctx->stream), "upload wavenumbers");
+    Lane& ln = ctx->main;
+    if ((st = ensure(ctx, ln.amp, amp_all.size() * sizeof(double))) != SC_OK) return st;
+    if ((st = ensure(ctx, ln.kval, k_all.size() * sizeof(double))) != SC_OK) return st;
+    SC_CUDA(cudaMemcpyAsync(ln.amp.p, amp_all.data(), amp_all.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, ln.stream), "upload amplitudes");
+    SC_CUDA(cudaMemcpyAsync(ln.kval.p, k_all.data(), k_all.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, ln.stream), "upload wavenumbers");
     std::vector<Chunk> ch;
     for (int r = 0; r < n_req; ++r) {
         const sc_request& q = reqs[r];
-        st = plan_request(ctx, tabs[r], q.omegas, q.n_omega, dom[r], q.points_xyz, q.n_points,
-                          (const double*)ctx->amp.p + 2 * om_off[r], (const double*)ctx->kval.p + om_off[r],
+        st = plan_request(ctx, ln, tabs[r], q.omegas, q.n_omega, dom[r], q.points_xyz, q.n_points,
+                          (const double*)ln.amp.p + 2 * om_off[r], (const double*)ln.kval.p + om_off[r],
                           (float2*)q.E_out, (float2*)q.B_out, ch);
         if (st != SC_OK) return st;
     }
-    st = run_chunks(ctx, ch);
+    st = run_chunks(ctx, ln, ch);
     if (st != SC_OK) return st;
     ctx->ctr.evals += evals;
     if (stats) {
@@ -1313,6 +1616,7 @@ sc_status sc_eval_fp32_static(sc_ctx* ctx, const sc_mirror_t* m, const sc_incide
                     "request needs %zu bytes of static scratch; the limit is %zu (points x omegas "
                     "<= %zu)", header_al + ws_bytes, sc::kStaticScratchBytes,
                     (sc::kStaticScratchBytes - header_al) / (2 * sc::kAcc * sizeof(float2)));
+    std::lock_guard<std::mutex> lock(ctx->mu);
     Table* tab = nullptr;
     for (auto& t : ctx->tables)
         if (t.mid == m->id && t.iid == in->id) tab = &t;
@@ -1384,6 +1688,7 @@ sc_status sc_time_domain(sc_ctx* ctx, sc_precision prec, const void* E_spec, con
     double dom = 0.0;
     if (!uniform_grid(omegas, n_omega, dom))
         return fail(ctx, SC_ERR_INVALID, "the inverse transform needs a uniform omega grid");
+    std::lock_guard<std::mutex> lock(ctx->mu);
     SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
     const size_t elem = prec == SC_FP64 ? sizeof(double2) : sizeof(float2);
     const long long n_vals = (long long)n_points * 3;
@@ -1394,7 +1699,7 @@ sc_status sc_time_domain(sc_ctx* ctx, sc_precision prec, const void* E_spec, con
     sc_status st;
     std::vector<double> kv(n_omega);
     for (int i = 0; i < n_omega; ++i) kv[i] = 2.0 * kPi * omegas[i];
-    if ((st = ensure(ctx, ctx->kval, kv.size() * sizeof(double))) != SC_OK) return st;
+    if ((st = ensure(ctx, ctx->tkval, kv.size() * sizeof(double))) != SC_OK) return st;
     if ((st = ensure(ctx, ctx->tvals, (size_t)n_t * sizeof(double))) != SC_OK) return st;
     if ((st = ensure(ctx, ctx->phasor, (size_t)n_omega * n_t * sizeof(float2))) != SC_OK) return st;
     const void* dEs = E_spec;
@@ -1416,7 +1721,7 @@ sc_status sc_time_domain(sc_ctx* ctx, sc_precision prec, const void* E_spec, con
         dEt = (float*)ctx->tE.p;
         dBt = B_t ? (float*)ctx->tB.p : nullptr;
     }
-    SC_CUDA(cudaMemcpyAsync(ctx->kval.p, kv.data(), kv.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload wavenumbers");
+    SC_CUDA(cudaMemcpyAsync(ctx->tkval.p, kv.data(), kv.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload wavenumbers");
     SC_CUDA(cudaMemcpyAsync(ctx->tvals.p, times, (size_t)n_t * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload times");
     const double dk = n_omega > 1 ? 2.0 * kPi * dom : 1.0;
     for (int pass = 0; pass < (B_spec ? 2 : 1); ++pass) {
@@ -1425,7 +1730,7 @@ sc_status sc_time_domain(sc_ctx* ctx, sc_precision prec, const void* E_spec, con
         l.f64 = prec == SC_FP64;
         l.n_omega = n_omega;
         l.n_vals = n_vals;
-        l.kval = (const double*)ctx->kval.p;
+        l.kval = (const double*)ctx->tkval.p;
         l.t = (const double*)ctx->tvals.p;
         l.n_t = n_t;
         l.dk = dk;
@@ -1443,9 +1748,177 @@ sc_status sc_time_domain(sc_ctx* ctx, sc_precision prec, const void* E_spec, con
     return SC_OK;
 }
 
+sc_status sc_submit(sc_ctx* ctx, const sc_request* req, uint64_t* ticket)
+{
+    if (!ctx) return SC_ERR_INVALID;
+    if (!req || !ticket || !req->mirror || !req->incident || !req->omegas || !req->points_xyz ||
+        req->n_omega < 1 || req->n_points < 1 || req->n_omega > 2048 * 64)
+        return fail(ctx, SC_ERR_INVALID, "invalid request");
+    double dom = 0.0;
+    for (int i = 0; i < req->n_omega; ++i)
+        if (!(req->omegas[i] > 0.0) || !std::isfinite(req->omegas[i]))
+            return fail(ctx, SC_ERR_INVALID, "omega[%d] must be positive", i);
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (!uniform_grid(req->omegas, req->n_omega, dom))
+        return fail(ctx, SC_ERR_INVALID, "serving needs a uniform, increasing omega grid");
+    SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    Ticket t;
+    t.mirror = req->mirror;
+    t.incident = req->incident;
+    t.omegas.assign(req->omegas, req->omegas + req->n_omega);
+    t.n_points = req->n_points;
+    t.n_omega = req->n_omega;
+    t.dom = dom;
+    if (is_device_ptr(req->points_xyz)) {
+        t.user_pts = req->points_xyz;
+    } else {
+        sc_status st = check_points_host(ctx, req->mirror, req->points_xyz, req->n_points);
+        if (st != SC_OK) return st;
+        t.host_pts.assign(req->points_xyz, req->points_xyz + 3 * (size_t)req->n_points);
+        t.own_pts = true;
+    }
+    if (req->E_out) {
+        if (!is_device_ptr(req->E_out) || (req->B_out && !is_device_ptr(req->B_out)))
+            return fail(ctx, SC_ERR_INVALID, "caller-owned serving outputs must be device buffers");
+        t.E_user = req->E_out;
+        t.B_user = req->B_out;
+    } else {
+        t.own_out = true;
+    }
+    const size_t b = ticket_bytes(t);
+    if (ctx->budget && b > ctx->budget)
+        return fail(ctx, SC_ERR_BUSY, "request needs %zu device bytes, more than the whole budget %zu", b,
+                    ctx->budget);
+    sc_status st = start_server(ctx);
+    if (st != SC_OK) return st;
+    Server* srv = ctx->server;
+    t.t_submit = srv->now();
+    const uint64_t id = srv->next_id++;
+    srv->tickets.emplace(id, std::move(t));
+    srv->queue.push_back(id);
+    *ticket = id;
+    srv->cv.notify_all();
+    return SC_OK;
+}
+
+sc_status sc_poll(sc_ctx* ctx, uint64_t ticket, int* done)
+{
+    if (!ctx || !done) return SC_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (!ctx->server) return fail(ctx, SC_ERR_NOT_FOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    auto it = ctx->server->tickets.find(ticket);
+    if (it == ctx->server->tickets.end())
+        return fail(ctx, SC_ERR_NOT_FOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    const Ticket& t = it->second;
+    *done = t.state >= 2;
+    if (t.state == 3) return fail(ctx, t.status, "request failed");
+    if (t.state == 4) return fail(ctx, SC_ERR_CANCELLED, "request cancelled");
+    return SC_OK;
+}
+
+sc_status sc_wait(sc_ctx* ctx, uint64_t ticket, double timeout_s)
+{
+    if (!ctx) return SC_ERR_INVALID;
+    std::unique_lock<std::mutex> lk(ctx->mu);
+    if (!ctx->server) return fail(ctx, SC_ERR_NOT_FOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    Server* srv = ctx->server;
+    const auto deadline = std::chrono::steady_clock::now() +
+                          std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                              std::chrono::duration<double>(timeout_s));
+    for (;;) {
+        auto it = srv->tickets.find(ticket);
+        if (it == srv->tickets.end())
+            return fail(ctx, SC_ERR_NOT_FOUND, "unknown ticket %llu", (unsigned long long)ticket);
+        const Ticket& t = it->second;
+        if (t.state == 2) return SC_OK;
+        if (t.state == 3) return fail(ctx, t.status, "request failed");
+        if (t.state == 4) return fail(ctx, SC_ERR_CANCELLED, "request cancelled");
+        if (srv->cv.wait_until(lk, deadline) == std::cv_status::timeout) {
+            auto jt = srv->tickets.find(ticket);
+            if (jt != srv->tickets.end() && jt->second.state == 2) return SC_OK;
+            return fail(ctx, SC_ERR_TIMEOUT, "request %llu not done after %.3f s",
+                        (unsigned long long)ticket, timeout_s);
+        }
+    }
+}
+
+sc_status sc_cancel(sc_ctx* ctx, uint64_t ticket)
+{
+    if (!ctx) return SC_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (!ctx->server) return fail(ctx, SC_ERR_NOT_FOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    Server* srv = ctx->server;
+    auto it = srv->tickets.find(ticket);
+    if (it == srv->tickets.end())
+        return fail(ctx, SC_ERR_NOT_FOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    Ticket& t = it->second;
+    if (t.state == 0) {
+        srv->queue.erase(std::find(srv->queue.begin(), srv->queue.end(), ticket));
+        t.state = 4;
+        t.t_done = srv->now();
+    } else if (t.state == 1) {
+        t.cancel = true;  // its batch finishes; the result is discarded
+    }
+    srv->cv.notify_all();
+    return SC_OK;
+}
+
+sc_status sc_fetch(sc_ctx* ctx, uint64_t ticket, void* E_dst, void* B_dst)
+{
+    if (!ctx) return SC_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (!ctx->server) return fail(ctx, SC_ERR_NOT_FOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    Server* srv = ctx->server;
+    auto it = srv->tickets.find(ticket);
+    if (it == srv->tickets.end())
+        return fail(ctx, SC_ERR_NOT_FOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    Ticket& t = it->second;
+    if (t.state != 2) return fail(ctx, SC_ERR_BUSY, "request %llu is not done", (unsigned long long)ticket);
+    SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const size_t ob = (size_t)t.n_omega * t.n_points * 3 * sizeof(float2);
+    cudaStream_t s = srv->lanes[t.lane].stream;
+    if (E_dst) SC_CUDA(cudaMemcpyAsync(E_dst, t.E, ob, cudaMemcpyDefault, s), "fetch E");
+    if (B_dst && t.B) SC_CUDA(cudaMemcpyAsync(B_dst, t.B, ob, cudaMemcpyDefault, s), "fetch B");
+    SC_CUDA(cudaStreamSynchronize(s), "fetch");
+    return SC_OK;
+}
+
+sc_status sc_release(sc_ctx* ctx, uint64_t ticket)
+{
+    if (!ctx) return SC_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (!ctx->server) return fail(ctx, SC_ERR_NOT_FOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    Server* srv = ctx->server;
+    auto it = srv->tickets.find(ticket);
+    if (it == srv->tickets.end())
+        return fail(ctx, SC_ERR_NOT_FOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    if (it->second.state == 1) return fail(ctx, SC_ERR_BUSY, "request %llu is still running", (unsigned long long)ticket);
+    if (it->second.state == 0) srv->queue.erase(std::find(srv->queue.begin(), srv->queue.end(), ticket));
+    cudaSetDevice(ctx->device);
+    free_ticket_memory(srv, it->second);
+    srv->tickets.erase(it);
+    srv->cv.notify_all();
+    return SC_OK;
+}
+
+sc_status sc_ticket_times(sc_ctx* ctx, uint64_t ticket, double* t_submit, double* t_start, double* t_done)
+{
+    if (!ctx) return SC_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (!ctx->server) return fail(ctx, SC_ERR_NOT_FOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    auto it = ctx->server->tickets.find(ticket);
+    if (it == ctx->server->tickets.end())
+        return fail(ctx, SC_ERR_NOT_FOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    if (t_submit) *t_submit = it->second.t_submit;
+    if (t_start) *t_start = it->second.t_start;
+    if (t_done) *t_done = it->second.t_done;
+    return SC_OK;
+}
+
 sc_status sc_get_counters(sc_ctx* ctx, sc_counters* out)
 {
     if (!ctx || !out) return SC_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(ctx->mu);
     SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
     sc_status st = check_device_error(ctx);
     settle_events(ctx);
@@ -1458,6 +1931,7 @@ sc_status sc_get_counters(sc_ctx* ctx, sc_counters* out)
 sc_status sc_reset_counters(sc_ctx* ctx)
 {
     if (!ctx) return SC_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(ctx->mu);
     SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
     SC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
     settle_events(ctx);
@@ -1468,6 +1942,7 @@ sc_status sc_reset_counters(sc_ctx* ctx)
 sc_status sc_set_option(sc_ctx* ctx, int option, long long value)
 {
     if (!ctx) return SC_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(ctx->mu);
     switch (option) {
     case SC_OPT_TIME_FIELD: ctx->time_field = value != 0; return SC_OK;
     case SC_OPT_NODES_PER_SPLIT:
