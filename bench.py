@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched and serving legs")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="broadband", choices=["broadband", "profile"],
                     help="broadband: the benchmark workload; profile: the same kernel "
@@ -200,6 +202,113 @@ def profile_traffic():
     return None
 
 
+def make_config_handles(ctx, configs):
+    out = []
+    for c in configs:
+        mc, b = c["mirror"], c["beam"]
+        m = ctx.mirror(mc["f"], mc["r_min"], mc["r_max"], mc["n_r"], mc["n_theta"], rim=mc["rim"])
+        inc = ctx.incident(profile=b["profile"], w0=b["w0"], sg_order=b["sg_order"], pol=b["pol"],
+                           zernike=b["zernike"], spectrum=c["spectrum"])
+        out.append((m, inc, mc["n_r"] * mc["n_theta"]))
+    return out
+
+
+def batch_leg(sc, torch, dev, n_req=64):
+    """The uneven batch: one sc_eval_batch against the same requests one by one."""
+    from paper_1609_08146_gb300 import workloads as wl
+
+    configs, reqs = wl.uneven_requests(n_req, seed=1609)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = sc.Context(dev.index or 0, stream=stream)
+    hs = make_config_handles(ctx, configs)
+    batch = [(hs[r["config"]][0], hs[r["config"]][1], r["omegas"],
+              torch.tensor(r["points"], device=dev)) for r in reqs]
+    evals = sum(len(r["points"]) * hs[r["config"]][2] * len(r["omegas"]) for r in reqs)
+    for (m, inc, om, P) in batch:  # tables resident, shapes tuned
+        ctx.eval(m, inc, om, P)
+    ctx.eval_batch(batch)
+    stream.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    ctx.eval_batch(batch)
+    ev[1].record(stream)
+    for (m, inc, om, P) in batch:
+        ctx.eval(m, inc, om, P)
+    ev[2].record(stream)
+    stream.synchronize()
+    t_batch = ev[0].elapsed_time(ev[1]) / 1000.0
+    t_seq = ev[1].elapsed_time(ev[2]) / 1000.0
+    ctx.close()
+    return {"requests": n_req, "evals": evals, "value": evals / t_batch, "unit": "evals/s",
+            "sequential_value": evals / t_seq, "batch_ms": 1000 * t_batch, "sequential_ms": 1000 * t_seq,
+            "workload": "64 seeded uneven requests: 8 mirror/beam configs (f 1e3-1e5, 64^2-256^2 nodes, "
+                        "Gaussian/super-Gaussian, linear/radial/azimuthal, Zernike), 256-8192 points, "
+                        "1-256 omegas"}
+
+
+def serving_leg(sc, torch, dev, n_per_rate=48, loads=(0.5, 0.8, 0.95)):
+    """Poisson arrivals of uneven requests at fractions of the saturated rate;
+    latency = observed completion - submission (library clock)."""
+    from paper_1609_08146_gb300 import workloads as wl
+
+    configs, reqs = wl.uneven_requests(n_per_rate * (len(loads) + 1), seed=2016)
+    ctx = sc.Context(dev.index or 0)
+    ctx.set_option(sc.SC_OPT_AUTOTUNE, 0)  # no timing runs on the serving path
+    hs = make_config_handles(ctx, configs)
+    for (m, inc, _) in hs:  # node tables resident before the first arrival
+        ctx.eval(m, inc, [1.0], np.zeros((1, 3)))
+
+    def evals(r):
+        return len(r["points"]) * hs[r["config"]][2] * len(r["omegas"])
+
+    def run(chunk, arrivals):
+        t0 = time.perf_counter()
+        pending, lat, tick = [], [], []
+        i = 0
+        while i < len(chunk) or pending:
+            now = time.perf_counter() - t0
+            while i < len(chunk) and arrivals[i] <= now:
+                r = chunk[i]
+                m, inc, _ = hs[r["config"]]
+                pending.append(ctx.submit(m, inc, r["omegas"], r["points"]))
+                i += 1
+            still = []
+            for t in pending:
+                if ctx.poll(t):
+                    s0, s1, s2 = ctx.ticket_times(t)
+                    lat.append(s2 - s0)
+                    tick.append(s2)
+                    ctx.release(t)
+                else:
+                    still.append(t)
+            pending = still
+            time.sleep(0.0002)
+        wall = time.perf_counter() - t0
+        return lat, wall
+
+    # saturated: everything submitted at once
+    sat_chunk = reqs[:n_per_rate]
+    lat, wall = run(sat_chunk, [0.0] * len(sat_chunk))
+    sat_rate = len(sat_chunk) / wall
+    out = {"saturated_req_per_s": sat_rate,
+           "saturated_evals_per_s": sum(evals(r) for r in sat_chunk) / wall,
+           "workload": "seeded uneven requests (8 resident mirror/beam configs, 64^2-256^2 nodes, "
+                       "256-8192 points, 1-256 omegas), Poisson arrivals", "rates": []}
+    rng = np.random.Generator(np.random.PCG64(5))
+    for k, load in enumerate(loads):
+        chunk = reqs[(k + 1) * n_per_rate:(k + 2) * n_per_rate]
+        rate = load * sat_rate
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(chunk)))
+        lat, wall = run(chunk, arrivals)
+        lat_ms = 1000.0 * np.array(lat)
+        out["rates"].append({"load": load, "rate_req_per_s": rate, "requests": len(chunk),
+                             "p50_ms": float(np.percentile(lat_ms, 50)),
+                             "p99_ms": float(np.percentile(lat_ms, 99)),
+                             "throughput_evals_per_s": sum(evals(r) for r in chunk) / wall})
+    ctx.close()
+    return out
+
+
 def run_reference(args, rank, world, pg):
     from paper_1609_08146_gb300 import workloads as wl
 
@@ -343,6 +452,12 @@ def main():
     fp64 = {"value": fp64_rate, "unit": "evals/s", "sample": "%d points x all nodes x all omegas"
             % sub.shape[0], "fp32_speedup": (value / world) / fp64_rate}
 
+    # ---- batched uneven requests and serving (single GPU, rank 0)
+    batched = serving = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        batched = batch_leg(sc, torch, dev)
+        serving = serving_leg(sc, torch, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, idx, dt, cores, E0, B0 = oracle_sample_rate(w, args.cpu_seconds)
@@ -377,6 +492,8 @@ def main():
             "gpu_launches_per_step": launches_per_step,
             "roofline": roof,
             "fp64_gpu": fp64,
+            "batched": batched,
+            "serving": serving,
             "cpu_baseline": cpu,
             "clocks": clk,
         }

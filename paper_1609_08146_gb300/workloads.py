@@ -80,6 +80,38 @@ def sweep(f: float, n_nodes: int, n_points: int = 4096, seed: int = 1609):
     )
 
 
+def uneven_requests(n: int, seed: int, max_nodes: int = 256, max_points: int = 8192,
+                    max_omega: int = 256, n_configs: int = 8):
+    """Seeded uneven requests shaped like a serving mix: a pool of n_configs
+    mirror/beam configurations (f log-uniform in [1e3, 1e5], r_max = 2f,
+    w0 = 0.6 f, N x N nodes with N in {64, 128, ..., max_nodes}, Gaussian or
+    super-Gaussian N=4, x-linear / radial / azimuthal, Zernike j = 2..15 with
+    N(0, 0.1) waves); each request picks a configuration, a log-uniform point
+    count in [256, max_points] (uniform in the +-2 cube) and a log-uniform
+    omega count in [1, max_omega] on [0.5, 1.5] (omega0 alone if 1)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sizes = [s for s in (64, 128, 256, 512, 1024) if s <= max_nodes]
+    configs = []
+    for _ in range(n_configs):
+        f = float(10 ** rng.uniform(3, 5))
+        N = int(rng.choice(sizes))
+        configs.append(dict(
+            mirror=dict(f=f, r_min=0.0, r_max=2 * f, n_r=N, n_theta=N, rim=True),
+            beam=dict(profile=str(rng.choice(["gauss", "supergauss"])), sg_order=4, w0=0.6 * f,
+                      pol=str(rng.choice(["linear", "radial", "azimuthal"])), pol_angle=0.0,
+                      zernike=list(rng.normal(0.0, 0.1, size=14))),
+            spectrum=dict(kind="gauss_time", fwhm_t=10.0 / FS_PER_UNIT_800NM, lambda_c=1.0,
+                          energy=1.0)))
+    reqs = []
+    for _ in range(n):
+        c = int(rng.integers(n_configs))
+        npts = int(round(10 ** rng.uniform(np.log10(256), np.log10(max_points))))
+        nom = int(round(10 ** rng.uniform(0, np.log10(max_omega))))
+        reqs.append(dict(config=c, omegas=uniform_omegas(nom),
+                         points=rng.uniform(-2.0, 2.0, size=(npts, 3))))
+    return configs, reqs
+
+
 def oracle_args(w):
     """The same workload in the oracle's parameter format."""
     m = dict(w["mirror"])
