@@ -108,7 +108,7 @@ struct sc_ctx {
     sc_counters ctr{};
     bool time_field = false;
     long long nodes_per_split = 0;  // 0: choose splits for load balance
-    long long flush_nodes = 1024;   // FP32 run length before each compensated fold
+    long long flush_nodes = 2048;   // FP32 run length before each compensated fold
     size_t ws_cap = size_t(2) << 30;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
     std::vector<cudaEvent_t> pool;

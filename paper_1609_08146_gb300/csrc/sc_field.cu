@@ -32,7 +32,7 @@
 //     and runs the 26-op inner loop over the tile's nodes, accumulators in
 //     registers (12 per omega);
 //   * each CTA sums one split of the node range.  Every flush_tiles tiles
-//     (1024 nodes by default) the FP32 register sums are folded into a
+//     (2048 nodes by default) the FP32 register sums are folded into a
 //     compensated float-float (hi, lo) partial in the workspace (TwoSum on
 //     the FP32 pipe) and restarted, so no FP32 running sum grows long; the
 //     reduce kernel adds the splits' partials in FP64 in a fixed order, so
@@ -383,13 +383,18 @@ struct Grouped {
     static constexpr int SEG = TPP >= 32 ? TPP / 32 : 1;  // seed segments of 32 groups per pair
     static constexpr int NPAIR = PPC * TC;
     static constexpr int NITEM = NPAIR * SEG;
-    static constexpr int COEF = 24;  // floats per pair: 10 duplicated pairs + rotation + pad
+    // floats per pair row: 10 duplicated pairs, rotation, rotation^2, pad to 28 so
+    // that consecutive producer lanes store to different banks
+    static constexpr int COEF = 28;
     // shared layout (bytes): node tiles | coefs | seeds | points | segment omegas | mbarriers | item
     static constexpr size_t OFF_NODE = 0;
     static constexpr size_t OFF_COEF = OFF_NODE + 2 * kTileBytes;
     static constexpr size_t COEF_BYTES = (size_t)NPAIR * COEF * 4;
     static constexpr size_t OFF_SEED = OFF_COEF + 2 * COEF_BYTES;
-    static constexpr size_t SEED_BYTES = (size_t)NPAIR * TPP * 8;
+    // seed rows padded by one entry: producer lanes (consecutive pairs) write
+    // rows TPP + 1 apart, so their stores fall in different banks
+    static constexpr int SROW = TPP + 1;
+    static constexpr size_t SEED_BYTES = (size_t)NPAIR * SROW * 8;
     static constexpr size_t OFF_PTS = OFF_SEED + 2 * SEED_BYTES;
     static constexpr size_t OFF_OMS = OFF_PTS + PPC * 16;
     static constexpr size_t NOMS = (TPP + 15) / 16;  // reseed omegas, every 16 groups
@@ -474,12 +479,12 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
                 const int pb = (int)(cg & 1);
                 if (!mbar_wait(&full[pb], (unsigned)((cg >> 1) & 1))) timed_out = true;
                 const float* cb = coefbuf + (size_t)pb * L::NPAIR * L::COEF + (size_t)pl * L::TC * L::COEF;
-                const float2* sb = seedbuf + (size_t)pb * L::NPAIR * TPP + (size_t)pl * L::TC * TPP + g;
+                const float2* sb = seedbuf + (size_t)pb * L::NPAIR * L::SROW + (size_t)pl * L::TC * L::SROW + g;
 #pragma unroll 1
                 for (int j = 0; j < L::TC; ++j) {
                     const float4* c4 = reinterpret_cast<const float4*>(cb + j * L::COEF);
                     float2 cp[10];
-                    float2 rot;
+                    float2 rot, rot2;
                     {
                         const float4 a0 = c4[0], a1 = c4[1], a2 = c4[2], a3 = c4[3], a4 = c4[4], a5 = c4[5];
                         cp[0] = make_float2(a0.x, a0.y); cp[1] = make_float2(a0.z, a0.w);
@@ -488,12 +493,20 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
                         cp[6] = make_float2(a3.x, a3.y); cp[7] = make_float2(a3.z, a3.w);
                         cp[8] = make_float2(a4.x, a4.y); cp[9] = make_float2(a4.z, a4.w);
                         rot = make_float2(a5.x, a5.y);
+                        rot2 = make_float2(a5.z, a5.w);
                     }
-                    float2 ph = sb[j * TPP];
+                    // two interleaved phasor chains (even and odd omegas) stepping by
+                    // e^{2i dk Phi}: half the dependent depth of one chain
+                    float2 pe = sb[j * L::SROW];
+                    float2 po = cmul(pe, rot);
 #pragma unroll
-                    for (int jj = 0; jj < kB; ++jj) {
-                        eval_x2(acc[jj], cp, kv[jj], ph);
-                        if (jj + 1 < kB) ph = cmul(ph, rot);
+                    for (int jj = 0; jj < kB; jj += 2) {
+                        eval_x2(acc[jj], cp, kv[jj], pe);
+                        eval_x2(acc[jj + 1], cp, kv[jj + 1], po);
+                        if (jj + 2 < kB) {
+                            pe = cmul(pe, rot2);
+                            po = cmul(po, rot2);
+                        }
                     }
                 }
                 // hand the table back: one arrival per consumer warp, after the warp is done
@@ -506,8 +519,6 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
             // ---------------- producers ----------------
             const int ptid = tid - L::NC;
             const float d1h = p.dom_hi, d1l = p.dom_lo;
-            const double domB = dom * kB;
-            const float dBh = (float)domB, dBl = (float)(domB - (double)(float)domB);
             unsigned issued[2] = {0, 0}, waited[2] = {0, 0};
             if (ptid == 0) {
                 for (int s = 0; s < 2 && s < nt; ++s) {
@@ -532,7 +543,7 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
                 if (cg >= 2 && !mbar_wait(&empty[pb], (unsigned)(((cg >> 1) - 1) & 1))) timed_out = true;
                 const float* nb = nodebuf + nbi * kTileFloats;
                 float* cb = coefbuf + (size_t)pb * L::NPAIR * L::COEF;
-                float2* sb = seedbuf + (size_t)pb * L::NPAIR * TPP;
+                float2* sb = seedbuf + (size_t)pb * L::NPAIR * L::SROW;
                 for (int i = ptid; i < L::NITEM; i += L::NPROD) {
                     const int q = i / L::SEG, seg = i % L::SEG;
                     const int pq = q / L::TC, j = q % L::TC;
@@ -540,17 +551,22 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
                     const float phi = pair_coefs(nb, sub * L::TC + j, spts[pq], co);
                     if (seg == 0) {
                         const float2 rot = phasor_2wphi(d1h, d1l, phi);
+                        const float2 rot2 = cmul(rot, rot);
                         float4* c4 = reinterpret_cast<float4*>(cb + (size_t)q * L::COEF);
                         c4[0] = make_float4(co[0], co[0], co[1], co[1]);
                         c4[1] = make_float4(co[2], co[2], co[3], co[3]);
                         c4[2] = make_float4(co[4], co[4], co[5], co[5]);
                         c4[3] = make_float4(co[6], co[6], co[7], co[7]);
                         c4[4] = make_float4(co[8], co[8], -co[9], -co[9]);
-                        c4[5] = make_float4(rot.x, rot.y, 0.f, 0.f);
+                        c4[5] = make_float4(rot.x, rot.y, rot2.x, rot2.y);
                     }
                     const int g0 = seg * 32, g1 = min(G, g0 + 32);
                     if (g0 < g1) {
-                        const float2 rotB = phasor_2wphi(dBh, dBl, phi);
+                        // e^{i 8 dk Phi} as the cube of squarings of e^{i dk Phi}
+                        float2 rotB = phasor_2wphi(d1h, d1l, phi);
+                        rotB = cmul(rotB, rotB);
+                        rotB = cmul(rotB, rotB);
+                        rotB = cmul(rotB, rotB);
                         float2 sd = make_float2(1.f, 0.f);
                         for (int gg = g0; gg < g1; ++gg) {
                             if ((gg & 15) == 0) {
@@ -559,7 +575,7 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
                             } else {
                                 sd = cmul(sd, rotB);
                             }
-                            sb[(size_t)q * TPP + gg] = sd;
+                            sb[(size_t)q * L::SROW + gg] = sd;
                         }
                     }
                 }

@@ -112,7 +112,7 @@ def test_ragged_tiles_splits_groups(ctx, beam):
         check(ctx, mirror, beam, om, pts)
     finally:
         ctx.set_option(sc.SC_OPT_NODES_PER_SPLIT, 0)
-        ctx.set_option(sc.SC_OPT_FLUSH_NODES, 1024)
+        ctx.set_option(sc.SC_OPT_FLUSH_NODES, 2048)
 
 
 @pytest.mark.parametrize("n_omega", [1, 2, 3, 5, 8, 9, 16, 17, 64, 100, 256, 600])
