@@ -397,7 +397,7 @@ struct Grouped {
     static constexpr size_t SEED_BYTES = (size_t)NPAIR * SROW * 8;
     static constexpr size_t OFF_PTS = OFF_SEED + 2 * SEED_BYTES;
     static constexpr size_t OFF_OMS = OFF_PTS + PPC * 16;
-    static constexpr size_t NOMS = (TPP + 15) / 16;  // reseed omegas, every 16 groups
+    static constexpr size_t NOMS = (TPP + 15) / 16;  // omegas of every 16th group (every 32nd used)
     static constexpr size_t OFF_BAR = (OFF_OMS + NOMS * 8 + 15) / 16 * 16;
     static constexpr size_t SMEM = OFF_BAR + 7 * 8;  // node[2], full[2], empty[2], item slot
     static_assert(SMEM <= 227 * 1024, "shared memory");
@@ -569,7 +569,7 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
                         rotB = cmul(rotB, rotB);
                         float2 sd = make_float2(1.f, 0.f);
                         for (int gg = g0; gg < g1; ++gg) {
-                            if ((gg & 15) == 0) {
+                            if ((gg & 31) == 0) {  // one direct seed per 32 groups
                                 const float2 wv = soms[gg >> 4];
                                 sd = phasor_2wphi(wv.x, wv.y, phi);
                             } else {
