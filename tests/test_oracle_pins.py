@@ -413,3 +413,63 @@ def test_paraboloid_reference_phase_identity():
     r = np.linspace(0, 2 * f, 11)
     z = r * r / (4 * f) - f
     assert np.max(np.abs(np.hypot(r, z) - (z + 2 * f))) < 1e-9 * f
+
+
+# --------------------------------------------------------------------------
+# Energy and the paraxial limit
+
+
+@pytest.mark.parametrize("f,w0,rho_max,tol", [(24.5, 8.0, 4.0, 1e-3), (24.5, 8.0, 8.0, 1e-3),
+                                               (49.0, 16.0, 8.0, 3e-4)])
+def test_poynting_flux_through_focal_plane(f, w0, rho_max, tol):
+    """The time-averaged reflected flux 1/2 Re(E x B*) . z through the focal
+    plane equals the incident power 1/2 SS |A|^2 dA (monochromatic analogue of
+    the energy check of Sec. IV.A).  NA = 0.7 (r_max = 0.816 f, the whole
+    mirror below z = 0), unclipped Gaussian; the deviation is the beam model's
+    O(eps^2), eps = 1/(pi w0)."""
+    m = dict(f=f, r_max=0.816 * f, n_r=48, n_theta=48, rim=1)
+    b = dict(profile="gauss", w0=w0, pol="linear")
+    h = 0.1
+    n = int(rho_max / h)
+    x = np.arange(-n, n + 1) * h
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    mask = X ** 2 + Y ** 2 <= rho_max ** 2
+    pts = np.stack([X[mask], Y[mask], np.zeros(mask.sum())], axis=1)
+    E, B = oracle.field(m, b, [1.0], pts)
+    Sz = 0.5 * np.real(E[0, :, 0] * np.conj(B[0, :, 1]) - E[0, :, 1] * np.conj(B[0, :, 0]))
+    flux = Sz.sum() * h * h
+    P_in = 0.5 * oracle.beam_power(b)
+    assert abs(flux / P_in - 1.0) < tol
+
+
+@pytest.mark.parametrize("f,w0", [(1000.0, 50.0), (2000.0, 40.0)])
+def test_paraxial_gaussian_focus(f, w0):
+    """Low NA: the reflected field is the Fresnel propagation of the beam
+    through a thin lens of focal length f at the vertex (z = -f), with the
+    mirror's reflection sign -1.  With q0 = -i k w0^2/2 and
+    1/q1 = 1/q0 - 1/f:  E_x = -(q1/q2) e^{ikz} e^{ik rho^2 / (2 q2)},
+    q2 = q1 + f + z.  This includes the focal shift of a beam of finite
+    Rayleigh range (the waist sits f/(1+(f/z_R)^2) from the vertex).
+    Agreement is O((w0/f)^2)."""
+    k = K0
+    a = 4.0 * w0
+    q0 = -1j * k * w0 ** 2 / 2
+    q1 = 1.0 / (1.0 / q0 - 1.0 / f)
+    wf = 2 * f / (k * w0)
+    zR = k * wf ** 2 / 2
+    pts = np.array([[0, 0, z] for z in np.linspace(-1.5 * zR, 1.5 * zR, 7)] +
+                   [[r, 0, 0] for r in np.linspace(0.3 * wf, 2.5 * wf, 5)] +
+                   [[0.6 * wf, -0.4 * wf, 0.5 * zR]])
+
+    def fresnel(x, y, z):
+        q2 = q1 + f + z
+        return -(q1 / q2) * np.exp(1j * k * z) * np.exp(1j * k * (x * x + y * y) / (2 * q2))
+
+    want = np.array([fresnel(*p) for p in pts])
+    E, B = oracle.field(dict(f=f, r_max=a, n_r=96, n_theta=48, rim=1),
+                        dict(profile="gauss", w0=w0, pol="linear"), [1.0], pts)
+    scale = np.max(np.abs(want))
+    assert np.max(np.abs(E[0, :, 0] - want)) < (w0 / f) ** 2 * scale
+    # transverse plane-wave relation B_y = E_x and weak longitudinal field
+    assert np.max(np.abs(B[0, :, 1] - E[0, :, 0])) < 2 * (w0 / f) * scale
+    assert np.max(np.abs(E[0, :, 1])) < 1e-3 * scale
