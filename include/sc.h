@@ -336,6 +336,15 @@ typedef struct {
     uint64_t graph_replays;  /* launches that replayed a cached graph               */
 } sc_counters;
 
+/*
+ * Failure-path self-test (no counterpart in the paper).  Launches one bounded
+ * wait, of the kind every field kernel uses for its bulk copies and table
+ * hand-overs, on an mbarrier that nothing completes.  The wait gives up
+ * after its wall-time limit (about one second), the kernel returns, and the
+ * call reports SC_ERR_TIMEOUT; the context stays usable.  Synchronizes.
+ */
+sc_status sc_selftest_wait(sc_ctx* ctx);
+
 /* Synchronizes the context stream and returns the counters. */
 sc_status sc_get_counters(sc_ctx* ctx, sc_counters* out);
 sc_status sc_reset_counters(sc_ctx* ctx);

@@ -101,6 +101,7 @@ SIGNATURES = {
     "sc_fetch": (ctypes.c_int, [_VP, ctypes.c_uint64, _VP, _VP]),
     "sc_release": (ctypes.c_int, [_VP, ctypes.c_uint64]),
     "sc_ticket_times": (ctypes.c_int, [_VP, ctypes.c_uint64, _DP, _DP, _DP]),
+    "sc_selftest_wait": (ctypes.c_int, [_VP]),
     "sc_get_counters": (ctypes.c_int, [_VP, ctypes.POINTER(sc_counters)]),
     "sc_reset_counters": (ctypes.c_int, [_VP]),
     "sc_set_option": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_longlong]),

@@ -1915,6 +1915,16 @@ sc_status sc_ticket_times(sc_ctx* ctx, uint64_t ticket, double* t_submit, double
     return SC_OK;
 }
 
+sc_status sc_selftest_wait(sc_ctx* ctx)
+{
+    if (!ctx) return SC_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const int r = sc::launch_wait_selftest(ctx->d_err, ctx->stream);
+    if (r < 0) return cuda_fail(ctx, (cudaError_t)(-r), "self-test launch");
+    return check_device_error(ctx);
+}
+
 sc_status sc_get_counters(sc_ctx* ctx, sc_counters* out)
 {
     if (!ctx || !out) return SC_ERR_INVALID;

@@ -896,6 +896,30 @@ int launch_field_f32(const FieldLaunch& p, cudaStream_t s)
     return launch_field_batch(cls, b, (int)b.n_items, s);
 }
 
+namespace {
+
+// One bounded wait on an mbarrier that nothing ever arrives on: the wait must
+// give up after its wall-time limit and raise ERR_TIMEOUT.
+__global__ void wait_selftest_kernel(int* err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(&bar, 0)) atomicOr(err, ERR_TIMEOUT);
+}
+
+}  // namespace
+
+int launch_wait_selftest(int* err, cudaStream_t s)
+{
+    wait_selftest_kernel<<<1, 32, 0, s>>>(err);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? 1 : -(int)e;
+}
+
 int launch_reduce_f32(const ReduceLaunch& r, cudaStream_t s)
 {
     const long long total = (long long)r.n_pts * r.n_omega;

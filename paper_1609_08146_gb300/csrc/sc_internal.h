@@ -133,6 +133,9 @@ struct IdftLaunch {
 };
 int launch_idft(const IdftLaunch& p, cudaStream_t s);
 
+// Failure-path self-test: one bounded mbarrier wait that nothing completes.
+int launch_wait_selftest(int* err, cudaStream_t s);
+
 // Fixed device scratch of the allocation-free entry point: 64 MiB of static
 // device memory per GPU.  static_scratch() returns its device address on
 // `device` (looked up once per device with that device current).
