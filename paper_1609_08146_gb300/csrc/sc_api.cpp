@@ -802,7 +802,7 @@ sc_status launch_chunks(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch, float2* w
     }
     if (off > ws_n) return fail(ctx, SC_ERR_OOM, "workspace plan exceeds its buffer");
     // per-class descriptor arrays
-    constexpr int kClasses = 12;
+    constexpr int kClasses = sc::kNumClasses;
     std::vector<sc::WorkReq> reqs[kClasses];
     long long items[kClasses] = {};
     for (auto& c : ch) {

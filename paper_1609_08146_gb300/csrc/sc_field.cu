@@ -185,29 +185,10 @@ __device__ __forceinline__ float pair_coefs(const float* nb, int j, float4 pt, f
     return phi;
 }
 
-// One (point, node, omega) evaluation: 26 FP32 pipe ops with the rotation.
-struct Acc12 {
-    float v[kAcc];
-};
-
-__device__ __forceinline__ void eval_one(Acc12& a, const float* co, float k, float2 ph)
-{
-    const float qr = -k * ph.y, qi = k * ph.x;              // q = ik ph
-    const float zr = fmaf(-co[9], ph.x, qr);                // z = q - ph/R
-    const float zi = fmaf(-co[9], ph.y, qi);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        a.v[2 * c] = fmaf(co[c], qr, fmaf(co[3 + c], zr, a.v[2 * c]));
-        a.v[2 * c + 1] = fmaf(co[c], qi, fmaf(co[3 + c], zi, a.v[2 * c + 1]));
-        a.v[6 + 2 * c] = fmaf(co[6 + c], zr, a.v[6 + 2 * c]);
-        a.v[6 + 2 * c + 1] = fmaf(co[6 + c], zi, a.v[6 + 2 * c + 1]);
-    }
-}
-
-// Packed form of the same evaluation for the grouped kernel: accumulators as
-// (re, im) pairs and coefficients stored pre-duplicated as (c, c) pairs, so
-// the 18 accumulation FMAs issue as 9 FFMA2 and z as one more.  Lane-ops per
-// evaluation stay 26; issued instructions drop from 26 to 16.
+// One (point, node, omega) evaluation, packed: accumulators as (re, im) pairs
+// and coefficients pre-duplicated as (c, c) pairs, so the 18 accumulation
+// FMAs issue as 9 FFMA2 and z as one more.  26 FP32 lane-ops per evaluation
+// with the phasor rotation; 16 issued instructions.
 struct AccX2 {
     float2 v[6];  // E_x, E_y, E_z, B_x, B_y, B_z as (re, im)
 };
@@ -223,6 +204,9 @@ __device__ __forceinline__ void eval_x2(AccX2& a, const float2* cp, float k, flo
     }
 }
 
+// Fold one thread's FP32 sums for omegas [n0, n0 + nb) into its compensated
+// partials: (hi, lo) <- (hi, lo) + acc by TwoSum, or a plain store on the
+// first fold.  Each (split, point, omega) entry belongs to exactly one thread.
 template <int NB>
 __device__ __forceinline__ void fold(float2* dst, AccX2* acc, int nb, bool first)
 {
@@ -253,38 +237,6 @@ __device__ __forceinline__ void fold(float2* dst, AccX2* acc, int nb, bool first
         }
 #pragma unroll
         for (int c = 0; c < kAcc / 2; ++c) acc[j].v[c] = make_float2(0.f, 0.f);
-    }
-}
-
-// Fold one thread's FP32 sums for omegas [n0, n0 + nb) into its compensated
-// partials: (hi, lo) <- (hi, lo) + acc by TwoSum, or a plain store on the
-// first fold.  Each (split, point, omega) entry belongs to exactly one thread.
-template <int NB>
-__device__ __forceinline__ void fold(float2* dst, Acc12* acc, int nb, bool first)
-{
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-        if (j < nb) {
-            float4* d4 = reinterpret_cast<float4*>(dst + (size_t)j * kAcc);
-#pragma unroll
-            for (int c = 0; c < kAcc / 2; ++c) {
-                const float a0 = acc[j].v[2 * c], a1 = acc[j].v[2 * c + 1];
-                if (first) {
-                    d4[c] = make_float4(a0, 0.f, a1, 0.f);
-                } else {
-                    const float4 h = d4[c];
-                    const float s0 = h.x + a0, b0 = s0 - h.x;
-                    const float e0 = (h.x - (s0 - b0)) + (a0 - b0);
-                    const float s1 = h.z + a1, b1 = s1 - h.z;
-                    const float e1 = (h.z - (s1 - b1)) + (a1 - b1);
-                    d4[c] = make_float4(s0, h.y + e0, s1, h.w + e1);
-                }
-                // keep the loads of the partials from being hoisted together
-                asm volatile("" ::: "memory");
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < kAcc; ++c) acc[j].v[c] = 0.f;
     }
 }
 
@@ -613,12 +565,19 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
 }
 
 // ------------------------------------------------------------------------
-// Direct kernel: n_omega <= 8 (a single group).  One thread per point computes
-// every pair itself; the CTA shares the staged node tiles.  256 points per item.
+// Direct kernel: n_omega <= 24.  GP threads per point (1, 2 or 4), each
+// owning NB = ceil(n_omega / GP) consecutive omegas (so no omega slot is
+// wasted beyond the last thread's); every thread computes the geometry and the
+// phasors of its pairs itself (no pair table: with so few omegas per pair a
+// shared table would not pay for its producers), and the CTA shares the
+// bulk-copied node tiles.  256 threads, 256 / GP points per item.  The
+// accumulation is the packed (FFMA2) form with two phasor chains, as in the
+// grouped kernel.
 
-template <int NB>
+template <int NB, int GP>
 __global__ void __launch_bounds__(256, 1) field_direct_kernel(BatchLaunch b)
 {
+    constexpr int PPI = 256 / GP;  // points per item
     __shared__ __align__(128) float nodebuf[2 * kTileFloats];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ long long slot;
@@ -633,7 +592,8 @@ __global__ void __launch_bounds__(256, 1) field_direct_kernel(BatchLaunch b)
     for (long long item = next_item(b, &slot, -1); item < b.n_items; item = next_item(b, &slot, item)) {
         const Item w = decode(b, item);
         const FieldLaunch& p = w.r->f;
-        const int pt = w.pbi * 256 + tid;
+        const int pt = w.pbi * PPI + tid / GP;
+        const int g = tid % GP;
         const int split = w.split;
         int t0, t1;
         split_range(p, split, t0, t1);
@@ -643,8 +603,10 @@ __global__ void __launch_bounds__(256, 1) field_direct_kernel(BatchLaunch b)
         load_point(p.pts, p.n_pts, pt, P);
         float kv[NB];
 #pragma unroll
-        for (int j = 0; j < NB; ++j) kv[j] = (float)(6.283185307179586 * (om0 + (double)j * dom));
-        const float w0h = p.om_hi0, w0l = p.om_lo0, d1h = p.dom_hi, d1l = p.dom_lo;
+        for (int j = 0; j < NB; ++j) kv[j] = (float)(6.283185307179586 * (om0 + (double)(g * NB + j) * dom));
+        const double wg = om0 + (double)(g * NB) * dom;  // first omega of this thread
+        const float wgh = (float)wg, wgl = (float)(wg - (double)wgh);
+        const float d1h = p.dom_hi, d1l = p.dom_lo;
         const int nt = t1 - t0;
         unsigned issued[2] = {0, 0}, waited[2] = {0, 0};
         if (tid == 0) {
@@ -656,14 +618,19 @@ __global__ void __launch_bounds__(256, 1) field_direct_kernel(BatchLaunch b)
                 issued[nbi]++;
             }
         }
-        Acc12 acc[NB];
+        AccX2 acc[NB];
 #pragma unroll
         for (int j = 0; j < NB; ++j)
 #pragma unroll
-            for (int c = 0; c < kAcc; ++c) acc[j].v[c] = 0.f;
-        const bool pt_ok = pt < p.n_pts;
-        const int nb_ok = min(NB, p.n_omega);
-        float2* dst = p.ws + ((size_t)split * p.n_pts + pt) * (size_t)p.n_omega * kAcc;
+            for (int c = 0; c < kAcc / 2; ++c) acc[j].v[c] = make_float2(0.f, 0.f);
+        const bool pt_ok = pt < p.n_pts && g * NB < p.n_omega;
+        const int nb_ok = min(NB, p.n_omega - g * NB);
+        auto fold_now = [&](bool first) {
+            if (pt_ok) {
+                float2* dst = p.ws + (((size_t)split * p.n_pts + pt) * (size_t)p.n_omega + (size_t)g * NB) * kAcc;
+                fold<NB>(dst, acc, nb_ok, first);
+            }
+        };
         for (int it = 0; it < nt; ++it) {
             const long long tg = tbase + it;
             const int nbi = (int)(tg & 1);
@@ -674,17 +641,28 @@ __global__ void __launch_bounds__(256, 1) field_direct_kernel(BatchLaunch b)
             for (int j = 0; j < kTile; ++j) {
                 float co[10];
                 const float phi = pair_coefs(nb, j, P, co);
-                float2 ph = phasor_2wphi(w0h, w0l, phi);
-                float2 rot = make_float2(1.f, 0.f);
-                if (NB > 1) rot = phasor_2wphi(d1h, d1l, phi);
+                const float2 cp[10] = {make_float2(co[0], co[0]), make_float2(co[1], co[1]),
+                                       make_float2(co[2], co[2]), make_float2(co[3], co[3]),
+                                       make_float2(co[4], co[4]), make_float2(co[5], co[5]),
+                                       make_float2(co[6], co[6]), make_float2(co[7], co[7]),
+                                       make_float2(co[8], co[8]), make_float2(-co[9], -co[9])};
+                float2 pe = phasor_2wphi(wgh, wgl, phi);
+                if (NB == 1) {
+                    eval_x2(acc[0], cp, kv[0], pe);
+                } else {
+                    const float2 rot = phasor_2wphi(d1h, d1l, phi);
+                    const float2 rot2 = cmul(rot, rot);
+                    float2 po = cmul(pe, rot);
 #pragma unroll
-                for (int jj = 0; jj < NB; ++jj) {
-                    eval_one(acc[jj], co, kv[jj], ph);
-                    if (jj + 1 < NB) ph = cmul(ph, rot);
+                    for (int jj = 0; jj < NB; jj += 2) {
+                        eval_x2(acc[jj], cp, kv[jj], pe);
+                        if (jj + 1 < NB) eval_x2(acc[jj + 1], cp, kv[jj + 1], po);
+                        if (jj + 2 < NB) pe = cmul(pe, rot2);
+                        if (jj + 3 < NB) po = cmul(po, rot2);
+                    }
                 }
             }
-            if (((it + 1) % p.flush_tiles == 0 || it + 1 == nt) && pt_ok)
-                fold<NB>(dst, acc, nb_ok, it + 1 <= p.flush_tiles);
+            if ((it + 1) % p.flush_tiles == 0 || it + 1 == nt) fold_now(it + 1 <= p.flush_tiles);
             __syncthreads();
             if (tid == 0 && it + 2 < nt) {
                 fence_proxy_async();
@@ -705,7 +683,7 @@ __global__ void __launch_bounds__(256, 1) field_direct_kernel(BatchLaunch b)
                     waited[s]++;
                 }
         }
-        if (nt == 0 && pt_ok) fold<NB>(dst, acc, nb_ok, true);
+        if (nt == 0) fold_now(true);
         tbase += nt;
     }
     if (timed_out) atomicOr(b.err, ERR_TIMEOUT);
@@ -808,10 +786,10 @@ int launch_grouped(const BatchLaunch& b, int grid, cudaStream_t s)
     return e == cudaSuccess ? 1 : -(int)e;
 }
 
-template <int NB>
+template <int NB, int GP>
 int launch_direct(const BatchLaunch& b, int grid, cudaStream_t s)
 {
-    field_direct_kernel<NB><<<grid, 256, 0, s>>>(b);
+    field_direct_kernel<NB, GP><<<grid, 256, 0, s>>>(b);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? 1 : -(int)e;
 }
@@ -828,30 +806,56 @@ void grouped_shape(int device, int* ppc, int* slots)
 
 int field_class(int n_omega)
 {
-    if (n_omega <= 1) return 0;
-    if (n_omega <= 2) return 1;
-    if (n_omega <= 4) return 2;
-    if (n_omega <= 8) return 3;
+    // 0..7   direct, 1 thread per point, NB = n_omega (1..8)
+    // 8..11  direct, 2 threads per point, NB = ceil(n_omega / 2) (5..8)
+    // 12..13 direct, 4 threads per point, NB = ceil(n_omega / 4) (5..6)
+    // 14     grouped, 4 threads per point (25..32 omegas: the shared pair
+    //        table beats per-thread geometry once a thread owns 7..8 omegas)
+    // 15..20 grouped, TPP = 8, 16, ..., 256 threads per point
+    if (n_omega <= 8) return std::max(1, n_omega) - 1;
+    if (n_omega <= 16) return 8 + (n_omega + 1) / 2 - 5;
+    if (n_omega <= 24) return 12 + (n_omega + 3) / 4 - 5;
+    if (n_omega <= 32) return 14;
     const int G = (n_omega + kB - 1) / kB;
-    int cls = 4, tpp = 2;
+    int cls = 15, tpp = 8;
     while (tpp < G) { tpp *= 2; ++cls; }
-    return cls;  // 4: TPP 2 ... 11: TPP 256
+    return cls;
 }
+
+namespace {
+
+template <int NB, int GP>
+void direct_shape(int device, int* ppc, int* slots)
+{
+    *ppc = 256 / GP;
+    *slots = resident(field_direct_kernel<NB, GP>, 256, 0, device);
+}
+
+}  // namespace
 
 void field_shape(int cls, int device, int* ppc, int* slots)
 {
     switch (cls) {
-    case 0: *ppc = 256; *slots = resident(field_direct_kernel<1>, 256, 0, device); return;
-    case 1: *ppc = 256; *slots = resident(field_direct_kernel<2>, 256, 0, device); return;
-    case 2: *ppc = 256; *slots = resident(field_direct_kernel<4>, 256, 0, device); return;
-    case 3: *ppc = 256; *slots = resident(field_direct_kernel<8>, 256, 0, device); return;
-    case 4: return grouped_shape<2>(device, ppc, slots);
-    case 5: return grouped_shape<4>(device, ppc, slots);
-    case 6: return grouped_shape<8>(device, ppc, slots);
-    case 7: return grouped_shape<16>(device, ppc, slots);
-    case 8: return grouped_shape<32>(device, ppc, slots);
-    case 9: return grouped_shape<64>(device, ppc, slots);
-    case 10: return grouped_shape<128>(device, ppc, slots);
+    case 0: return direct_shape<1, 1>(device, ppc, slots);
+    case 1: return direct_shape<2, 1>(device, ppc, slots);
+    case 2: return direct_shape<3, 1>(device, ppc, slots);
+    case 3: return direct_shape<4, 1>(device, ppc, slots);
+    case 4: return direct_shape<5, 1>(device, ppc, slots);
+    case 5: return direct_shape<6, 1>(device, ppc, slots);
+    case 6: return direct_shape<7, 1>(device, ppc, slots);
+    case 7: return direct_shape<8, 1>(device, ppc, slots);
+    case 8: return direct_shape<5, 2>(device, ppc, slots);
+    case 9: return direct_shape<6, 2>(device, ppc, slots);
+    case 10: return direct_shape<7, 2>(device, ppc, slots);
+    case 11: return direct_shape<8, 2>(device, ppc, slots);
+    case 12: return direct_shape<5, 4>(device, ppc, slots);
+    case 13: return direct_shape<6, 4>(device, ppc, slots);
+    case 14: return grouped_shape<4>(device, ppc, slots);
+    case 15: return grouped_shape<8>(device, ppc, slots);
+    case 16: return grouped_shape<16>(device, ppc, slots);
+    case 17: return grouped_shape<32>(device, ppc, slots);
+    case 18: return grouped_shape<64>(device, ppc, slots);
+    case 19: return grouped_shape<128>(device, ppc, slots);
     default: return grouped_shape<256>(device, ppc, slots);
     }
 }
@@ -860,18 +864,27 @@ int launch_field_batch(int cls, const BatchLaunch& b, int grid, cudaStream_t s)
 {
     if (grid < 1) return 0;
     switch (cls) {
-    case 0: return launch_direct<1>(b, grid, s);
-    case 1: return launch_direct<2>(b, grid, s);
-    case 2: return launch_direct<4>(b, grid, s);
-    case 3: return launch_direct<8>(b, grid, s);
-    case 4: return launch_grouped<2>(b, grid, s);
-    case 5: return launch_grouped<4>(b, grid, s);
-    case 6: return launch_grouped<8>(b, grid, s);
-    case 7: return launch_grouped<16>(b, grid, s);
-    case 8: return launch_grouped<32>(b, grid, s);
-    case 9: return launch_grouped<64>(b, grid, s);
-    case 10: return launch_grouped<128>(b, grid, s);
-    case 11: return launch_grouped<256>(b, grid, s);
+    case 0: return launch_direct<1, 1>(b, grid, s);
+    case 1: return launch_direct<2, 1>(b, grid, s);
+    case 2: return launch_direct<3, 1>(b, grid, s);
+    case 3: return launch_direct<4, 1>(b, grid, s);
+    case 4: return launch_direct<5, 1>(b, grid, s);
+    case 5: return launch_direct<6, 1>(b, grid, s);
+    case 6: return launch_direct<7, 1>(b, grid, s);
+    case 7: return launch_direct<8, 1>(b, grid, s);
+    case 8: return launch_direct<5, 2>(b, grid, s);
+    case 9: return launch_direct<6, 2>(b, grid, s);
+    case 10: return launch_direct<7, 2>(b, grid, s);
+    case 11: return launch_direct<8, 2>(b, grid, s);
+    case 12: return launch_direct<5, 4>(b, grid, s);
+    case 13: return launch_direct<6, 4>(b, grid, s);
+    case 14: return launch_grouped<4>(b, grid, s);
+    case 15: return launch_grouped<8>(b, grid, s);
+    case 16: return launch_grouped<16>(b, grid, s);
+    case 17: return launch_grouped<32>(b, grid, s);
+    case 18: return launch_grouped<64>(b, grid, s);
+    case 19: return launch_grouped<128>(b, grid, s);
+    case 20: return launch_grouped<256>(b, grid, s);
     default: return -(int)cudaErrorInvalidValue;
     }
 }

@@ -75,8 +75,10 @@ struct BatchLaunch {
     int* err;
 };
 
-// Kernel class for a chunk of n_omega (<= 2048) omegas: 0..3 direct kernel
-// with 1, 2, 4, 8 omegas per thread; 4 + log2(TPP/2) grouped kernel.
+// Kernel class for a chunk of n_omega (<= 2048) omegas: 0..13 the direct
+// kernel (1, 2 or 4 threads per point, 1..8 omegas per thread), 14..20 the
+// grouped kernel with 4 ... 256 threads per point.
+constexpr int kNumClasses = 21;
 int field_class(int n_omega);
 // Observation points per work item and resident CTAs on the device.
 void field_shape(int cls, int device, int* points_per_item, int* resident_ctas);
