@@ -3,8 +3,8 @@
 One step = one pass of the whole path over the broadband workload
 (512 x 512 mirror nodes, 256 uniform omegas, 4160 focal points, 10 fs pulse
 at f = 62,500 lambda0, NA = 1): spectrum a_n (Eqs. 16-18), per-pair geometry
-with the compensated phase, the 26-op field-sum inner loop with the omega
-rotation recurrence (Eq. 11), the FP64 cross-split reduction and epilogue,
+with the compensated phase, the 24-op field-sum inner loop with the
+three-term omega recurrence of the phasor (Eq. 11), the FP64 cross-split reduction and epilogue,
 and the inverse transform to 512 time samples (Eq. 13).
 
 Metric: obs x node x omega evaluations per second (surface nodes), whole job.
@@ -15,7 +15,9 @@ Metric: obs x node x omega evaluations per second (surface nodes), whole job.
           pinned host memory in, time-domain E(t), B(t) back to pinned host
           memory, copies inside the timed region.
   roofline  the dominant kernel (FP32 field sum) against the FP32-pipe peak
-          SMs x 128 lanes x clock at 26 FP32 lane-ops per evaluation.
+          SMs x 128 lanes x clock at 24 FP32 lane-ops per evaluation (the
+          form the kernel computes; a plain complex rotation per omega would
+          be 26, the unfactored sum 28).
   cpu_baseline  the FP64 oracle on the host cores over a bounded sample of
           the same workload.
 --impl reference times that oracle as the reference arm.
@@ -39,7 +41,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-OPS_PER_EVAL = 26  # FP32 lane-ops per (point, node, omega) in the field-sum inner loop
+OPS_PER_EVAL = 24  # FP32 lane-ops per (point, node, omega) in the field-sum inner loop
 FIELD_KERNEL = "field_grouped_kernel<32>"
 PROFILE_JSON = os.path.join(ROOT, "profiles", "field_grouped_broadband.json")
 FIELD_SRC = os.path.join(ROOT, "paper_1609_08146_gb300", "csrc", "sc_field.cu")

@@ -15,9 +15,13 @@
 //     E += U q + V z,   B += Wv z,
 //     q = ik ph,  z = (ik - 1/R) ph,
 //     U = J/R,  V = rho R^/R,  Wv = U x R^.
-// That is 26 FP32 pipe operations per (point, node, omega): 4 for the phasor
-// recurrence ph <- ph e^{i dk Phi} (uniform omega grid: one complex rotation
-// per step instead of a sincos), 2 for q, 2 for z, 12 for E, 6 for B.
+// On the uniform omega grid the phasors of consecutive omegas follow the
+// three-term recurrence ph_{n+1} = c ph_n - ph_{n-1}, c = 2 cos(dk Phi), one
+// packed FMA (2 lane-ops) per step instead of a sincos; a thread's first two
+// phasors come from its seed and one complex rotation e^{i dk Phi}.  With 8
+// omegas per thread that is 2 lane-ops per evaluation for the phasor, plus 2
+// for q, 2 for z, 12 for E and 6 for B: 24 FP32 pipe operations per (point,
+// node, omega).
 // Boundary (rim) nodes carry U = 0 and rho = (J . m^) dl / (2 pi); their E sum
 // is multiplied by i/k_n in the epilogue, which reproduces the line integral
 // -(2/ik) O grad g [n x (n x B_inc)] . dl of Eq. 11.
@@ -29,7 +33,7 @@
 //     the 12 coefficients, the rotation e^{i dk Phi} and the seed phasor of
 //     every omega group, into a shared-memory pair table (double buffered);
 //   * phase 2: thread (point, group) owns 8 consecutive omegas of one point
-//     and runs the 26-op inner loop over the tile's nodes, accumulators in
+//     and runs the 24-op inner loop over the tile's nodes, accumulators in
 //     registers (12 per omega);
 //   * each CTA sums one split of the node range.  Every flush_tiles tiles
 //     (2048 nodes by default) the FP32 register sums are folded into a
@@ -187,8 +191,8 @@ __device__ __forceinline__ float pair_coefs(const float* nb, int j, float4 pt, f
 
 // One (point, node, omega) evaluation, packed: accumulators as (re, im) pairs
 // and coefficients pre-duplicated as (c, c) pairs, so the 18 accumulation
-// FMAs issue as 9 FFMA2 and z as one more.  26 FP32 lane-ops per evaluation
-// with the phasor rotation; 16 issued instructions.
+// FMAs issue as 9 FFMA2 and z as one more: 22 FP32 lane-ops in 12 issued
+// instructions, plus the phasor step.
 struct AccX2 {
     float2 v[6];  // E_x, E_y, E_z, B_x, B_y, B_z as (re, im)
 };
@@ -206,7 +210,9 @@ __device__ __forceinline__ void eval_x2(AccX2& a, const float2* cp, float k, flo
 
 // Fold one thread's FP32 sums for omegas [n0, n0 + nb) into its compensated
 // partials: (hi, lo) <- (hi, lo) + acc by TwoSum, or a plain store on the
-// first fold.  Each (split, point, omega) entry belongs to exactly one thread.
+// first fold.  Slots j with j & 2 set hold the negated sums (the sign that the
+// phasor recurrence carries) and are folded with the sign taken out.  Each
+// (split, point, omega) entry belongs to exactly one thread.
 template <int NB>
 __device__ __forceinline__ void fold(float2* dst, AccX2* acc, int nb, bool first)
 {
@@ -214,17 +220,18 @@ __device__ __forceinline__ void fold(float2* dst, AccX2* acc, int nb, bool first
     for (int j = 0; j < NB; ++j) {
         if (j < nb) {
             float4* d4 = reinterpret_cast<float4*>(dst + (size_t)j * kAcc);
+            const float sg = (j & 2) ? -1.f : 1.f;  // sign carried by the phasor recurrence
             if (first) {
 #pragma unroll
                 for (int c = 0; c < kAcc / 2; ++c)
-                    d4[c] = make_float4(acc[j].v[c].x, 0.f, acc[j].v[c].y, 0.f);
+                    d4[c] = make_float4(sg * acc[j].v[c].x, 0.f, sg * acc[j].v[c].y, 0.f);
             } else {
                 float4 h[kAcc / 2];
 #pragma unroll
                 for (int c = 0; c < kAcc / 2; ++c) h[c] = d4[c];  // six loads in flight together
 #pragma unroll
                 for (int c = 0; c < kAcc / 2; ++c) {
-                    const float a0 = acc[j].v[c].x, a1 = acc[j].v[c].y;
+                    const float a0 = sg * acc[j].v[c].x, a1 = sg * acc[j].v[c].y;
                     const float s0 = h[c].x + a0, b0 = s0 - h[c].x;
                     const float e0 = (h[c].x - (s0 - b0)) + (a0 - b0);
                     const float s1 = h[c].z + a1, b1 = s1 - h[c].z;
@@ -311,7 +318,7 @@ __device__ __forceinline__ Item decode(const BatchLaunch& b, long long item)
 // Grouped kernel: G = ceil(n_omega / 8) >= 2 omega groups per point.
 // Warp-specialised, 384 threads:
 //   consumers  warps 0-7 (256 threads): thread (point pl, group g) owns 8
-//              consecutive omegas of one point and runs only the 26-op loop;
+//              consecutive omegas of one point and runs only the 24-op loop;
 //              PPC = 256 / TPP points per item, TPP = threads per point
 //              (power of two >= G, <= 256);
 //   producers  warps 8-11 (128 threads): stage node tiles with bulk copies and
@@ -436,29 +443,32 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
                 for (int j = 0; j < L::TC; ++j) {
                     const float4* c4 = reinterpret_cast<const float4*>(cb + j * L::COEF);
                     float2 cp[10];
-                    float2 rot, rot2;
+                    float2 rot, cc, ncc;
                     {
                         const float4 a0 = c4[0], a1 = c4[1], a2 = c4[2], a3 = c4[3], a4 = c4[4], a5 = c4[5];
+                        ncc = *reinterpret_cast<const float2*>(c4 + 6);
                         cp[0] = make_float2(a0.x, a0.y); cp[1] = make_float2(a0.z, a0.w);
                         cp[2] = make_float2(a1.x, a1.y); cp[3] = make_float2(a1.z, a1.w);
                         cp[4] = make_float2(a2.x, a2.y); cp[5] = make_float2(a2.z, a2.w);
                         cp[6] = make_float2(a3.x, a3.y); cp[7] = make_float2(a3.z, a3.w);
                         cp[8] = make_float2(a4.x, a4.y); cp[9] = make_float2(a4.z, a4.w);
                         rot = make_float2(a5.x, a5.y);
-                        rot2 = make_float2(a5.z, a5.w);
+                        cc = make_float2(a5.z, a5.w);
                     }
-                    // two interleaved phasor chains (even and odd omegas) stepping by
-                    // e^{2i dk Phi}: half the dependent depth of one chain
-                    float2 pe = sb[j * L::SROW];
-                    float2 po = cmul(pe, rot);
+                    // one phasor chain by the three-term recurrence; the phasors of
+                    // slots 2, 3, 6, 7 carry a minus sign so that every step is a
+                    // single FFMA2 with no negated operand (c' alternates -c, +c),
+                    // and fold() takes the sign back out of those slots
+                    float2 p0 = sb[j * L::SROW];
+                    float2 p1 = cmul(p0, rot);
+                    eval_x2(acc[0], cp, kv[0], p0);
+                    eval_x2(acc[1], cp, kv[1], p1);
 #pragma unroll
-                    for (int jj = 0; jj < kB; jj += 2) {
-                        eval_x2(acc[jj], cp, kv[jj], pe);
-                        eval_x2(acc[jj + 1], cp, kv[jj + 1], po);
-                        if (jj + 2 < kB) {
-                            pe = cmul(pe, rot2);
-                            po = cmul(po, rot2);
-                        }
+                    for (int jj = 2; jj < kB; ++jj) {
+                        const float2 pn = __ffma2_rn((jj & 1) ? cc : ncc, p1, p0);
+                        eval_x2(acc[jj], cp, kv[jj], pn);
+                        p0 = p1;
+                        p1 = pn;
                     }
                 }
                 // hand the table back: one arrival per consumer warp, after the warp is done
@@ -503,14 +513,16 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
                     const float phi = pair_coefs(nb, sub * L::TC + j, spts[pq], co);
                     if (seg == 0) {
                         const float2 rot = phasor_2wphi(d1h, d1l, phi);
-                        const float2 rot2 = cmul(rot, rot);
+                        const float c2 = 2.f * rot.x;
                         float4* c4 = reinterpret_cast<float4*>(cb + (size_t)q * L::COEF);
                         c4[0] = make_float4(co[0], co[0], co[1], co[1]);
                         c4[1] = make_float4(co[2], co[2], co[3], co[3]);
                         c4[2] = make_float4(co[4], co[4], co[5], co[5]);
                         c4[3] = make_float4(co[6], co[6], co[7], co[7]);
                         c4[4] = make_float4(co[8], co[8], -co[9], -co[9]);
-                        c4[5] = make_float4(rot.x, rot.y, rot2.x, rot2.y);
+                        // rotation, and (c, c), (-c, -c) for the three-term recurrence
+                        c4[5] = make_float4(rot.x, rot.y, c2, c2);
+                        *reinterpret_cast<float2*>(c4 + 6) = make_float2(-c2, -c2);
                     }
                     const int g0 = seg * 32, g1 = min(G, g0 + 32);
                     if (g0 < g1) {
@@ -571,8 +583,8 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
 // phasors of its pairs itself (no pair table: with so few omegas per pair a
 // shared table would not pay for its producers), and the CTA shares the
 // bulk-copied node tiles.  256 threads, 256 / GP points per item.  The
-// accumulation is the packed (FFMA2) form with two phasor chains, as in the
-// grouped kernel.
+// accumulation is the packed (FFMA2) form with the three-term phasor
+// recurrence, as in the grouped kernel.
 
 template <int NB, int GP>
 __global__ void __launch_bounds__(256, 1) field_direct_kernel(BatchLaunch b)
@@ -651,14 +663,18 @@ __global__ void __launch_bounds__(256, 1) field_direct_kernel(BatchLaunch b)
                     eval_x2(acc[0], cp, kv[0], pe);
                 } else {
                     const float2 rot = phasor_2wphi(d1h, d1l, phi);
-                    const float2 rot2 = cmul(rot, rot);
-                    float2 po = cmul(pe, rot);
+                    const float2 cc = make_float2(2.f * rot.x, 2.f * rot.x);
+                    const float2 ncc = make_float2(-2.f * rot.x, -2.f * rot.x);
+                    float2 p0 = pe;
+                    float2 p1 = cmul(pe, rot);
+                    eval_x2(acc[0], cp, kv[0], p0);
+                    eval_x2(acc[1], cp, kv[1], p1);
 #pragma unroll
-                    for (int jj = 0; jj < NB; jj += 2) {
-                        eval_x2(acc[jj], cp, kv[jj], pe);
-                        if (jj + 1 < NB) eval_x2(acc[jj + 1], cp, kv[jj + 1], po);
-                        if (jj + 2 < NB) pe = cmul(pe, rot2);
-                        if (jj + 3 < NB) po = cmul(po, rot2);
+                    for (int jj = 2; jj < NB; ++jj) {
+                        const float2 pn = __ffma2_rn((jj & 1) ? cc : ncc, p1, p0);
+                        eval_x2(acc[jj], cp, kv[jj], pn);
+                        p0 = p1;
+                        p1 = pn;
                     }
                 }
             }
