@@ -64,6 +64,7 @@ class _Beam(ctypes.Structure):
         ("pol_angle", ctypes.c_double),
         ("r_norm", ctypes.c_double),
         ("zern", ctypes.POINTER(ctypes.c_double)),
+        ("order", ctypes.c_int),
     ]
 
 
@@ -86,6 +87,9 @@ def _load():
         lib.or_field.argtypes = [
             ctypes.POINTER(_Mirror), ctypes.POINTER(_Beam), ctypes.c_int, ctypes.c_int, _DP, _DP,
             ctypes.c_int, _DP, _DP, _DP, ctypes.c_int,
+        ]
+        lib.or_incident.argtypes = [
+            ctypes.POINTER(_Beam), ctypes.c_double, ctypes.c_int, _DP, ctypes.c_int, _DP, _DP, _DP,
         ]
         lib.or_spectrum.argtypes = [
             ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
@@ -118,7 +122,7 @@ def _beam(b: dict, keep: list) -> _Beam:
         profile=PROFILES[b.get("profile", "gauss")], sg_order=int(b.get("sg_order", 4)),
         pol=POLS[b.get("pol", "linear")], n_zern=int(z.size), w0=float(b.get("w0", 1.0)),
         pol_angle=float(b.get("pol_angle", 0.0)), r_norm=float(b.get("r_norm", 1.0)),
-        zern=_ptr(z) if z.size else None,
+        zern=_ptr(z) if z.size else None, order=int(b.get("order", 0)),
     )
 
 
@@ -166,7 +170,22 @@ def field(mirror: dict, beam: dict, omegas, pts, amp=None, form: str = "stokes",
         int(threads),
     )
     if rc != 0:
-        raise ValueError("invalid mirror parameters")
+        raise ValueError("invalid mirror or beam parameters")
+    return E, B
+
+
+def incident(beam: dict, omegas, pts, zref: float):
+    """Incident field (E_inc, B_inc) [n_omega, n_pts, 3] of readings R4 / R14
+    (beam["order"] = 1 adds the first-order longitudinal terms), unit a_n,
+    phase reference exp(-ik(z + zref))."""
+    om = np.ascontiguousarray(np.atleast_1d(omegas), dtype=np.float64)
+    p = np.ascontiguousarray(np.asarray(pts, dtype=np.float64).reshape(-1, 3))
+    E = np.zeros((om.size, p.shape[0], 3), dtype=np.complex128)
+    B = np.zeros_like(E)
+    keep: list = []
+    b = _beam(beam, keep)
+    _load().or_incident(ctypes.byref(b), float(zref), om.size, _ptr(om), p.shape[0], _ptr(p),
+                        _ptr(E.view(np.float64)), _ptr(B.view(np.float64)))
     return E, B
 
 

@@ -48,6 +48,15 @@
  *       energy per unit k includes |d lambda / dk| = lambda^2 / (2 pi).
  *   R6  units: lambda0 = c = 1, k = 2 pi omega with omega in units of
  *       omega0 = 2 pi c / lambda0; time in lambda0 / c.
+ *   R14 first-order incident field (beam order 1): the collimated beam of R4
+ *       is not divergence-free at O(eps), eps = lambda / (pi w0) (Sec. III.A).
+ *       Order 1 adds the longitudinal terms that make div E = div B = 0 and
+ *       leave Faraday's and Ampere's laws violated only at O(eps^2):
+ *         E_z = -(i/k) div_perp(e_perp exp(ikW)) exp(-ik(z + z_ref)),
+ *         B_z = -(i/k) div_perp(b_perp exp(ikW)) exp(-ik(z + z_ref)),
+ *       b_perp = (-z) x e_perp; B_perp stays (-z) x E_perp.  Here the
+ *       transverse divergences are taken by fourth-order central
+ *       differences of step 1e-3 w0 (the library uses closed forms).
  *
  * Output layout: E[n_omega][n_pts][3] complex, stored as interleaved doubles
  * (re, im); same for B.
@@ -88,6 +97,7 @@ typedef struct {
     double pol_angle; /* direction of linear polarisation in the xy-plane      */
     double r_norm;    /* radius of the Zernike unit disk                       */
     const double* zern;
+    int order;        /* 0: collimated beam (R4); 1: plus the O(eps) terms (R14) */
 } or_beam;
 
 /* ------------------------------------------------------------------------ */
@@ -223,6 +233,41 @@ static double beam_opd(const or_beam* bm, double x, double y)
     return w;
 }
 
+/* Transverse envelope component c of the incident beam at (x, y), with the
+ * aberration phase: c = 0, 1 the x, y components of e_perp exp(ikW), c = 2, 3
+ * those of b_perp exp(ikW), b_perp = (-z) x e_perp = (e_y, -e_x). */
+static cplx envelope(const or_beam* bm, double k, double x, double y, int c)
+{
+    double es[3];
+    beam_field(bm, x, y, es);
+    cplx ph = cexp(I * k * beam_opd(bm, x, y));
+    switch (c) {
+    case 0: return es[0] * ph;
+    case 1: return es[1] * ph;
+    case 2: return es[1] * ph;
+    default: return -es[0] * ph;
+    }
+}
+
+/* d/dx of component cx plus d/dy of component cy, fourth-order central
+ * differences of step h = 1e-3 w0 (truncation ~ h^4, far below FP64 needs) */
+static cplx div_perp(const or_beam* bm, double k, double x, double y, int cx, int cy)
+{
+    const double h = 1e-3 * bm->w0;
+    cplx dx = (-envelope(bm, k, x + 2 * h, y, cx) + 8.0 * envelope(bm, k, x + h, y, cx) -
+               8.0 * envelope(bm, k, x - h, y, cx) + envelope(bm, k, x - 2 * h, y, cx)) / (12.0 * h);
+    cplx dy = (-envelope(bm, k, x, y + 2 * h, cy) + 8.0 * envelope(bm, k, x, y + h, cy) -
+               8.0 * envelope(bm, k, x, y - h, cy) + envelope(bm, k, x, y - 2 * h, cy)) / (12.0 * h);
+    return dx + dy;
+}
+
+/* longitudinal terms of reading R14 without the phase exp(-ik(z + z_ref)) */
+static void longitudinal(const or_beam* bm, double k, double x, double y, cplx* ez, cplx* bz)
+{
+    *ez = -(I / k) * div_perp(bm, k, x, y, 0, 1);
+    *bz = -(I / k) * div_perp(bm, k, x, y, 2, 3);
+}
+
 /* beam power integral SS |f_E|^2 dA over the transverse plane (Eq. 16 with
  * Re(f_E x f_B*) . dA = |f_E|^2 dA for the collimated beam), by plain
  * trapezoid quadrature in rho on a fine grid -- deliberately numerical. */
@@ -317,6 +362,13 @@ static void field_at(const or_mirror* m, const or_beam* bm, int form, double k,
             /* E_inc and B_inc = (-z) x E_inc at the node, with g's phase attached */
             cplx Einc[3] = {es[0] * ph, es[1] * ph, 0.0};
             cplx Binc[3] = {es[1] * ph, -es[0] * ph, 0.0};
+            if (bm->order >= 1) {
+                cplx ez, bz;
+                longitudinal(bm, k, x, y, &ez, &bz);
+                cplx pp = cexp(I * k * (R - (z + zref)));
+                Einc[2] = ez * pp;
+                Binc[2] = bz * pp;
+            }
             cplx nh[3] = {nhat[0], nhat[1], nhat[2]};
             cplx J[3];
             ccross(nh, Binc, J); /* n x B_inc */
@@ -367,6 +419,11 @@ static void field_at(const or_mirror* m, const or_beam* bm, int form, double k,
                 double Rh[3] = {d[0] / R, d[1] / R, d[2] / R};
                 cplx ph = cexp(I * k * (R - (z + zref) + W));
                 cplx Binc[3] = {es[1] * ph, -es[0] * ph, 0.0};
+                if (bm->order >= 1) {
+                    cplx ez, bz;
+                    longitudinal(bm, k, x, y, &ez, &bz);
+                    Binc[2] = bz * cexp(I * k * (R - (z + zref)));
+                }
                 cplx t1[3], t2[3];
                 ccross(nh, Binc, t1);
                 ccross(nh, t1, t2); /* n x (n x B_inc) */
@@ -376,6 +433,41 @@ static void field_at(const or_mirror* m, const or_beam* bm, int form, double k,
             }
         }
     }
+}
+
+/*
+ * Incident field E_inc, B_inc of readings R4 / R14 at arbitrary points for
+ * n_omega frequencies (unit a_n), phase reference exp(-ik(z + z_ref)).
+ * Layout as or_field's outputs.  Returns 0.
+ */
+int or_incident(const or_beam* bm, double zref, int n_omega, const double* omega, int n_pts,
+                const double* pts, double* E_out, double* B_out)
+{
+    for (int n = 0; n < n_omega; ++n) {
+        double k = 2.0 * OR_PI * omega[n];
+        for (int p = 0; p < n_pts; ++p) {
+            double x = pts[3 * p], y = pts[3 * p + 1], z = pts[3 * p + 2];
+            double es[3];
+            beam_field(bm, x, y, es);
+            cplx ph = cexp(I * k * (beam_opd(bm, x, y) - (z + zref)));
+            cplx E[3] = {es[0] * ph, es[1] * ph, 0.0}, B[3] = {es[1] * ph, -es[0] * ph, 0.0};
+            if (bm->order >= 1) {
+                cplx ez, bz;
+                longitudinal(bm, k, x, y, &ez, &bz);
+                cplx pp = cexp(-I * k * (z + zref));
+                E[2] = ez * pp;
+                B[2] = bz * pp;
+            }
+            for (int c = 0; c < 3; ++c) {
+                long o = 2 * (((long)n * n_pts + p) * 3 + c);
+                E_out[o] = creal(E[c]);
+                E_out[o + 1] = cimag(E[c]);
+                B_out[o] = creal(B[c]);
+                B_out[o + 1] = cimag(B[c]);
+            }
+        }
+    }
+    return 0;
 }
 
 /*
@@ -391,6 +483,7 @@ int or_field(const or_mirror* m, const or_beam* bm, int form, int n_omega, const
 {
     if (m->n_r < 1 || m->n_theta < 1 || m->r_max <= m->r_min || m->r_min < 0.0) return 1;
     if (m->surface == 0 && m->f <= 0.0) return 1;
+    if (bm->order >= 1 && bm->profile == 2) return 1; /* a top-hat has no transverse derivative */
     double* gl_r = (double*)malloc(sizeof(double) * m->n_r);
     double* gl_w = (double*)malloc(sizeof(double) * m->n_r);
     or_gauss_legendre(m->n_r, m->r_min, m->r_max, gl_r, gl_w);

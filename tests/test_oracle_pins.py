@@ -473,3 +473,103 @@ def test_paraxial_gaussian_focus(f, w0):
     # transverse plane-wave relation B_y = E_x and weak longitudinal field
     assert np.max(np.abs(B[0, :, 1] - E[0, :, 0])) < 2 * (w0 / f) * scale
     assert np.max(np.abs(E[0, :, 1])) < 1e-3 * scale
+
+
+# --------------------------------------------------------------------------
+# First-order incident field (reading R14): E_z, B_z of the collimated beam
+
+
+def _incident_residuals(beam, om, p0, h=1e-2):
+    """div E, div B, |curl E - ikB|, |curl B + ikE| of the incident field at p0,
+    each over k|E(p0)|, by fourth-order central differences."""
+    pts = [np.array(p0, dtype=float)]
+    for ax in range(3):
+        for s in (-2, -1, 1, 2):
+            q = np.array(p0, dtype=float)
+            q[ax] += s * h
+            pts.append(q)
+    E, B = oracle.incident(beam, [om], np.array(pts), zref=0.0)
+    E, B = E[0], B[0]
+
+    def d(F, ax, c):
+        i = 1 + 4 * ax
+        return (-F[i + 3, c] + 8 * F[i + 2, c] - 8 * F[i + 1, c] + F[i, c]) / (12 * h)
+
+    def curl(F):
+        return np.array([d(F, 1, 2) - d(F, 2, 1), d(F, 2, 0) - d(F, 0, 2), d(F, 0, 1) - d(F, 1, 0)])
+
+    k = K0 * om
+    n = k * np.linalg.norm(E[0])
+    return (abs(d(E, 0, 0) + d(E, 1, 1) + d(E, 2, 2)) / n, abs(d(B, 0, 0) + d(B, 1, 1) + d(B, 2, 2)) / n,
+            np.linalg.norm(curl(E) - 1j * k * B[0]) / n, np.linalg.norm(curl(B) + 1j * k * E[0]) / n)
+
+
+def test_first_order_terms_closed_forms():
+    """Hand-derived E_z, B_z = -(i/k) div_perp of e_perp, b_perp = (-z) x e_perp:
+    linear x:   E_z = (2i x / (k w0^2)) A,   B_z = -(2i y / (k w0^2)) A;
+    radial:     E_z = -(2i / (k w0)) (1 - rho^2 / w0^2) A,   B_z = 0;
+    azimuthal:  E_z = 0,   B_z = -(2i / (k w0)) (1 - rho^2 / w0^2) A."""
+    w0, om = 5.0, 1.1
+    k = K0 * om
+    pts = np.array([[1.3, -0.7, 0.4], [-2.0, 1.1, -0.3], [0.2, 3.1, 0.0]])
+    x, y, z = pts.T
+    A = np.exp(-(x * x + y * y) / w0 ** 2) * np.exp(-1j * k * z)
+    ring = (1 - (x * x + y * y) / w0 ** 2) * A
+    cases = {
+        "linear": (2j * x / (k * w0 ** 2) * A, -2j * y / (k * w0 ** 2) * A),
+        "radial": (-2j / (k * w0) * ring, 0 * A),
+        "azimuthal": (0 * A, -2j / (k * w0) * ring),
+    }
+    for pol, (ez, bz) in cases.items():
+        E, B = oracle.incident(dict(profile="gauss", pol=pol, w0=w0, order=1), [om], pts, zref=0.0)
+        scale = np.max(np.abs(A)) / (k * w0)
+        assert np.max(np.abs(E[0, :, 2] - ez)) < 1e-9 * scale, pol
+        assert np.max(np.abs(B[0, :, 2] - bz)) < 1e-9 * scale, pol
+        E0, _ = oracle.incident(dict(profile="gauss", pol=pol, w0=w0, order=0), [om], pts, zref=0.0)
+        assert np.array_equal(E0[0, :, :2], E[0, :, :2]) and not np.any(E0[0, :, 2])
+
+
+@pytest.mark.parametrize("pol", ["linear", "radial", "azimuthal"])
+def test_first_order_incident_field_obeys_maxwell_to_eps_squared(pol):
+    """The collimated beam misses Maxwell's equations at O(eps); with the
+    longitudinal terms div E = div B = 0 and the curl equations fail only at
+    O(eps^2), eps = 1/(pi w0): halving eps quarters the residual."""
+    res = {}
+    for w0 in (4.0, 8.0):
+        eps = 1 / (math.pi * w0)
+        p0 = [0.4 * w0, -0.3 * w0, 0.2]
+        b = dict(profile="gauss", pol=pol, w0=w0, pol_angle=0.3)
+        r0 = _incident_residuals(dict(b, order=0), 1.1, p0)
+        r1 = _incident_residuals(dict(b, order=1), 1.1, p0)
+        assert max(r0) > 0.2 * eps
+        assert max(r1[:2]) < 1e-6
+        assert max(r1) < 3 * eps ** 2
+        res[w0] = max(r1[2:])
+    assert 3.0 < res[4.0] / res[8.0] < 5.0
+
+
+def test_first_order_beam_closes_maxwell_for_the_reflected_field():
+    """Ampere's law, div E' = 0 and Eq. 10 = Eq. 11 need a Maxwell incident
+    field; the O(eps) terms shrink all three residuals of a w0 = 3 lambda
+    Gaussian by two orders of magnitude (Faraday holds either way)."""
+    f, om = 8.0, 1.1
+    k = K0 * om
+    m = dict(f=f, r_max=16.0, n_r=64, n_theta=64, rim=1)
+    out = {}
+    for order in (0, 1):
+        b = dict(profile="gauss", pol="linear", w0=3.0, order=order)
+        E, B, cE, cB, dE = _curl(m, b, om, [0.23, 0.11, -0.19], 2e-3)
+        E1, _ = oracle.field(m, b, [1.0], [[0.2, 0.1, 0.0]], form="stokes")
+        E2, _ = oracle.field(m, b, [1.0], [[0.2, 0.1, 0.0]], form="dyadic")
+        out[order] = (np.linalg.norm(cB + 1j * k * E) / np.linalg.norm(k * E),
+                      abs(dE) / (k * np.linalg.norm(E)),
+                      np.max(np.abs(E1 - E2)) / np.max(np.abs(E1)))
+        assert np.linalg.norm(cE - 1j * k * B) / np.linalg.norm(k * B) < 1e-7
+    for r0, r1 in zip(out[0], out[1]):
+        assert r0 > 1e-2 and r1 < 0.03 * r0
+
+
+def test_first_order_rejects_tophat():
+    m = dict(f=8.0, r_max=16.0, n_r=8, n_theta=8, rim=1)
+    with pytest.raises(ValueError):
+        oracle.field(m, dict(profile="tophat", w0=5.0, order=1), [1.0], [[0.0, 0.0, 0.0]])
