@@ -126,6 +126,15 @@ enum {
  *   W: optical path difference sum_j c_j Z_j(rho / r_max, theta), Noll
  *      ordering and normalisation, j = 2 .. n_zernike + 1, c_j in waves at
  *      lambda0 (the caller's array is copied).
+ *   order: 0 the collimated beam above, which satisfies div E = 0 only to
+ *      O(eps), eps = lambda / (pi w0) (Sec. III.A); 1 adds the first-order
+ *      longitudinal terms
+ *        E_z = -(i/k) div_perp(e_perp e^{ikW}) e^{-ik(z + 2f)},
+ *        B_z = -(i/k) div_perp(b_perp e^{ikW}) e^{-ik(z + 2f)},
+ *      e_perp = A p, b_perp = (-z_hat) x e_perp, so that div E = div B = 0
+ *      and Maxwell's curl equations hold to O(eps^2).  The 1/k part has its
+ *      own node table and doubles the field-sum work; the top-hat (no
+ *      transverse derivative) is invalid with order 1.
  */
 typedef struct {
     int kind;
@@ -133,6 +142,7 @@ typedef struct {
     int sg_order;
     int n_zernike;
     const double* zernike_noll_waves;
+    int order;
 } sc_profile;
 
 /* p: fixed direction (cos angle, sin angle, 0), or rho_hat * rho/w0
@@ -167,8 +177,9 @@ typedef struct {
 } sc_spectrum;
 
 /* Copy the description of an incident beam.  Errors: SC_ERR_INVALID
- * (unknown kind, w0 <= 0, sg_order < 1, n_zernike outside 0..64, a
- * spectrum with non-positive width or lambda_c, SAMPLED with n < 1). */
+ * (unknown kind, w0 <= 0, sg_order < 1, n_zernike outside 0..64, order not
+ * 0 or 1, order 1 with a top-hat, a spectrum with non-positive width or
+ * lambda_c, SAMPLED with n < 1). */
 sc_status sc_incident(sc_ctx* ctx, const sc_profile* prof, const sc_polarization* pol,
                       const sc_spectrum* spec, sc_incident_t** out);
 void sc_incident_free(sc_incident_t* inc);
@@ -237,7 +248,9 @@ sc_status sc_time_domain(sc_ctx* ctx, sc_precision prec, const void* E_spec, con
  * (SC_STATIC_SCRATCH_BYTES), which every GPU that loads the library holds
  * until the process exits.
  *   Preconditions: the node table of (mirror, inc) is already resident in
- *   ctx, i.e. sc_eval ran once for this pair (that call may allocate).
+ *   ctx, i.e. sc_eval ran once for this pair (that call may allocate), and
+ *   inc has order 0 (a first-order beam, with its second table, is
+ *   rejected with SC_ERR_INVALID: use sc_eval).
  *   omega_n = omega0 + n * domega, n < n_omega (<= 2048), omega0 > 0.
  *   amp_re_im   host, [n_omega][2], e.g. from sc_spectrum_eval.
  *   points_xyz  device, [n_points][3] doubles.

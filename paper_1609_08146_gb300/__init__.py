@@ -44,7 +44,7 @@ class sc_quadrature(ctypes.Structure):
 
 class sc_profile(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("w0", ctypes.c_double), ("sg_order", ctypes.c_int),
-                ("n_zernike", ctypes.c_int), ("zernike_noll_waves", _DP)]
+                ("n_zernike", ctypes.c_int), ("zernike_noll_waves", _DP), ("order", ctypes.c_int)]
 
 
 class sc_polarization(ctypes.Structure):
@@ -170,14 +170,14 @@ class Mirror:
 
 class Incident:
     def __init__(self, ctx, profile="gauss", w0=1.0, sg_order=4, zernike=(), pol="linear",
-                 pol_angle=0.0, spectrum=None):
+                 pol_angle=0.0, spectrum=None, order=0):
         self._lib = ctx._lib
         spectrum = dict(spectrum or {"kind": "mono"})
         self._keep = []
         z = np.ascontiguousarray(zernike, dtype=np.float64)
         self._keep.append(z)
         prof = sc_profile(PROFILES[profile], float(w0), int(sg_order), int(z.size),
-                          _dptr(z) if z.size else None)
+                          _dptr(z) if z.size else None, int(order))
         pl = sc_polarization(POLS[pol], float(pol_angle))
         kind = SPECTRA[spectrum.get("kind", "mono")]
         om = amp = None

@@ -46,6 +46,7 @@ struct sc_mirror_t {
 struct sc_incident_t {
     uint64_t id;
     int profile, sg_order, pol;
+    int order;                      // 0 collimated, 1 plus the O(eps) longitudinal terms
     double w0, angle;
     std::vector<double> zern;
     int spec_kind;
@@ -67,6 +68,10 @@ struct Table {
     int n_surf_tiles = 0, n_rim_tiles = 0;
     sc::Node64* d64 = nullptr;     // FP64 records, surface then rim
     int n_surf = 0, n_rim = 0;
+    // first-order beams: the second table (surface nodes only) follows the
+    // first in both allocations; null otherwise
+    const float* d32_1 = nullptr;
+    const sc::Node64* d64_1 = nullptr;
     size_t bytes = 0;
     uint64_t last_use = 0;
     int inflight = 0;              // serving batches on the GPU that read this table
@@ -118,7 +123,7 @@ struct sc_ctx {
     bool autotune = true;
     uint64_t graph_tick = 0;
     uint64_t graph_captures = 0, graph_replays = 0;
-    std::map<std::tuple<int, int, int, int, int>, int> tuned;  // shape -> split count
+    std::map<std::tuple<int, int, int, int, int, int>, int> tuned;  // shape -> split count
     std::mutex mu;                                              // guards all of the above
     Server* server = nullptr;
 };
@@ -314,6 +319,74 @@ double incident_opd(const sc_incident_t* in, double rho, double th, double r_uni
     return W;
 }
 
+// Partial derivatives of Z_j(u, th) in u and th.
+void zernike_grad(int j, double u, double th, double& dzdu, double& dzdth)
+{
+    int n, m;
+    noll_nm(j, n, m);
+    const int am = m < 0 ? -m : m;
+    double R = 0.0, dR = 0.0;
+    for (int s = 0; s <= (n - am) / 2; ++s) {
+        const double c = ((s & 1) ? -1.0 : 1.0) * tgamma(n - s + 1.0) /
+                         (tgamma(s + 1.0) * tgamma((n + am) / 2 - s + 1.0) * tgamma((n - am) / 2 - s + 1.0));
+        const int p = n - 2 * s;
+        R += c * pow(u, p);
+        if (p > 0) dR += c * p * pow(u, p - 1);
+    }
+    if (m == 0) {
+        dzdu = sqrt(n + 1.0) * dR;
+        dzdth = 0.0;
+        return;
+    }
+    const double nrm = sqrt(2.0 * (n + 1.0));
+    const double ca = cos(am * th), sa = sin(am * th);
+    dzdu = nrm * dR * (m > 0 ? ca : sa);
+    dzdth = nrm * R * am * (m > 0 ? -sa : ca);
+}
+
+// Cartesian gradient (gx, gy) of the optical path difference W at (rho, th).
+void incident_opd_grad(const sc_incident_t* in, double rho, double th, double r_unit, double& gx,
+                       double& gy)
+{
+    double dr = 0.0, dt = 0.0;
+    for (size_t i = 0; i < in->zern.size(); ++i) {
+        double du, dth;
+        zernike_grad((int)i + 2, rho / r_unit, th, du, dth);
+        dr += in->zern[i] * du / r_unit;
+        dt += in->zern[i] * dth;
+    }
+    const double c = cos(th), s = sin(th), at = rho > 0.0 ? dt / rho : 0.0;
+    gx = dr * c - at * s;  // dW/drho rho^ + (1/rho) dW/dth th^
+    gy = dr * s + at * c;
+}
+
+// dA/drho of the profile (the top-hat has none and is refused at order 1).
+double profile_damp(const sc_incident_t* in, double rho)
+{
+    const double A = profile_amp(in, rho), u = rho / in->w0;
+    if (in->profile == SC_PROFILE_GAUSS) return -2.0 * u / in->w0 * A;
+    if (in->profile == SC_PROFILE_SUPERGAUSS)
+        return -2.0 * in->sg_order / in->w0 * pow(u, 2.0 * in->sg_order - 1.0) * A;
+    return 0.0;
+}
+
+// Transverse divergences of e_perp = A p and b_perp = (-z) x e_perp, closed
+// forms: linear  div e = A' cos(th - a), div b = A' sin(a - th);
+//        radial  div e = (2A + rho A') / w0, div b = 0;
+//        azimuthal div e = 0, div b = (2A + rho A') / w0.
+void incident_div(const sc_incident_t* in, double rho, double th, double& div_e, double& div_b)
+{
+    const double A = profile_amp(in, rho), dA = profile_damp(in, rho);
+    if (in->pol == SC_POL_LINEAR) {
+        div_e = dA * cos(th - in->angle);
+        div_b = dA * sin(in->angle - th);
+    } else {
+        const double d = (2.0 * A + rho * dA) / in->w0;
+        div_e = in->pol == SC_POL_RADIAL ? d : 0.0;
+        div_b = in->pol == SC_POL_RADIAL ? 0.0 : d;
+    }
+}
+
 // SS |A p|^2 dA over the transverse plane, closed forms.
 double beam_power(const sc_incident_t* in)
 {
@@ -385,36 +458,68 @@ struct HostNode {
     double px, py, pz, pn, w, jx, jy, jz, rho;
 };
 
+// Surface and rim nodes of (m, in).  For a first-order beam (order 1) surf1
+// receives the second table: the same nodes carrying the 1/k part of the
+// longitudinal terms, E~1 = z div_perp e_perp and B~1 = z div_perp b_perp,
+// whose sums the reduce multiplies by -i/k_n.  Its rim term vanishes (a
+// z-directed B has n x (n x B) . theta^ = 0), so it has no rim nodes.  The
+// aberration part of the longitudinal terms, z (e_perp . grad W), carries no
+// 1/k and joins the first table.
 void build_nodes(const sc_mirror_t* m, const sc_incident_t* in, std::vector<HostNode>& surf,
-                 std::vector<HostNode>& rim)
+                 std::vector<HostNode>& rim, std::vector<HostNode>& surf1)
 {
     const double f = m->f;
     const int nr = m->q.n_r, nt = m->q.n_theta;
+    const bool first = in->order >= 1;
     std::vector<double> gr, gw;
     gauss_legendre(nr, m->r_min, m->r_max, gr, gw);
     const double dth = 2.0 * kPi / nt;
+    // E~, B~ of the first table at (r, th), z components included
+    auto fields = [&](double r, double th, double e[3], double bv[3]) {
+        incident_E(in, r, th, e[0], e[1]);
+        bv[0] = e[1];
+        bv[1] = -e[0];  // B~ = (-z) x E~
+        e[2] = bv[2] = 0.0;
+        if (first && !in->zern.empty()) {
+            double gx, gy;
+            incident_opd_grad(in, r, th, m->r_max, gx, gy);
+            e[2] = e[0] * gx + e[1] * gy;
+            bv[2] = bv[0] * gx + bv[1] * gy;
+        }
+    };
     surf.clear();
+    surf1.clear();
     surf.reserve((size_t)nr * nt);
+    if (first) surf1.reserve((size_t)nr * nt);
     for (int i = 0; i < nr; ++i) {
         const double r = gr[i];
         for (int l = 0; l < nt; ++l) {
             const double th = l * dth;
             const double x = r * cos(th), y = r * sin(th), z = r * r / (4.0 * f) - f;
             const double Nx = -x / (2.0 * f), Ny = -y / (2.0 * f), Nz = 1.0;
-            double ex, ey;
-            incident_E(in, r, th, ex, ey);
-            const double bx = ey, by = -ex;  // B~ = (-z) x E~
+            double e[3], bv[3];
+            fields(r, th, e, bv);
             const double wq = gw[i] * dth * r / (2.0 * kPi);
             HostNode nd;
             nd.px = x; nd.py = y; nd.pz = z;
             nd.pn = r * r / (4.0 * f) + f;
             nd.w = incident_opd(in, r, th, m->r_max);
-            // J = N x B~ (B~_z = 0), rho = N . E~
-            nd.jx = (Ny * 0.0 - Nz * by) * wq;
-            nd.jy = (Nz * bx - Nx * 0.0) * wq;
-            nd.jz = (Nx * by - Ny * bx) * wq;
-            nd.rho = (Nx * ex + Ny * ey) * wq;
+            // J = N x B~, rho = N . E~
+            nd.jx = (Ny * bv[2] - Nz * bv[1]) * wq;
+            nd.jy = (Nz * bv[0] - Nx * bv[2]) * wq;
+            nd.jz = (Nx * bv[1] - Ny * bv[0]) * wq;
+            nd.rho = (Nx * e[0] + Ny * e[1] + Nz * e[2]) * wq;
             surf.push_back(nd);
+            if (first) {
+                double de, db;
+                incident_div(in, r, th, de, db);
+                HostNode n1 = nd;
+                n1.jx = Ny * db * wq;   // N x (0, 0, db)
+                n1.jy = -Nx * db * wq;
+                n1.jz = 0.0;
+                n1.rho = Nz * de * wq;  // N . (0, 0, de)
+                surf1.push_back(n1);
+            }
         }
     }
     rim.clear();
@@ -429,10 +534,10 @@ void build_nodes(const sc_mirror_t* m, const sc_incident_t* in, std::vector<Host
             const double c = cos(th), s = sin(th);
             const double x = r * c, y = r * s, z = r * r / (4.0 * f) - f;
             const double Nx = -x / (2.0 * f), Ny = -y / (2.0 * f);
-            double ex, ey;
-            incident_E(in, r, th, ex, ey);
-            const double bx = ey, by = -ex;
-            const double jx = -by, jy = bx, jz = Nx * by - Ny * bx;  // N x B~
+            double e[3], bv[3];
+            fields(r, th, e, bv);
+            // N x B~ (N_z = 1)
+            const double jx = Ny * bv[2] - bv[1], jy = bv[0] - Nx * bv[2], jz = Nx * bv[1] - Ny * bv[0];
             // q = (J . m^) dl with J = (N x B~)/|N|, m^ = sgn (c, s, r/2f)/|N|, dl = r dth
             const double q = sgn * (jx * c + jy * s + jz * r / (2.0 * f)) / nlen2 * r * dth;
             HostNode nd;
@@ -488,18 +593,20 @@ sc_status get_table(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, 
             *out = &t;
             return SC_OK;
         }
-    std::vector<HostNode> surf, rim;
-    build_nodes(m, in, surf, rim);
-    std::vector<float> ts, tr;
+    std::vector<HostNode> surf, rim, surf1;
+    build_nodes(m, in, surf, rim, surf1);
+    std::vector<float> ts, tr, ts1;
     Table t;
     t.mid = m->id;
     t.iid = in->id;
     pack_tiles(surf, ts, t.n_surf_tiles);
     if (!rim.empty()) pack_tiles(rim, tr, t.n_rim_tiles);
+    int n1_tiles = 0;
+    if (!surf1.empty()) pack_tiles(surf1, ts1, n1_tiles);
     t.n_surf = (int)surf.size();
     t.n_rim = (int)rim.size();
-    const size_t b32 = (ts.size() + tr.size()) * sizeof(float);
-    const size_t b64 = (surf.size() + rim.size()) * sizeof(sc::Node64);
+    const size_t b32 = (ts.size() + tr.size() + ts1.size()) * sizeof(float);
+    const size_t b64 = (surf.size() + rim.size() + surf1.size()) * sizeof(sc::Node64);
     t.bytes = b32 + b64;
     // evict least recently used tables while over budget
     while (ctx->budget && ctx->held + t.bytes > ctx->budget && !ctx->tables.empty()) {
@@ -524,8 +631,8 @@ sc_status get_table(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, 
         return fail(ctx, SC_ERR_OOM, "node table allocation failed: %s", cudaGetErrorString(e));
     }
     std::vector<sc::Node64> h64;
-    h64.reserve(surf.size() + rim.size());
-    for (auto* vec : {&surf, &rim})
+    h64.reserve(surf.size() + rim.size() + surf1.size());
+    for (auto* vec : {&surf, &rim, &surf1})
         for (const auto& nd : *vec)
             h64.push_back(sc::Node64{nd.px, nd.py, nd.pz, nd.pn, nd.w, nd.jx, nd.jy, nd.jz, nd.rho, 0.0});
     SC_CUDA(cudaMemcpyAsync(t.d32, ts.data(), ts.size() * sizeof(float), cudaMemcpyHostToDevice,
@@ -533,6 +640,12 @@ sc_status get_table(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, 
     if (!tr.empty())
         SC_CUDA(cudaMemcpyAsync(t.d32 + ts.size(), tr.data(), tr.size() * sizeof(float),
                                 cudaMemcpyHostToDevice, stream), "upload rim table");
+    if (!ts1.empty()) {
+        t.d32_1 = t.d32 + ts.size() + tr.size();
+        t.d64_1 = t.d64 + surf.size() + rim.size();
+        SC_CUDA(cudaMemcpyAsync(t.d32 + ts.size() + tr.size(), ts1.data(), ts1.size() * sizeof(float),
+                                cudaMemcpyHostToDevice, stream), "upload first-order table");
+    }
     SC_CUDA(cudaMemcpyAsync(t.d64, h64.data(), b64, cudaMemcpyHostToDevice, stream),
             "upload FP64 table");
     // the host vectors die at return: make the copies complete first
@@ -632,10 +745,25 @@ bool uniform_grid(const double* om, int n, double& d)
 
 struct Chunk {
     sc::FieldLaunch f;      // ws assigned at execution
-    sc::ReduceLaunch rl;    // ws, off assigned at execution
+    sc::FieldLaunch f1;     // first-order table of the same chunk (when has1)
+    sc::ReduceLaunch rl;    // ws, ws1, off assigned at execution
     int cls = 0, ppc = 1, pb = 1;
-    size_t ws_elems = 0;    // float2 elements
+    bool has1 = false;
+    size_t ws_elems = 0;    // float2 elements, both tables
 };
+
+// Split a chunk's surface tiles S ways; the first-order table (same nodes)
+// uses the same splits and a workspace section of its own after the first.
+void set_splits(Chunk& c, int S, int tiles)
+{
+    const int tps = (tiles + S - 1) / S;
+    c.f.tiles_per_split = tps;
+    c.f.n_splits = (tiles + tps - 1) / tps;
+    c.f1.tiles_per_split = tps;
+    c.f1.n_splits = c.f.n_splits;
+    c.rl.n_splits = c.f.n_splits;
+    c.ws_elems = (size_t)(c.f.n_splits + 1) * c.f.n_pts * c.f.n_omega * sc::kAcc * (c.has1 ? 2 : 1);
+}
 
 int heuristic_splits(int tiles, long long pb, int slots)
 {
@@ -651,11 +779,7 @@ sc_status launch_chunks_direct(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch, fl
 // Time one chunk with split count S (the chunk's outputs are overwritten later).
 float time_chunk(sc_ctx* ctx, Lane& ln, Chunk c, int S, const Table* tab, float2* ws)
 {
-    const int tps = (tab->n_surf_tiles + S - 1) / S;
-    c.f.tiles_per_split = tps;
-    c.f.n_splits = (tab->n_surf_tiles + tps - 1) / tps;
-    c.rl.n_splits = c.f.n_splits;
-    c.ws_elems = (size_t)(c.f.n_splits + 1) * c.f.n_pts * c.f.n_omega * sc::kAcc;
+    set_splits(c, S, tab->n_surf_tiles);
     std::vector<Chunk> one{c};
     cudaEvent_t a = take_event(ctx), b = take_event(ctx);
     cudaEventRecord(a, ln.stream);
@@ -679,7 +803,7 @@ sc_status choose_splits(sc_ctx* ctx, Lane& ln, Chunk& c, const Table* tab, int s
         *S_out = (tiles + tps - 1) / tps;
         return SC_OK;
     }
-    const auto key = std::make_tuple(c.cls, tiles, tab->n_rim_tiles, c.f.n_pts, c.f.n_omega);
+    const auto key = std::make_tuple(c.cls, tiles, tab->n_rim_tiles, c.f.n_pts, c.f.n_omega, (int)c.has1);
     auto hit = ctx->tuned.find(key);
     if (hit != ctx->tuned.end()) {
         *S_out = hit->second;
@@ -700,7 +824,7 @@ sc_status choose_splits(sc_ctx* ctx, Lane& ln, Chunk& c, const Table* tab, int s
         for (int s : cand) {
             const int tps = (tiles + s - 1) / s;
             const int ns = (tiles + tps - 1) / tps;
-            const size_t n = (size_t)(ns + 1) * c.f.n_pts * c.f.n_omega * sc::kAcc;
+            const size_t n = (size_t)(ns + 1) * c.f.n_pts * c.f.n_omega * sc::kAcc * (c.has1 ? 2 : 1);
             if (n * sizeof(float2) <= ctx->ws_cap) {
                 fit.push_back(s);
                 need = std::max(need, n);
@@ -757,16 +881,21 @@ sc_status plan_request(sc_ctx* ctx, Lane& ln, const Table* tab, const double* om
         c.rl.B = dB ? dB + (size_t)o0 * n_points * 3 : nullptr;
         c.rl.n_pts = n_points;
         c.rl.n_omega = no;
+        c.rl.ws1 = nullptr;
+        c.has1 = tab->d32_1 != nullptr;
+        if (c.has1) {
+            // the first-order table: surface nodes only (its rim term vanishes)
+            c.f1 = c.f;
+            c.f1.nodes = tab->d32_1;
+            c.f1.n_rim_tiles = 0;
+        }
         int S = 1;
         sc_status st = choose_splits(ctx, ln, c, tab, slots, &S);
         if (st != SC_OK) return st;
-        int tps = (tab->n_surf_tiles + S - 1) / S;
-        const int n_splits = (tab->n_surf_tiles + tps - 1) / tps;
-        c.f.tiles_per_split = tps;
-        c.f.n_splits = n_splits;
-        c.rl.n_splits = n_splits;
+        set_splits(c, S, tab->n_surf_tiles);
+        const int n_splits = c.f.n_splits;
         // point chunks bounded by the workspace cap
-        const size_t per_pt = (size_t)(n_splits + 1) * no * sc::kAcc;
+        const size_t per_pt = (size_t)(n_splits + 1) * no * sc::kAcc * (c.has1 ? 2 : 1);
         long long pchunk = std::max<long long>(1, (long long)(ctx->ws_cap / sizeof(float2) / per_pt));
         if (pchunk < n_points) pchunk = std::max<long long>(c.ppc, pchunk / c.ppc * c.ppc);
         for (int p0 = 0; p0 < n_points; p0 += (int)pchunk) {
@@ -774,6 +903,8 @@ sc_status plan_request(sc_ctx* ctx, Lane& ln, const Table* tab, const double* om
             Chunk d = c;
             d.f.pts = d_pts + 3 * (size_t)p0;
             d.f.n_pts = np;
+            d.f1.pts = d.f.pts;
+            d.f1.n_pts = np;
             d.pb = (np + c.ppc - 1) / c.ppc;
             d.rl.n_pts = np;
             d.rl.E = c.rl.E + (size_t)p0 * 3;
@@ -796,6 +927,8 @@ sc_status launch_chunks(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch, float2* w
     for (auto& c : ch) {
         c.f.ws = ws + off;
         c.rl.ws = ws + off;
+        c.f1.ws = c.has1 ? ws + off + c.ws_elems / 2 : nullptr;
+        c.rl.ws1 = c.f1.ws;
         c.rl.off = roff;
         off += c.ws_elems;
         roff += (long long)c.rl.n_pts * c.rl.n_omega;
@@ -805,15 +938,16 @@ sc_status launch_chunks(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch, float2* w
     constexpr int kClasses = sc::kNumClasses;
     std::vector<sc::WorkReq> reqs[kClasses];
     long long items[kClasses] = {};
-    for (auto& c : ch) {
-        sc::WorkReq w;
-        w.f = c.f;
-        w.pb = c.pb;
-        w.cls = c.cls;
-        w.item0 = items[c.cls];
-        items[c.cls] += (long long)c.pb * (c.f.n_splits + 1);
-        reqs[c.cls].push_back(w);
-    }
+    for (auto& c : ch)
+        for (int t = 0; t < (c.has1 ? 2 : 1); ++t) {
+            sc::WorkReq w;
+            w.f = t == 0 ? c.f : c.f1;
+            w.pb = c.pb;
+            w.cls = c.cls;
+            w.item0 = items[c.cls];
+            items[c.cls] += (long long)c.pb * (w.f.n_splits + 1);
+            reqs[c.cls].push_back(w);
+        }
     std::vector<sc::ReduceLaunch> rls;
     for (auto& c : ch) rls.push_back(c.rl);
     // arena: queues (64 B each) | WorkReq arrays | ReduceLaunch array
@@ -1312,6 +1446,8 @@ sc_status sc_incident(sc_ctx* ctx, const sc_profile* prof, const sc_polarization
         (prof->kind == SC_PROFILE_SUPERGAUSS && prof->sg_order < 1) || prof->n_zernike < 0 ||
         prof->n_zernike > 64 || (prof->n_zernike > 0 && !prof->zernike_noll_waves))
         return fail(ctx, SC_ERR_INVALID, "invalid beam profile");
+    if (prof->order < 0 || prof->order > 1 || (prof->order == 1 && prof->kind == SC_PROFILE_TOPHAT))
+        return fail(ctx, SC_ERR_INVALID, "beam order must be 0 or 1 (1 needs a smooth profile)");
     if (pol->kind < 0 || pol->kind > 2) return fail(ctx, SC_ERR_INVALID, "invalid polarization");
     if (spec->kind < 0 || spec->kind > 3) return fail(ctx, SC_ERR_INVALID, "invalid spectrum kind");
     if (!(spec->lambda_c > 0.0) && spec->kind != SC_SPEC_MONO && spec->kind != SC_SPEC_SAMPLED)
@@ -1328,6 +1464,7 @@ sc_status sc_incident(sc_ctx* ctx, const sc_profile* prof, const sc_polarization
     in->id = g_next_id++;
     in->profile = prof->kind;
     in->sg_order = prof->sg_order;
+    in->order = prof->order;
     in->w0 = prof->w0;
     in->zern.assign(prof->zernike_noll_waves, prof->zernike_noll_waves + prof->n_zernike);
     in->pol = pol->kind;
@@ -1446,6 +1583,8 @@ sc_status sc_eval(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, co
         a.n_surf = tab->n_surf;
         a.rim = tab->d64 + tab->n_surf;
         a.n_rim = tab->n_rim;
+        a.surf1 = tab->d64_1;
+        a.n_surf1 = tab->d64_1 ? tab->n_surf : 0;
         a.pts = d_pts;
         a.n_pts = n_points;
         a.kval = d_k;
@@ -1623,6 +1762,8 @@ sc_status sc_eval_fp32_static(sc_ctx* ctx, const sc_mirror_t* m, const sc_incide
     if (!tab)
         return fail(ctx, SC_ERR_INVALID,
                     "node table not resident: run sc_eval once for this mirror and incident first");
+    if (tab->d32_1)
+        return fail(ctx, SC_ERR_INVALID, "a first-order beam needs sc_eval (two node tables)");
     ctx->tick++;
     void* scratch = nullptr;
     cudaError_t e = sc::static_scratch(ctx->device, &scratch);

@@ -708,15 +708,15 @@ __global__ void __launch_bounds__(256, 1) field_direct_kernel(BatchLaunch b)
 // ------------------------------------------------------------------------
 // FP64 cross-split reduction and epilogue.
 
-__device__ __forceinline__ void reduce_one(const ReduceLaunch& r, long long idx)
+// Sum one (point, omega) entry of a workspace over its surface splits (s)
+// and read its rim slot (rim, the E sums only), in FP64, in split order.
+__device__ __forceinline__ void section_sums(const float2* ws, int n_splits, size_t stride, size_t at,
+                                             double s[kAcc], double rim[6])
 {
-    const int pt = (int)(idx / r.n_omega), n = (int)(idx % r.n_omega);
-    double s[kAcc];
 #pragma unroll
     for (int c = 0; c < kAcc; ++c) s[c] = 0.0;
-    const size_t stride = (size_t)r.n_pts * r.n_omega * kAcc;
-    const float2* base = r.ws + ((size_t)pt * r.n_omega + n) * kAcc;
-    for (int sp = 0; sp < r.n_splits; ++sp) {
+    const float2* base = ws + at;
+    for (int sp = 0; sp < n_splits; ++sp) {
         const float4* v = reinterpret_cast<const float4*>(base + sp * stride);
 #pragma unroll
         for (int c = 0; c < kAcc / 2; ++c) {
@@ -725,32 +725,55 @@ __device__ __forceinline__ void reduce_one(const ReduceLaunch& r, long long idx)
             s[2 * c + 1] += (double)h.z + (double)h.w;
         }
     }
-    // rim slot: its E sum carries the factor i/k of the line integral
-    const float4* v = reinterpret_cast<const float4*>(base + (size_t)r.n_splits * stride);
-    double rim[6];
+    const float4* v = reinterpret_cast<const float4*>(base + (size_t)n_splits * stride);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const float4 h = v[c];
         rim[2 * c] = (double)h.x + (double)h.y;
         rim[2 * c + 1] = (double)h.z + (double)h.w;
     }
+}
+
+__device__ __forceinline__ void reduce_one(const ReduceLaunch& r, long long idx)
+{
+    const int pt = (int)(idx / r.n_omega), n = (int)(idx % r.n_omega);
+    const size_t stride = (size_t)r.n_pts * r.n_omega * kAcc;
+    const size_t at = ((size_t)pt * r.n_omega + n) * kAcc;
+    double s[kAcc], rim[6];
+    section_sums(r.ws, r.n_splits, stride, at, s, rim);
     const double ik = 1.0 / r.kval[n];
+    // T = S + (i/k) rim: the rim slot's E sum carries the factor i/k of the
+    // line integral
+    double er[3], ei[3], br[3], bi[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        er[c] = s[2 * c] - ik * rim[2 * c + 1];
+        ei[c] = s[2 * c + 1] + ik * rim[2 * c];
+        br[c] = s[6 + 2 * c];
+        bi[c] = s[6 + 2 * c + 1];
+    }
+    if (r.ws1) {
+        // first-order table: + (-i/k) T1, T1 = S1 + (i/k) rim1
+        section_sums(r.ws1, r.n_splits, stride, at, s, rim);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double tr = s[2 * c] - ik * rim[2 * c + 1], ti = s[2 * c + 1] + ik * rim[2 * c];
+            er[c] += ik * ti;
+            ei[c] -= ik * tr;
+            br[c] += ik * s[6 + 2 * c + 1];
+            bi[c] -= ik * s[6 + 2 * c];
+        }
+    }
     const double ar = r.amp[2 * n], ai = r.amp[2 * n + 1];
     float2* E = r.E + (size_t)n * r.out_pt_stride_omega + (size_t)pt * 3;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        // S + (i/k) rim
-        const double er = s[2 * c] - ik * rim[2 * c + 1];
-        const double ei = s[2 * c + 1] + ik * rim[2 * c];
-        E[c] = make_float2((float)(ar * er - ai * ei), (float)(ar * ei + ai * er));
-    }
+    for (int c = 0; c < 3; ++c)
+        E[c] = make_float2((float)(ar * er[c] - ai * ei[c]), (float)(ar * ei[c] + ai * er[c]));
     if (r.B) {
         float2* B = r.B + (size_t)n * r.out_pt_stride_omega + (size_t)pt * 3;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const double br = s[6 + 2 * c], bi = s[6 + 2 * c + 1];
-            B[c] = make_float2((float)(ar * br - ai * bi), (float)(ar * bi + ai * br));
-        }
+        for (int c = 0; c < 3; ++c)
+            B[c] = make_float2((float)(ar * br[c] - ai * bi[c]), (float)(ar * bi[c] + ai * br[c]));
     }
 }
 

@@ -95,6 +95,8 @@ int launch_field_f32(const FieldLaunch& p, cudaStream_t s);
 // at (omega offset, point offset).
 struct ReduceLaunch {
     const float2* ws;
+    const float2* ws1 = nullptr;  // partials of the first-order table (same layout), or null:
+                            // the result gains -i/k_n times their sum
     int n_splits;           // surface splits (the rim slot follows)
     int n_pts, n_omega;
     const double* amp;      // [n_omega][2] of this chunk
@@ -113,6 +115,8 @@ int launch_reduce_batch(const ReduceLaunch* reqs, int n_req, long long total, cu
 struct Field64Launch {
     const Node64* surf; int n_surf;
     const Node64* rim;  int n_rim;
+    const Node64* surf1 = nullptr;       // first-order table (sums times -i/k), or null
+    int n_surf1 = 0;
     const double* pts;  int n_pts;
     const double* kval; int n_omega;     // k_n per omega
     const double* amp;                   // [n_omega][2]

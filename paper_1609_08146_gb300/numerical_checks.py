@@ -32,14 +32,17 @@ F_M = 0.0675
 W0_M = 0.05
 
 
-def config(n_nodes: int = 384, n_omega: int = 100, w0_m: float = W0_M, pol: str = "radial"):
-    """Sec. IV.A's set-up: Table 1's spectrum and focal length, NA = 1."""
+def config(n_nodes: int = 384, n_omega: int = 100, w0_m: float = W0_M, pol: str = "radial",
+           order: int = 0):
+    """Sec. IV.A's set-up: Table 1's spectrum and focal length, NA = 1.  order 1
+    adds the first-order longitudinal terms to the collimated beam."""
     base = pe.config(n_nodes=n_nodes, n_grid=3, half=1.0, n_omega=n_omega)
     f = F_M / pe.LAMBDA0_M
     base["name"] = ("Sec. IV.A checks: %s Gaussian w0=%g m, f=0.0675 m, NA=1, %dx%d nodes"
                     % (pol, w0_m, n_nodes, n_nodes))
     base["mirror"] = dict(f=f, r_min=0.0, r_max=2 * f, n_r=n_nodes, n_theta=n_nodes, rim=True)
-    base["beam"] = dict(profile="gauss", w0=w0_m / pe.LAMBDA0_M, pol=pol, pol_angle=0.0, zernike=[])
+    base["beam"] = dict(profile="gauss", w0=w0_m / pe.LAMBDA0_M, pol=pol, pol_angle=0.0, zernike=[],
+                        order=order)
     return base
 
 
@@ -55,7 +58,8 @@ def cube(half: float, h: float):
 def _handles(ctx, cfg, n_r=None, n_theta=None):
     mc, b = cfg["mirror"], cfg["beam"]
     m = ctx.mirror(mc["f"], mc["r_min"], mc["r_max"], n_r or mc["n_r"], n_theta or mc["n_theta"])
-    inc = ctx.incident(profile=b["profile"], w0=b["w0"], pol=b["pol"], spectrum=cfg["spectrum"])
+    inc = ctx.incident(profile=b["profile"], w0=b["w0"], pol=b["pol"], spectrum=cfg["spectrum"],
+                       order=b.get("order", 0))
     return m, inc
 
 

@@ -50,6 +50,22 @@ def test_host_validation_without_gpu():
     assert lib.sc_create(0, None, 0, None) == sc.SC_ERR_INVALID
 
 
+def test_first_order_beam_validation():
+    """Beam order 1 (the O(eps) longitudinal terms) needs a smooth profile."""
+    lib = sc.load()
+    pol = sc.sc_polarization(0, 0.0)
+    spec = sc.sc_spectrum(0, 1.0, 1.0, 0.1, 3, 1.0, 0, None, None, 0, None)
+    cases = [(0, 0, sc.SC_OK), (0, 1, sc.SC_OK), (1, 1, sc.SC_OK), (2, 0, sc.SC_OK),
+             (2, 1, sc.SC_ERR_INVALID), (0, 2, sc.SC_ERR_INVALID), (0, -1, sc.SC_ERR_INVALID)]
+    for kind, order, want in cases:
+        h = ctypes.c_void_p()
+        prof = sc.sc_profile(kind, 2.0, 4, 0, None, order)
+        st = lib.sc_incident(None, ctypes.byref(prof), ctypes.byref(pol), ctypes.byref(spec), ctypes.byref(h))
+        assert st == want, (kind, order)
+        if st == sc.SC_OK:
+            lib.sc_incident_free(h)
+
+
 def _incident(lib, beam, spec):
     keep = []
     prof = sc.sc_profile(sc.PROFILES[beam["profile"]], beam["w0"], beam.get("sg_order", 4), 0, None)

@@ -7,7 +7,8 @@ unclipped Gaussian beam with Table 1's spectrum on an NA = 1 paraboloid.
     cells far larger than the wavelength (Sec. IV.A: more than 100 lambda);
   * the frequency-domain Maxwell residual e_f of Eq. 26a: it falls as the
     square of the finite-difference step until it meets the O(eps) error of
-    the collimated incident beam (eps = lambda / (pi w0), Sec. III.A);
+    the collimated incident beam (eps = lambda / (pi w0), Sec. III.A), and
+    below that with the first-order beam;
   * energy: the time-domain field in a 25 lambda cube around the focus holds
     the energy of the incident pulse (Sec. IV.A).
 """
@@ -90,6 +91,19 @@ def test_maxwell_frequency_residual(ctx):
         assert f["max_e_f"] < c["max_e_f"] / 30
         # then the collimated beam's own O(eps) error
         assert z["max_e_f"] < 3 * eps
+
+
+def test_first_order_beam_removes_the_eps_floor(ctx):
+    """With the O(eps) longitudinal terms the incident beam obeys Maxwell to
+    O(eps^2) (about 3e-11 here), so e_f keeps falling with dx below the
+    collimated beam's eps = 5e-6 floor, down to the finite-difference error."""
+    cfg = nc.config(n_nodes=256, order=1)
+    eps = 1.0 / (math.pi * cfg["beam"]["w0"])
+    fine = nc.maxwell_freq(ctx, cfg, dx=1e-4, omega_indices=[0, 99], precision="fp64")
+    for r in fine:
+        k = 2 * math.pi * r["omega"]
+        assert r["max_e_f"] < 0.1 * eps
+        assert r["max_e_f"] < 10 * (k * 1e-4) ** 2
 
 
 def test_focal_volume_energy(ctx):
