@@ -65,10 +65,31 @@ class _Beam(ctypes.Structure):
         ("r_norm", ctypes.c_double),
         ("zern", ctypes.POINTER(ctypes.c_double)),
         ("order", ctypes.c_int),
+        ("lg_p", ctypes.c_int),
+        ("lg_l", ctypes.c_int),
+        ("z_waist", ctypes.c_double),
+        ("env_fn", ctypes.c_void_p),
+        ("env_user", ctypes.c_void_p),
     ]
 
 
-PROFILES = {"gauss": 0, "supergauss": 1, "tophat": 2}
+# fn(user, n, xyz[n][3], k, e[n][2][2]): the caller's envelope (profile "envelope")
+ENVELOPE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                               ctypes.c_double, ctypes.POINTER(ctypes.c_double))
+
+
+def envelope_callback(fn):
+    """Wrap fn(xyz [n, 3], k) -> e [n, 2] complex (the transverse envelope
+    e_perp at mirror points) as a C callback.  Keep the returned object alive
+    while it is in use."""
+    def _cb(user, n, xyz, k, out):
+        pts = np.ctypeslib.as_array(xyz, shape=(n, 3))
+        e = np.asarray(fn(pts.copy(), k), dtype=np.complex128).reshape(n, 2)
+        np.ctypeslib.as_array(out, shape=(n, 4))[:] = e.view(np.float64)
+    return ENVELOPE_FN(_cb)
+
+
+PROFILES = {"gauss": 0, "supergauss": 1, "tophat": 2, "laguerre_gauss": 3, "envelope": 4}
 POLS = {"linear": 0, "radial": 1, "azimuthal": 2}
 SPECTRA = {"mono": 0, "gauss_time": 1, "supergauss_lambda": 2, "sampled": 3}
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -88,6 +109,7 @@ def _load():
             ctypes.POINTER(_Mirror), ctypes.POINTER(_Beam), ctypes.c_int, ctypes.c_int, _DP, _DP,
             ctypes.c_int, _DP, _DP, _DP, ctypes.c_int,
         ]
+        lib.or_envelope.argtypes = [ctypes.POINTER(_Beam), ctypes.c_double, ctypes.c_int, _DP, _DP]
         lib.or_incident.argtypes = [
             ctypes.POINTER(_Beam), ctypes.c_double, ctypes.c_int, _DP, ctypes.c_int, _DP, _DP, _DP,
         ]
@@ -123,6 +145,9 @@ def _beam(b: dict, keep: list) -> _Beam:
         pol=POLS[b.get("pol", "linear")], n_zern=int(z.size), w0=float(b.get("w0", 1.0)),
         pol_angle=float(b.get("pol_angle", 0.0)), r_norm=float(b.get("r_norm", 1.0)),
         zern=_ptr(z) if z.size else None, order=int(b.get("order", 0)),
+        lg_p=int(b.get("lg_p", 0)), lg_l=int(b.get("lg_l", 0)), z_waist=float(b.get("z_waist", 0.0)),
+        env_fn=ctypes.cast(b["env_fn"], ctypes.c_void_p) if b.get("env_fn") is not None else None,
+        env_user=None,
     )
 
 
@@ -172,6 +197,18 @@ def field(mirror: dict, beam: dict, omegas, pts, amp=None, form: str = "stokes",
     if rc != 0:
         raise ValueError("invalid mirror or beam parameters")
     return E, B
+
+
+def envelope(beam: dict, k: float, pts):
+    """Transverse envelope e_perp [n, 2] complex of a built-in beam (R4
+    profiles or the Laguerre-Gauss mode of R15) at points [n, 3]."""
+    p = np.ascontiguousarray(np.asarray(pts, dtype=np.float64).reshape(-1, 3))
+    e = np.zeros((p.shape[0], 2), dtype=np.complex128)
+    keep: list = []
+    b = _beam(beam, keep)
+    if _load().or_envelope(ctypes.byref(b), float(k), p.shape[0], _ptr(p), _ptr(e.view(np.float64))):
+        raise ValueError("a caller's envelope is not sampled here")
+    return e
 
 
 def incident(beam: dict, omegas, pts, zref: float):

@@ -48,6 +48,22 @@
  *       energy per unit k includes |d lambda / dk| = lambda^2 / (2 pi).
  *   R6  units: lambda0 = c = 1, k = 2 pi omega with omega in units of
  *       omega0 = 2 pi c / lambda0; time in lambda0 / c.
+ *   R15 frequency-dependent incident envelopes (profiles 3 and 4): the beam
+ *       is E_inc = e_perp(x, y, z; k) exp(-ik(z + z_ref)) exp(ikW), B_inc =
+ *       (-z) x E_inc, with a complex transverse envelope e_perp that may
+ *       depend on k.  Profile 3 is the Laguerre-Gauss mode (p, l) of the
+ *       paraxial wave equation travelling along -z with its waist at
+ *       z = z_waist (Sec. III.A's beam basis): with zeta = z_waist - z,
+ *       z_R = k w0^2 / 2, w = w0 sqrt(1 + zeta^2/z_R^2),
+ *       1/R = zeta / (zeta^2 + z_R^2), psi = atan(zeta / z_R),
+ *         u = (w0/w)^(|l|+1) (rho/w0)^|l| L_p^|l|(2 rho^2/w^2)
+ *             exp(-rho^2/w^2) exp(ik rho^2 / (2R)) exp(-i(2p+|l|+1) psi),
+ *       e_perp = u exp(i l theta) p_lin (linear), u rho_hat (radial) or
+ *       u theta_hat (azimuthal), the last two with |l| = 1; as z_R -> oo it
+ *       is the collimated beam of R4.  The constant phase exp(ik(z_waist +
+ *       z_ref)) is dropped, so t = 0 stays the geometric focal arrival.
+ *       Profile 4 takes e_perp from a caller's function (measured maps,
+ *       spatio-temporal couplings), sampled once per frequency and node.
  *   R14 first-order incident field (beam order 1): the collimated beam of R4
  *       is not divergence-free at O(eps), eps = lambda / (pi w0) (Sec. III.A).
  *       Order 1 adds the longitudinal terms that make div E = div B = 0 and
@@ -98,6 +114,11 @@ typedef struct {
     double r_norm;    /* radius of the Zernike unit disk                       */
     const double* zern;
     int order;        /* 0: collimated beam (R4); 1: plus the O(eps) terms (R14) */
+    int lg_p, lg_l;   /* Laguerre-Gauss indices (profile 3)                   */
+    double z_waist;   /* waist plane of the Laguerre-Gauss beam               */
+    /* profile 4: fn(user, n, xyz[n][3], k, e[n][2][2]) writes e_perp (re, im) */
+    void (*env_fn)(void* user, int n, const double* xyz, double k, double* e);
+    void* env_user;
 } or_beam;
 
 /* ------------------------------------------------------------------------ */
@@ -233,6 +254,43 @@ static double beam_opd(const or_beam* bm, double x, double y)
     return w;
 }
 
+/* generalised Laguerre polynomial L_p^a(x) by its three-term recurrence */
+static double laguerre(int p, int a, double x)
+{
+    double l0 = 1.0, l1 = 1.0 + a - x;
+    if (p == 0) return l0;
+    for (int n = 1; n < p; ++n) {
+        double l2 = ((2.0 * n + 1.0 + a - x) * l1 - (n + a) * l0) / (n + 1.0);
+        l0 = l1;
+        l1 = l2;
+    }
+    return l1;
+}
+
+/* Laguerre-Gauss envelope e_perp (complex x, y) of reading R15 at (x, y, z) */
+static void lg_envelope(const or_beam* bm, double k, double x, double y, double z, cplx e[2])
+{
+    const double w0 = bm->w0, zr = 0.5 * k * w0 * w0, zeta = bm->z_waist - z;
+    const double w = w0 * sqrt(1.0 + (zeta / zr) * (zeta / zr));
+    const double invR = zeta / (zeta * zeta + zr * zr), psi = atan(zeta / zr);
+    const double rho2 = x * x + y * y, rho = sqrt(rho2), th = atan2(y, x);
+    const int al = (bm->pol == 0) ? abs(bm->lg_l) : 1;
+    const double amp = pow(w0 / w, al + 1.0) * pow(rho / w0, al) *
+                       laguerre(bm->lg_p, al, 2.0 * rho2 / (w * w)) * exp(-rho2 / (w * w));
+    const cplx u = amp * cexp(I * (0.5 * k * rho2 * invR - (2.0 * bm->lg_p + al + 1.0) * psi));
+    if (bm->pol == 0) {
+        const cplx v = u * cexp(I * (double)bm->lg_l * th);
+        e[0] = v * cos(bm->pol_angle);
+        e[1] = v * sin(bm->pol_angle);
+    } else if (bm->pol == 1) {
+        e[0] = u * cos(th);
+        e[1] = u * sin(th);
+    } else {
+        e[0] = -u * sin(th);
+        e[1] = u * cos(th);
+    }
+}
+
 /* Transverse envelope component c of the incident beam at (x, y), with the
  * aberration phase: c = 0, 1 the x, y components of e_perp exp(ikW), c = 2, 3
  * those of b_perp exp(ikW), b_perp = (-z) x e_perp = (e_y, -e_x). */
@@ -273,6 +331,7 @@ static void longitudinal(const or_beam* bm, double k, double x, double y, cplx* 
  * trapezoid quadrature in rho on a fine grid -- deliberately numerical. */
 double or_beam_power(const or_beam* bm)
 {
+    if (bm->profile == 4) return -1.0; /* a caller's envelope has no defined power */
     double rmax;
     if (bm->profile == 2) rmax = bm->w0;
     else rmax = 12.0 * bm->w0;
@@ -280,9 +339,17 @@ double or_beam_power(const or_beam* bm)
     double h = rmax / n, s = 0.0;
     for (int i = 0; i <= n; ++i) {
         double rho = i * h;
-        double e[3];
-        beam_field(bm, rho, 0.0, e);
-        double v = (e[0] * e[0] + e[1] * e[1]) * 2.0 * OR_PI * rho;
+        double v;
+        if (bm->profile == 3) {
+            /* at the waist plane the envelope does not depend on k */
+            cplx e[2];
+            lg_envelope(bm, 1.0, rho, 0.0, bm->z_waist, e);
+            v = (creal(e[0] * conj(e[0])) + creal(e[1] * conj(e[1]))) * 2.0 * OR_PI * rho;
+        } else {
+            double e[3];
+            beam_field(bm, rho, 0.0, e);
+            v = (e[0] * e[0] + e[1] * e[1]) * 2.0 * OR_PI * rho;
+        }
         s += (i == 0 || i == n) ? 0.5 * v : v;
     }
     return s * h;
@@ -329,9 +396,12 @@ static void ccross(const cplx a[3], const cplx b[3], cplx c[3])
 /* One frequency, one observation point.                                     */
 
 /* Eq. 11 (form 0) or Eq. 10 with the Appendix-A dyadic (form 1). */
+/* env_s, env_r (nullable): the sampled envelope e_perp at this k for the
+ * surface nodes [n_r][n_theta][2] and the rim nodes [edge][n_theta][2]
+ * (profiles 3 and 4); NULL for the real profiles 0-2. */
 static void field_at(const or_mirror* m, const or_beam* bm, int form, double k,
                      const double* gl_r, const double* gl_w, const double rp[3],
-                     cplx E[3], cplx B[3])
+                     const cplx* env_s, const cplx* env_r, cplx E[3], cplx B[3])
 {
     for (int c = 0; c < 3; ++c) { E[c] = 0.0; B[c] = 0.0; }
     const double dth = 2.0 * OR_PI / m->n_theta;
@@ -350,8 +420,16 @@ static void field_at(const or_mirror* m, const or_beam* bm, int form, double k,
             /* dS = |N| r dr dtheta for z = F(r, theta) */
             double dS = nlen * r * gl_w[i] * dth;
 
-            double es[3];
-            beam_field(bm, x, y, es);
+            cplx es[2];
+            if (env_s) {
+                es[0] = env_s[2 * ((long)i * m->n_theta + l)];
+                es[1] = env_s[2 * ((long)i * m->n_theta + l) + 1];
+            } else {
+                double er[3];
+                beam_field(bm, x, y, er);
+                es[0] = er[0];
+                es[1] = er[1];
+            }
             double W = beam_opd(bm, x, y);
             double d[3] = {x - rp[0], y - rp[1], z - rp[2]};
             double R = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
@@ -411,8 +489,16 @@ static void field_at(const or_mirror* m, const or_beam* bm, int form, double k,
                 /* tangent dP/dtheta = (-r sin, r cos, 0); dl = tangent * dtheta */
                 double dl[3] = {-r * sin(th) * dth * orient, r * cos(th) * dth * orient, 0.0};
 
-                double es[3];
-                beam_field(bm, x, y, es);
+                cplx es[2];
+                if (env_r) {
+                    es[0] = env_r[2 * ((long)edge * m->n_theta + l)];
+                    es[1] = env_r[2 * ((long)edge * m->n_theta + l) + 1];
+                } else {
+                    double er[3];
+                    beam_field(bm, x, y, er);
+                    es[0] = er[0];
+                    es[1] = er[1];
+                }
                 double W = beam_opd(bm, x, y);
                 double d[3] = {x - rp[0], y - rp[1], z - rp[2]};
                 double R = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
@@ -433,6 +519,34 @@ static void field_at(const or_mirror* m, const or_beam* bm, int form, double k,
             }
         }
     }
+}
+
+/*
+ * Transverse envelope e_perp (complex x, y) of the incident beam at
+ * arbitrary points and one k, without the phases exp(-ik(z + z_ref)) and
+ * exp(ikW): R4's real profiles (0-2) or the Laguerre-Gauss mode (3).
+ * Output e[n][2] complex as interleaved doubles.  Returns 0, or 1 for a
+ * caller's envelope (4), which the caller already has.
+ */
+int or_envelope(const or_beam* bm, double k, int n, const double* xyz, double* e)
+{
+    if (bm->profile == 4) return 1;
+    for (int j = 0; j < n; ++j) {
+        cplx v[2];
+        if (bm->profile == 3) {
+            lg_envelope(bm, k, xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2], v);
+        } else {
+            double er[3];
+            beam_field(bm, xyz[3 * j], xyz[3 * j + 1], er);
+            v[0] = er[0];
+            v[1] = er[1];
+        }
+        for (int c = 0; c < 2; ++c) {
+            e[4 * j + 2 * c] = creal(v[c]);
+            e[4 * j + 2 * c + 1] = cimag(v[c]);
+        }
+    }
+    return 0;
 }
 
 /*
@@ -483,10 +597,47 @@ int or_field(const or_mirror* m, const or_beam* bm, int form, int n_omega, const
 {
     if (m->n_r < 1 || m->n_theta < 1 || m->r_max <= m->r_min || m->r_min < 0.0) return 1;
     if (m->surface == 0 && m->f <= 0.0) return 1;
-    if (bm->order >= 1 && bm->profile == 2) return 1; /* a top-hat has no transverse derivative */
+    if (bm->order >= 1 && bm->profile >= 2) return 1; /* needs a smooth real profile (R14) */
+    if (bm->profile == 4 && !bm->env_fn) return 1;
     double* gl_r = (double*)malloc(sizeof(double) * m->n_r);
     double* gl_w = (double*)malloc(sizeof(double) * m->n_r);
     or_gauss_legendre(m->n_r, m->r_min, m->r_max, gl_r, gl_w);
+    /* profiles 3 and 4: the envelope at every (omega, node), sampled up front
+     * on this thread (a caller's function is not called from worker threads) */
+    const long n_s = (long)m->n_r * m->n_theta, n_rim = 2L * m->n_theta, n_nd = n_s + n_rim;
+    cplx* env = NULL;
+    if (bm->profile >= 3) {
+        env = (cplx*)malloc(sizeof(cplx) * 2 * n_nd * n_omega);
+        double* xyz = (double*)malloc(sizeof(double) * 3 * n_nd);
+        double* e = (double*)malloc(sizeof(double) * 4 * n_nd);
+        const double dth = 2.0 * OR_PI / m->n_theta;
+        for (long j = 0; j < n_nd; ++j) {
+            double r;
+            long l;
+            if (j < n_s) {
+                r = gl_r[j / m->n_theta];
+                l = j % m->n_theta;
+            } else {
+                r = ((j - n_s) / m->n_theta == 0) ? m->r_max : m->r_min;
+                l = (j - n_s) % m->n_theta;
+            }
+            xyz[3 * j] = r * cos(l * dth);
+            xyz[3 * j + 1] = r * sin(l * dth);
+            xyz[3 * j + 2] = surf_z(m, r);
+        }
+        for (int n = 0; n < n_omega; ++n) {
+            const double k = 2.0 * OR_PI * omega[n];
+            cplx* en = env + 2 * n_nd * n;
+            if (bm->profile == 3) {
+                for (long j = 0; j < n_nd; ++j) lg_envelope(bm, k, xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2], en + 2 * j);
+            } else {
+                bm->env_fn(bm->env_user, (int)n_nd, xyz, k, e);
+                for (long j = 0; j < 2 * n_nd; ++j) en[j] = e[2 * j] + I * e[2 * j + 1];
+            }
+        }
+        free(xyz);
+        free(e);
+    }
     long total = (long)n_omega * n_pts;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -496,7 +647,8 @@ int or_field(const or_mirror* m, const or_beam* bm, int form, int n_omega, const
         int n = (int)(idx / n_pts), p = (int)(idx % n_pts);
         double k = 2.0 * OR_PI * omega[n];
         cplx E[3], B[3];
-        field_at(m, bm, form, k, gl_r, gl_w, pts + 3 * p, E, B);
+        const cplx* es = env ? env + 2 * n_nd * n : NULL;
+        field_at(m, bm, form, k, gl_r, gl_w, pts + 3 * p, es, es ? es + 2 * n_s : NULL, E, B);
         cplx a = 1.0;
         if (amp) a = amp[2 * n] + I * amp[2 * n + 1];
         for (int c = 0; c < 3; ++c) {
@@ -508,6 +660,7 @@ int or_field(const or_mirror* m, const or_beam* bm, int form, int n_omega, const
             B_out[o + 1] = cimag(b);
         }
     }
+    free(env);
     free(gl_r);
     free(gl_w);
     return 0;

@@ -573,3 +573,98 @@ def test_first_order_rejects_tophat():
     m = dict(f=8.0, r_max=16.0, n_r=8, n_theta=8, rim=1)
     with pytest.raises(ValueError):
         oracle.field(m, dict(profile="tophat", w0=5.0, order=1), [1.0], [[0.0, 0.0, 0.0]])
+
+
+# --------------------------------------------------------------------------
+# Frequency-dependent envelopes (reading R15): Laguerre-Gauss modes and a
+# caller's envelope
+
+
+def _lg(pol="linear", p=0, l=0, w0=5.0, z_waist=0.0, pol_angle=0.0):
+    return dict(profile="laguerre_gauss", pol=pol, lg_p=p, lg_l=l, w0=w0, z_waist=z_waist,
+                pol_angle=pol_angle)
+
+
+def _d4(f, x0, h, ax):
+    """first and second derivatives of f along axis ax, fourth-order stencils"""
+    pts = []
+    for s in (-2, -1, 0, 1, 2):
+        q = np.array(x0, dtype=float)
+        q[ax] += s * h
+        pts.append(q)
+    v = f(np.array(pts))
+    d1 = (v[0] - 8 * v[1] + 8 * v[3] - v[4]) / (12 * h)
+    d2 = (-v[0] + 16 * v[1] - 30 * v[2] + 16 * v[3] - v[4]) / (12 * h * h)
+    return d1, d2, v[2]
+
+
+@pytest.mark.parametrize("pol,p,l", [("linear", 0, 0), ("linear", 1, 0), ("linear", 0, 2), ("linear", 2, -1),
+                                     ("radial", 0, 1), ("azimuthal", 1, 1)])
+def test_laguerre_gauss_envelope_solves_the_paraxial_equation(pol, p, l):
+    """u exp(ik zeta), zeta = z_waist - z, solves the paraxial wave equation
+    lap_perp u + 2ik du/dzeta = 0 (each Cartesian component of the vector
+    modes too); a sign slip in the curvature or Gouy phase breaks it."""
+    w0, k = 5.0, K0 * 1.1
+    zr = 0.5 * k * w0 * w0
+    b = _lg(pol, p, l, w0, z_waist=3.0)
+    for x0 in ([0.6 * w0, -0.4 * w0, 3.0 - 0.7 * zr], [-0.9 * w0, 0.3 * w0, 3.0 + 0.4 * zr],
+               [0.2 * w0, 1.1 * w0, 3.0 - 1.5 * zr]):
+        h = 0.02 * w0
+        for c in range(2):
+            f = lambda q: oracle.envelope(b, k, q)[:, c]  # noqa: E731
+            _, dxx, u = _d4(f, x0, h, 0)
+            _, dyy, _ = _d4(f, x0, h, 1)
+            dz, _, _ = _d4(f, x0, 0.02 * zr, 2)
+            lap, prop = dxx + dyy, 2j * k * (-dz)  # d/dzeta = -d/dz
+            assert abs(lap + prop) <= 1e-5 * (abs(lap) + abs(prop)), (pol, p, l, c)
+
+
+def test_laguerre_gauss_is_the_collimated_beam_at_its_waist():
+    rng = np.random.default_rng(3)
+    pts = np.column_stack([rng.uniform(-9, 9, (20, 2)), np.full(20, 2.5)])
+    for pol in ("linear", "radial", "azimuthal"):
+        e_lg = oracle.envelope(_lg(pol, 0, 1 if pol != "linear" else 0, 5.0, z_waist=2.5, pol_angle=0.4), 7.0, pts)
+        e_r4 = oracle.envelope(dict(profile="gauss", pol=pol, w0=5.0, pol_angle=0.4), 7.0, pts)
+        assert np.max(np.abs(e_lg - e_r4)) < 1e-15
+
+
+@pytest.mark.parametrize("p,l", [(0, 0), (1, 0), (2, 0), (0, 3), (1, 2)])
+def test_laguerre_gauss_power_closed_form_and_conservation(p, l):
+    """SS |u|^2 dA = (pi w0^2 / 2) 2^-|l| Gamma(p + |l| + 1) / p! (Laguerre
+    orthogonality), the same in every plane (w0/w normalisation)."""
+    w0 = 4.0
+    b = _lg("linear", p, l, w0)
+    closed = math.pi * w0 ** 2 / 2 * 2.0 ** (-abs(l)) * math.gamma(p + abs(l) + 1) / math.factorial(p)
+    assert abs(oracle.beam_power(b) - closed) < 1e-9 * closed
+    k = K0
+    zr = 0.5 * k * w0 * w0
+    for zeta in (0.5 * zr, 2.0 * zr):
+        w = w0 * math.sqrt(1 + (zeta / zr) ** 2)
+        rho = np.linspace(0, 10 * w, 20001)[1:]
+        th = np.zeros_like(rho)
+        pts = np.column_stack([rho * np.cos(th), rho * np.sin(th), np.full_like(rho, -zeta)])
+        e = oracle.envelope(b, k, pts)
+        P = np.trapezoid(np.sum(np.abs(e) ** 2, axis=1) * 2 * math.pi * rho, rho)
+        assert abs(P - closed) < 1e-6 * closed
+
+
+def test_caller_envelope_reproduces_built_in_beams():
+    """A caller's envelope that returns a built-in beam gives that beam's
+    reflected field: the sampled-envelope path of the oracle is the same sum."""
+    m = dict(f=8.0, r_max=16.0, n_r=24, n_theta=24, rim=1)
+    pts = np.array([[0.0, 0.0, 0.0], [0.3, -0.2, 0.4]])
+    om = [0.9, 1.1]
+    for ref in (dict(profile="gauss", pol="radial", w0=6.0), _lg("linear", 1, 2, 5.0, z_waist=-4.0)):
+        cb = oracle.envelope_callback(lambda q, k, ref=ref: oracle.envelope(ref, k, q))
+        E0, B0 = oracle.field(m, dict(ref, r_norm=16.0), om, pts)
+        E1, B1 = oracle.field(m, dict(profile="envelope", w0=6.0, env_fn=cb, r_norm=16.0), om, pts)
+        assert np.max(np.abs(E1 - E0)) <= 1e-13 * np.max(np.abs(E0))
+        assert np.max(np.abs(B1 - B0)) <= 1e-13 * np.max(np.abs(B0))
+
+
+def test_faraday_holds_for_a_laguerre_gauss_beam():
+    f, om = 8.0, 1.1
+    k = K0 * om
+    m = dict(f=f, r_max=16.0, n_r=48, n_theta=48, rim=1)
+    E, B, cE, cB, dE = _curl(m, _lg("linear", 1, 1, 3.0, z_waist=-6.0), om, [0.31, -0.22, 0.17], 2e-3)
+    assert np.linalg.norm(cE - 1j * k * B) / np.linalg.norm(1j * k * B) < 1e-7
