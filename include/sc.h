@@ -106,7 +106,24 @@ void sc_mirror_free(sc_mirror_t* m);
 /* ---------------------------------------------------------------------- */
 /* Incident field (Sec. III.A; Sec. III.B, Eqs. 14-18; Sec. IV.B, Eq. 27)   */
 
-enum { SC_PROFILE_GAUSS = 0, SC_PROFILE_SUPERGAUSS = 1, SC_PROFILE_TOPHAT = 2 };
+enum {
+    SC_PROFILE_GAUSS = 0,
+    SC_PROFILE_SUPERGAUSS = 1,
+    SC_PROFILE_TOPHAT = 2,
+    SC_PROFILE_LAGUERRE_GAUSS = 3, /* paraxial LG mode with finite Rayleigh range */
+    SC_PROFILE_ENVELOPE = 4        /* the caller's envelope function             */
+};
+
+/*
+ * Caller's transverse envelope (SC_PROFILE_ENVELOPE): for n mirror points
+ * xyz[n][3] and one wavenumber k, write e_perp at each point as
+ * e[n][2][2] = (E_x re, im), (E_y re, im).  It stands for measured maps of
+ * every frequency component on the mirror and for spatio-temporal couplings
+ * (Sec. III.A, Sec. III.B).  The library calls it from the calling thread
+ * while it builds a node table (inside sc_eval / sc_eval_batch / the
+ * serving thread for sc_submit), never concurrently with itself.
+ */
+typedef void (*sc_envelope_fn)(void* user, int n, const double* xyz, double k, double* e);
 enum { SC_POL_LINEAR = 0, SC_POL_RADIAL = 1, SC_POL_AZIMUTHAL = 2 };
 enum {
     SC_SPEC_MONO = 0,              /* a_n = 1                                     */
@@ -117,6 +134,9 @@ enum {
 };
 
 /*
+ * Beam on the mirror.  Kinds 0-2 are the collimated beam below; kinds 3 and
+ * 4 have a complex envelope that depends on k (see after the struct).
+ *
  * Collimated beam on the mirror (the Supplementary Material with the
  * paper's explicit fields is not available; this is the waist-plane limit
  * of its paraxial modes): E_inc = A(rho) p(theta) e^{-ik(z + 2f)} e^{ikW},
@@ -143,7 +163,36 @@ typedef struct {
     int n_zernike;
     const double* zernike_noll_waves;
     int order;
+    /* kinds 3 and 4 */
+    int lg_p, lg_l;           /* Laguerre-Gauss indices (kind 3)                    */
+    double z_waist;           /* waist plane of the Laguerre-Gauss beam (kind 3)    */
+    sc_envelope_fn envelope;  /* kind 4; must stay valid while the handle lives    */
+    void* envelope_user;
+    double omega_lo, omega_hi;  /* band of every omega later evaluated (kinds 3, 4) */
+    double fit_tol;           /* truncation tolerance of the fit in k, relative to  */
+                              /* the envelope's peak (<= 0: 1e-8)                   */
 } sc_profile;
+
+/*
+ * Kinds 3 and 4: E_inc = e_perp(x, y, z; k) e^{-ik(z + 2f)} e^{ikW}, B_inc =
+ * (-z_hat) x E_inc (order 0 only).
+ *   Kind 3, the Laguerre-Gauss mode (p, l) of the paraxial wave equation,
+ *   travelling along -z with its waist (radius w0) at z = z_waist: with
+ *   zeta = z_waist - z, z_R = k w0^2 / 2, w = w0 sqrt(1 + (zeta/z_R)^2),
+ *   1/R = zeta / (zeta^2 + z_R^2) and psi = atan(zeta / z_R),
+ *     u = (w0/w)^(|l|+1) (rho/w0)^|l| L_p^|l|(2 rho^2/w^2) e^{-rho^2/w^2}
+ *         e^{ik rho^2 / (2R)} e^{-i(2p+|l|+1) psi},
+ *   e_perp = u e^{i l theta} p (linear), u rho_hat or u theta_hat (radial,
+ *   azimuthal; |l| = 1).  As z_R -> oo it is the collimated beam above.
+ *   Kind 4, the caller's envelope function.  Its spectrum must be SAMPLED
+ *   or MONO (Eq. 16 has no beam power for it).
+ * The node table holds a Chebyshev expansion of e_perp in k over
+ * [2 pi omega_lo, 2 pi omega_hi], sum_m c_m(node) T_m(x(k)), truncated where
+ * the remaining coefficients sum below fit_tol times the envelope's peak;
+ * the real and imaginary parts of each c_m are tables of their own, so a
+ * beam costs one field pass per table (see sc_eval_stats.tables).  An
+ * envelope that needs more than 20 terms over the band is rejected.
+ */
 
 /* p: fixed direction (cos angle, sin angle, 0), or rho_hat * rho/w0
  * (radial), or theta_hat * rho/w0 (azimuthal). */
@@ -178,8 +227,11 @@ typedef struct {
 
 /* Copy the description of an incident beam.  Errors: SC_ERR_INVALID
  * (unknown kind, w0 <= 0, sg_order < 1, n_zernike outside 0..64, order not
- * 0 or 1, order 1 with a top-hat, a spectrum with non-positive width or
- * lambda_c, SAMPLED with n < 1). */
+ * 0 or 1, order 1 with a top-hat or kinds 3-4, lg_p < 0, |lg_l| != 1 for a
+ * radial or azimuthal kind 3, kind 4 without a function, kinds 3-4 without
+ * 0 < omega_lo < omega_hi, kind 4 with a GAUSS_TIME or SUPERGAUSS_LAMBDA
+ * spectrum, a spectrum with non-positive width or lambda_c, SAMPLED with
+ * n < 1). */
 sc_status sc_incident(sc_ctx* ctx, const sc_profile* prof, const sc_polarization* pol,
                       const sc_spectrum* spec, sc_incident_t** out);
 void sc_incident_free(sc_incident_t* inc);
@@ -198,6 +250,8 @@ typedef struct {
     double field_ms;    /* CUDA-event time of the field-sum launches              */
     double total_ms;    /* CUDA-event time of the whole call on the stream        */
     int launches;       /* kernels launched by the call                           */
+    int tables;         /* node tables summed per evaluation (field passes; for a */
+                        /* batch the largest over its requests)                   */
 } sc_eval_stats;
 
 /*

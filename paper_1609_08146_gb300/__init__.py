@@ -27,7 +27,7 @@ __all__ = ["load", "ScError", "Context", "Mirror", "Incident"]
 SC_OK, SC_ERR_INVALID, SC_ERR_OOM, SC_ERR_CUDA, SC_ERR_TIMEOUT = 0, 1, 2, 3, 4
 SC_ERR_BUSY, SC_ERR_CANCELLED, SC_ERR_NOT_FOUND = 5, 6, 7
 SC_FP32_COMP, SC_FP64 = 0, 1
-PROFILES = {"gauss": 0, "supergauss": 1, "tophat": 2}
+PROFILES = {"gauss": 0, "supergauss": 1, "tophat": 2, "laguerre_gauss": 3, "envelope": 4}
 POLS = {"linear": 0, "radial": 1, "azimuthal": 2}
 SPECTRA = {"mono": 0, "gauss_time": 1, "supergauss_lambda": 2, "sampled": 3}
 SC_OPT_TIME_FIELD, SC_OPT_NODES_PER_SPLIT, SC_OPT_WORKSPACE_CAP, SC_OPT_FLUSH_NODES = 1, 2, 3, 4
@@ -44,7 +44,15 @@ class sc_quadrature(ctypes.Structure):
 
 class sc_profile(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("w0", ctypes.c_double), ("sg_order", ctypes.c_int),
-                ("n_zernike", ctypes.c_int), ("zernike_noll_waves", _DP), ("order", ctypes.c_int)]
+                ("n_zernike", ctypes.c_int), ("zernike_noll_waves", _DP), ("order", ctypes.c_int),
+                ("lg_p", ctypes.c_int), ("lg_l", ctypes.c_int), ("z_waist", ctypes.c_double),
+                ("envelope", ctypes.c_void_p), ("envelope_user", ctypes.c_void_p),
+                ("omega_lo", ctypes.c_double), ("omega_hi", ctypes.c_double), ("fit_tol", ctypes.c_double)]
+
+
+# sc_envelope_fn: (user, n, xyz[n][3], k, e[n][2][2])
+ENVELOPE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                               ctypes.c_double, ctypes.POINTER(ctypes.c_double))
 
 
 class sc_polarization(ctypes.Structure):
@@ -60,7 +68,7 @@ class sc_spectrum(ctypes.Structure):
 
 class sc_eval_stats(ctypes.Structure):
     _fields_ = [("evals", ctypes.c_double), ("field_ms", ctypes.c_double),
-                ("total_ms", ctypes.c_double), ("launches", ctypes.c_int)]
+                ("total_ms", ctypes.c_double), ("launches", ctypes.c_int), ("tables", ctypes.c_int)]
 
 
 class sc_counters(ctypes.Structure):
@@ -170,14 +178,27 @@ class Mirror:
 
 class Incident:
     def __init__(self, ctx, profile="gauss", w0=1.0, sg_order=4, zernike=(), pol="linear",
-                 pol_angle=0.0, spectrum=None, order=0):
+                 pol_angle=0.0, spectrum=None, order=0, lg_p=0, lg_l=0, z_waist=0.0,
+                 omega_band=(0.0, 0.0), fit_tol=0.0, envelope=None):
+        """profile "laguerre_gauss" (lg_p, lg_l, z_waist) or "envelope" (envelope:
+        a function (xyz [n, 3], k) -> e_perp [n, 2] complex) need omega_band =
+        (lo, hi) covering every omega evaluated later."""
         self._lib = ctx._lib
         spectrum = dict(spectrum or {"kind": "mono"})
         self._keep = []
         z = np.ascontiguousarray(zernike, dtype=np.float64)
         self._keep.append(z)
+        self._cb = None
+        if envelope is not None:
+            def _cb(user, n, xyz, k, out, fn=envelope):
+                pts = np.ctypeslib.as_array(xyz, shape=(n, 3)).copy()
+                e = np.asarray(fn(pts, k), dtype=np.complex128).reshape(n, 2)
+                np.ctypeslib.as_array(out, shape=(n, 4))[:] = e.view(np.float64)
+            self._cb = ENVELOPE_FN(_cb)
         prof = sc_profile(PROFILES[profile], float(w0), int(sg_order), int(z.size),
-                          _dptr(z) if z.size else None, int(order))
+                          _dptr(z) if z.size else None, int(order), int(lg_p), int(lg_l), float(z_waist),
+                          ctypes.cast(self._cb, ctypes.c_void_p) if self._cb else None, None,
+                          float(omega_band[0]), float(omega_band[1]), float(fit_tol))
         pl = sc_polarization(POLS[pol], float(pol_angle))
         kind = SPECTRA[spectrum.get("kind", "mono")]
         om = amp = None
@@ -286,7 +307,7 @@ class Context:
                                       ctypes.byref(st) if stats else None))
         if stats:
             return E, B, dict(evals=st.evals, field_ms=st.field_ms, total_ms=st.total_ms,
-                              launches=st.launches)
+                              launches=st.launches, tables=st.tables)
         return E, B
 
     def time_domain(self, E, B, omegas, times, precision: str = "fp32", out=None):
@@ -336,7 +357,7 @@ class Context:
                                             ctypes.byref(st) if stats else None))
         if stats:
             return outs, dict(evals=st.evals, field_ms=st.field_ms, total_ms=st.total_ms,
-                              launches=st.launches)
+                              launches=st.launches, tables=st.tables)
         return outs
 
     # ---- serving

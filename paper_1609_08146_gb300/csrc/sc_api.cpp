@@ -47,6 +47,11 @@ struct sc_incident_t {
     uint64_t id;
     int profile, sg_order, pol;
     int order;                      // 0 collimated, 1 plus the O(eps) longitudinal terms
+    int lg_p = 0, lg_l = 0;         // Laguerre-Gauss mode (profile 3)
+    double z_waist = 0.0;
+    sc_envelope_fn env = nullptr;   // caller's envelope (profile 4)
+    void* env_user = nullptr;
+    double om_lo = 0.0, om_hi = 0.0, fit_tol = 1e-8;  // band and tolerance of the k fit
     double w0, angle;
     std::vector<double> zern;
     int spec_kind;
@@ -62,16 +67,29 @@ struct DevBuf {
     size_t n = 0;
 };
 
+// One node table of an incident.  Every part sums over the same nodes; its
+// sums enter the result with a per-omega complex weight w_p(omega_n):
+//   PART_ONE 1,  PART_INV_K -i/k_n (the 1/k longitudinal terms of order 1),
+//   PART_CHEB_RE T_m(x_n),  PART_CHEB_IM i T_m(x_n)  (x_n = (k_n - kc) / kh,
+//   the Chebyshev expansion in k of a k-dependent envelope).
+enum { PART_ONE = 0, PART_INV_K = 1, PART_CHEB_RE = 2, PART_CHEB_IM = 3 };
+
+struct TablePart {
+    int kind = PART_ONE, m = 0;
+    const float* d32 = nullptr;       // surface tiles, then this part's rim tiles
+    int n_rim_tiles = 0;
+    const sc::Node64* d64 = nullptr;  // surface records, then rim records
+    int n_rim = 0;
+};
+
 struct Table {
     uint64_t mid = 0, iid = 0;
-    float* d32 = nullptr;          // tiled FP32 table, surface tiles then rim tiles
-    int n_surf_tiles = 0, n_rim_tiles = 0;
-    sc::Node64* d64 = nullptr;     // FP64 records, surface then rim
+    float* d32 = nullptr;          // one allocation for every part's FP32 tiles
+    int n_surf_tiles = 0, n_rim_tiles = 0;  // (rim: part 0's)
+    sc::Node64* d64 = nullptr;     // and one for their FP64 records
     int n_surf = 0, n_rim = 0;
-    // first-order beams: the second table (surface nodes only) follows the
-    // first in both allocations; null otherwise
-    const float* d32_1 = nullptr;
-    const sc::Node64* d64_1 = nullptr;
+    std::vector<TablePart> parts;
+    double kc = 0.0, kh = 1.0;     // Chebyshev band in k of the CHEB parts
     size_t bytes = 0;
     uint64_t last_use = 0;
     int inflight = 0;              // serving batches on the GPU that read this table
@@ -374,6 +392,46 @@ double profile_damp(const sc_incident_t* in, double rho)
 // forms: linear  div e = A' cos(th - a), div b = A' sin(a - th);
 //        radial  div e = (2A + rho A') / w0, div b = 0;
 //        azimuthal div e = 0, div b = (2A + rho A') / w0.
+// Laguerre-Gauss envelope of kind 3 at (x, y, z) and wavenumber k: complex
+// (e_x, e_y) as (re, im) pairs.  L_p^a by upward recurrence in p.
+void lg_envelope(const sc_incident_t* in, double k, double x, double y, double z, double e[4])
+{
+    const double w0 = in->w0, zr = 0.5 * k * w0 * w0, zeta = in->z_waist - z;
+    const double q = zeta / zr;
+    const double w2 = w0 * w0 * (1.0 + q * q);
+    const double rho2 = x * x + y * y, rho = sqrt(rho2), th = atan2(y, x);
+    const int a = in->pol == SC_POL_LINEAR ? abs(in->lg_l) : 1;
+    const double X = 2.0 * rho2 / w2;
+    double L = 1.0;
+    if (in->lg_p > 0) {
+        double lm = 1.0, lc = 1.0 + a - X;
+        for (int n = 1; n < in->lg_p; ++n) {
+            const double ln = ((2.0 * n + 1.0 + a - X) * lc - (n + a) * lm) / (n + 1.0);
+            lm = lc;
+            lc = ln;
+        }
+        L = lc;
+    }
+    const double amp = pow(w0 * w0 / w2, 0.5 * (a + 1)) * pow(rho / w0, a) * L * exp(-rho2 / w2);
+    // phase: k rho^2 zeta / (2 (zeta^2 + z_R^2)) - (2p + a + 1) atan(zeta / z_R)
+    double ph = 0.5 * k * rho2 * zeta / (zeta * zeta + zr * zr) - (2.0 * in->lg_p + a + 1) * atan(q);
+    double px = 1.0, py = 0.0;  // polarisation (real for the vector modes)
+    if (in->pol == SC_POL_LINEAR) {
+        ph += in->lg_l * th;
+        px = cos(in->angle);
+        py = sin(in->angle);
+    } else if (in->pol == SC_POL_RADIAL) {
+        px = cos(th);
+        py = sin(th);
+    } else {
+        px = -sin(th);
+        py = cos(th);
+    }
+    const double ur = amp * cos(ph), ui = amp * sin(ph);
+    e[0] = ur * px; e[1] = ui * px;
+    e[2] = ur * py; e[3] = ui * py;
+}
+
 void incident_div(const sc_incident_t* in, double rho, double th, double& div_e, double& div_b)
 {
     const double A = profile_amp(in, rho), dA = profile_damp(in, rho);
@@ -392,6 +450,11 @@ double beam_power(const sc_incident_t* in)
 {
     const double w2 = in->w0 * in->w0;
     const bool lin = in->pol == SC_POL_LINEAR;
+    if (in->profile == SC_PROFILE_LAGUERRE_GAUSS) {
+        // (pi w0^2 / 2) 2^-a Gamma(p + a + 1) / p!, a = |l| (1 for the vector modes)
+        const int a = lin ? abs(in->lg_l) : 1;
+        return kPi * w2 / 2.0 * pow(2.0, -a) * tgamma(in->lg_p + a + 1.0) / tgamma(in->lg_p + 1.0);
+    }
     if (in->profile == SC_PROFILE_GAUSS) return lin ? kPi * w2 / 2.0 : kPi * w2 / 4.0;
     if (in->profile == SC_PROFILE_SUPERGAUSS) {
         const double N = in->sg_order;
@@ -551,6 +614,130 @@ void build_nodes(const sc_mirror_t* m, const sc_incident_t* in, std::vector<Host
     }
 }
 
+// Host nodes of one table part (see TablePart).
+struct HostPart {
+    int kind = PART_ONE, m = 0;
+    std::vector<HostNode> surf, rim;
+};
+
+// Kinds 3 and 4: Chebyshev expansion in k of the envelope e_perp over the
+// band [kc - kh, kc + kh], from kCheb samples at the Chebyshev points
+// x_j = cos(pi (j + 1/2) / kCheb): c_m = (2 - [m = 0]) / kCheb sum_j f(x_j)
+// T_m(x_j).  It keeps the first M terms, M the least with sum_{m >= M}
+// max |c_m| <= fit_tol max |f|; the real and imaginary parts of each kept
+// c_m become parts of their own (a part that is zero everywhere is left
+// out).  B~ = (-z) x E~ (order 0).
+constexpr int kCheb = 24;
+constexpr int kChebMaxTerms = 20;
+
+sc_status build_cheb_parts(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in,
+                           std::vector<HostPart>& parts, double& kc, double& kh)
+{
+    const double f = m->f;
+    const int nr = m->q.n_r, nt = m->q.n_theta;
+    std::vector<double> gr, gw;
+    gauss_legendre(nr, m->r_min, m->r_max, gr, gw);
+    const double dth = 2.0 * kPi / nt;
+    // node positions: surface (r_i, theta_l), then the rim edges
+    struct Pos { double r, th; int edge; };
+    std::vector<Pos> pos;
+    pos.reserve((size_t)nr * nt + 2 * (size_t)nt);
+    for (int i = 0; i < nr; ++i)
+        for (int l = 0; l < nt; ++l) pos.push_back({gr[i], l * dth, -1});
+    const size_t n_surf = pos.size();
+    if (m->q.rim_term)
+        for (int edge = 0; edge < 2; ++edge) {
+            const double r = edge == 0 ? m->r_max : m->r_min;
+            if (r <= 0.0) continue;
+            for (int l = 0; l < nt; ++l) pos.push_back({r, l * dth, edge});
+        }
+    const size_t n = pos.size();
+    std::vector<double> xyz(3 * n);
+    for (size_t j = 0; j < n; ++j) {
+        xyz[3 * j] = pos[j].r * cos(pos[j].th);
+        xyz[3 * j + 1] = pos[j].r * sin(pos[j].th);
+        xyz[3 * j + 2] = pos[j].r * pos[j].r / (4.0 * f) - f;
+    }
+    kc = kPi * (in->om_lo + in->om_hi);
+    kh = kPi * (in->om_hi - in->om_lo);
+    // coefficients c[m][node][4] (e_x re, im, e_y re, im)
+    std::vector<double> c((size_t)kCheb * n * 4, 0.0), e(4 * n);
+    double peak = 0.0;
+    for (int j = 0; j < kCheb; ++j) {
+        const double tj = kPi * (j + 0.5) / kCheb;
+        const double k = kc + kh * cos(tj);
+        if (in->profile == SC_PROFILE_LAGUERRE_GAUSS) {
+            for (size_t q = 0; q < n; ++q) lg_envelope(in, k, xyz[3 * q], xyz[3 * q + 1], xyz[3 * q + 2], &e[4 * q]);
+        } else {
+            std::fill(e.begin(), e.end(), 0.0);
+            in->env(in->env_user, (int)n, xyz.data(), k, e.data());
+        }
+        for (double v : e)
+            if (!std::isfinite(v)) return fail(ctx, SC_ERR_INVALID, "the envelope is not finite on the mirror");
+        for (size_t q = 0; q < 4 * n; q += 2) peak = std::max(peak, std::hypot(e[q], e[q + 1]));
+        for (int mm = 0; mm < kCheb; ++mm) {
+            const double w = (mm == 0 ? 1.0 : 2.0) / kCheb * cos(mm * tj);
+            double* cm = &c[(size_t)mm * n * 4];
+            for (size_t q = 0; q < 4 * n; ++q) cm[q] += w * e[q];
+        }
+    }
+    if (!(peak > 0.0)) return fail(ctx, SC_ERR_INVALID, "the envelope vanishes on the mirror");
+    std::vector<double> cmax(kCheb, 0.0);
+    for (int mm = 0; mm < kCheb; ++mm) {
+        const double* cm = &c[(size_t)mm * n * 4];
+        for (size_t q = 0; q < 4 * n; q += 2) cmax[mm] = std::max(cmax[mm], std::hypot(cm[q], cm[q + 1]));
+    }
+    int M = kCheb;
+    double tail = 0.0;
+    while (M > 1 && tail + cmax[M - 1] <= in->fit_tol * peak) tail += cmax[--M];
+    if (M > kChebMaxTerms)
+        return fail(ctx, SC_ERR_INVALID,
+                    "the envelope needs more than %d Chebyshev terms in k over the band (tolerance %g)",
+                    kChebMaxTerms, in->fit_tol);
+    parts.clear();
+    for (int mm = 0; mm < M; ++mm)
+        for (int im = 0; im < 2; ++im) {
+            const double* cm = &c[(size_t)mm * n * 4];
+            double pmax = 0.0;
+            for (size_t q = 0; q < n; ++q)
+                pmax = std::max(pmax, std::max(fabs(cm[4 * q + im]), fabs(cm[4 * q + 2 + im])));
+            if (pmax <= 1e-3 * in->fit_tol * peak) continue;
+            HostPart hp;
+            hp.kind = im ? PART_CHEB_IM : PART_CHEB_RE;
+            hp.m = mm;
+            hp.surf.reserve(n_surf);
+            for (size_t q = 0; q < n; ++q) {
+                const double ex = cm[4 * q + im], ey = cm[4 * q + 2 + im];
+                const double bx = ey, by = -ex;  // B~ = (-z) x E~
+                const double r = pos[q].r, th = pos[q].th;
+                const double x = xyz[3 * q], y = xyz[3 * q + 1];
+                const double Nx = -x / (2.0 * f), Ny = -y / (2.0 * f);
+                HostNode nd;
+                nd.px = x; nd.py = y; nd.pz = xyz[3 * q + 2];
+                nd.pn = r * r / (4.0 * f) + f;
+                nd.w = incident_opd(in, r, th, m->r_max);
+                if (q < n_surf) {
+                    const double wq = gw[q / nt] * dth * r / (2.0 * kPi);
+                    nd.jx = -by * wq;  // N x B~ with B~_z = 0, N_z = 1
+                    nd.jy = bx * wq;
+                    nd.jz = (Nx * by - Ny * bx) * wq;
+                    nd.rho = (Nx * ex + Ny * ey) * wq;
+                    hp.surf.push_back(nd);
+                } else {
+                    const double sgn = pos[q].edge == 0 ? 1.0 : -1.0;
+                    const double nlen2 = 1.0 + r * r / (4.0 * f * f);
+                    const double jx = -by, jy = bx, jz = Nx * by - Ny * bx;
+                    const double qq = sgn * (jx * cos(th) + jy * sin(th) + jz * r / (2.0 * f)) / nlen2 * r * dth;
+                    nd.jx = nd.jy = nd.jz = 0.0;
+                    nd.rho = qq / (2.0 * kPi);
+                    hp.rim.push_back(nd);
+                }
+            }
+            parts.push_back(std::move(hp));
+        }
+    return SC_OK;
+}
+
 void pack_tiles(const std::vector<HostNode>& v, std::vector<float>& out, int& n_tiles)
 {
     n_tiles = (int)((v.size() + sc::kTile - 1) / sc::kTile);
@@ -593,20 +780,49 @@ sc_status get_table(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, 
             *out = &t;
             return SC_OK;
         }
-    std::vector<HostNode> surf, rim, surf1;
-    build_nodes(m, in, surf, rim, surf1);
-    std::vector<float> ts, tr, ts1;
+    std::vector<HostPart> hp;
     Table t;
     t.mid = m->id;
     t.iid = in->id;
-    pack_tiles(surf, ts, t.n_surf_tiles);
-    if (!rim.empty()) pack_tiles(rim, tr, t.n_rim_tiles);
-    int n1_tiles = 0;
-    if (!surf1.empty()) pack_tiles(surf1, ts1, n1_tiles);
-    t.n_surf = (int)surf.size();
-    t.n_rim = (int)rim.size();
-    const size_t b32 = (ts.size() + tr.size() + ts1.size()) * sizeof(float);
-    const size_t b64 = (surf.size() + rim.size() + surf1.size()) * sizeof(sc::Node64);
+    if (in->profile >= SC_PROFILE_LAGUERRE_GAUSS) {
+        sc_status st = build_cheb_parts(ctx, m, in, hp, t.kc, t.kh);
+        if (st != SC_OK) return st;
+    } else {
+        hp.resize(1);
+        std::vector<HostNode> surf1;
+        build_nodes(m, in, hp[0].surf, hp[0].rim, surf1);
+        if (!surf1.empty()) {
+            HostPart p1;
+            p1.kind = PART_INV_K;
+            p1.surf = std::move(surf1);
+            hp.push_back(std::move(p1));
+        }
+    }
+    // FP32 tiles and FP64 records of every part, part after part
+    std::vector<float> t32;
+    std::vector<sc::Node64> h64;
+    std::vector<size_t> off32, off64;
+    std::vector<int> rim_tiles;
+    for (const auto& p : hp) {
+        std::vector<float> ts, tr;
+        int nst = 0, nrt = 0;
+        pack_tiles(p.surf, ts, nst);
+        if (!p.rim.empty()) pack_tiles(p.rim, tr, nrt);
+        t.n_surf_tiles = nst;
+        t.n_surf = (int)p.surf.size();
+        off32.push_back(t32.size());
+        off64.push_back(h64.size());
+        rim_tiles.push_back(nrt);
+        t32.insert(t32.end(), ts.begin(), ts.end());
+        t32.insert(t32.end(), tr.begin(), tr.end());
+        for (const auto* vec : {&p.surf, &p.rim})
+            for (const auto& nd : *vec)
+                h64.push_back(sc::Node64{nd.px, nd.py, nd.pz, nd.pn, nd.w, nd.jx, nd.jy, nd.jz, nd.rho, 0.0});
+    }
+    t.n_rim_tiles = rim_tiles[0];
+    t.n_rim = (int)hp[0].rim.size();
+    const size_t b32 = t32.size() * sizeof(float);
+    const size_t b64 = h64.size() * sizeof(sc::Node64);
     t.bytes = b32 + b64;
     // evict least recently used tables while over budget
     while (ctx->budget && ctx->held + t.bytes > ctx->budget && !ctx->tables.empty()) {
@@ -630,30 +846,59 @@ sc_status get_table(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, 
         if (t.d32) cudaFree(t.d32);
         return fail(ctx, SC_ERR_OOM, "node table allocation failed: %s", cudaGetErrorString(e));
     }
-    std::vector<sc::Node64> h64;
-    h64.reserve(surf.size() + rim.size() + surf1.size());
-    for (auto* vec : {&surf, &rim, &surf1})
-        for (const auto& nd : *vec)
-            h64.push_back(sc::Node64{nd.px, nd.py, nd.pz, nd.pn, nd.w, nd.jx, nd.jy, nd.jz, nd.rho, 0.0});
-    SC_CUDA(cudaMemcpyAsync(t.d32, ts.data(), ts.size() * sizeof(float), cudaMemcpyHostToDevice,
-                            stream), "upload node table");
-    if (!tr.empty())
-        SC_CUDA(cudaMemcpyAsync(t.d32 + ts.size(), tr.data(), tr.size() * sizeof(float),
-                                cudaMemcpyHostToDevice, stream), "upload rim table");
-    if (!ts1.empty()) {
-        t.d32_1 = t.d32 + ts.size() + tr.size();
-        t.d64_1 = t.d64 + surf.size() + rim.size();
-        SC_CUDA(cudaMemcpyAsync(t.d32 + ts.size() + tr.size(), ts1.data(), ts1.size() * sizeof(float),
-                                cudaMemcpyHostToDevice, stream), "upload first-order table");
+    for (size_t i = 0; i < hp.size(); ++i) {
+        TablePart tp;
+        tp.kind = hp[i].kind;
+        tp.m = hp[i].m;
+        tp.d32 = t.d32 + off32[i];
+        tp.n_rim_tiles = rim_tiles[i];
+        tp.d64 = t.d64 + off64[i];
+        tp.n_rim = (int)hp[i].rim.size();
+        t.parts.push_back(tp);
     }
-    SC_CUDA(cudaMemcpyAsync(t.d64, h64.data(), b64, cudaMemcpyHostToDevice, stream),
-            "upload FP64 table");
+    SC_CUDA(cudaMemcpyAsync(t.d32, t32.data(), b32, cudaMemcpyHostToDevice, stream), "upload node tables");
+    SC_CUDA(cudaMemcpyAsync(t.d64, h64.data(), b64, cudaMemcpyHostToDevice, stream), "upload FP64 tables");
     // the host vectors die at return: make the copies complete first
     SC_CUDA(cudaStreamSynchronize(stream), "node table upload");
     ctx->held += t.bytes;
     t.last_use = ctx->tick;
     ctx->tables.push_back(t);
     *out = &ctx->tables.back();
+    return SC_OK;
+}
+
+// Per-part amplitudes of one request, [n_parts][n][2]: a_n times the part's
+// weight w_p(omega_n).  Chebyshev parts need every omega inside their band.
+sc_status request_amps(sc_ctx* ctx, const sc_incident_t* in, const Table* tab, const double* om, int n,
+                       std::vector<double>& out)
+{
+    std::vector<double> a;
+    sc_status st = spectrum_amps(ctx, in, om, n, a);
+    if (st != SC_OK) return st;
+    const size_t np = tab->parts.size();
+    out.assign(np * 2 * (size_t)n, 0.0);
+    for (size_t p = 0; p < np; ++p) {
+        const TablePart& tp = tab->parts[p];
+        for (int i = 0; i < n; ++i) {
+            const double k = 2.0 * kPi * om[i];
+            double wr = 1.0, wi = 0.0;
+            if (tp.kind == PART_INV_K) {
+                wr = 0.0;
+                wi = -1.0 / k;
+            } else if (tp.kind != PART_ONE) {
+                const double x = (k - tab->kc) / tab->kh;
+                if (!(fabs(x) <= 1.0 + 1e-12))
+                    return fail(ctx, SC_ERR_INVALID, "omega %.17g lies outside the beam's band [%g, %g]", om[i],
+                                in->om_lo, in->om_hi);
+                const double T = cos(tp.m * acos(std::max(-1.0, std::min(1.0, x))));
+                wr = tp.kind == PART_CHEB_RE ? T : 0.0;
+                wi = tp.kind == PART_CHEB_RE ? 0.0 : T;
+            }
+            const double ar = a[2 * i], ai = a[2 * i + 1];
+            out[(p * n + i) * 2] = ar * wr - ai * wi;
+            out[(p * n + i) * 2 + 1] = ar * wi + ai * wr;
+        }
+    }
     return SC_OK;
 }
 
@@ -733,6 +978,7 @@ bool uniform_grid(const double* om, int n, double& d)
     return true;
 }
 
+
 // ------------------------------------------------------------------------
 // Batched FP32 execution (A8): requests are cut into chunks (<= 2048 omegas,
 // points bounded by the workspace cap); chunks of one kernel class run in one
@@ -744,25 +990,23 @@ bool uniform_grid(const double* om, int n, double& d)
 // request gives bitwise the same result alone or in a mix.
 
 struct Chunk {
-    sc::FieldLaunch f;      // ws assigned at execution
-    sc::FieldLaunch f1;     // first-order table of the same chunk (when has1)
-    sc::ReduceLaunch rl;    // ws, ws1, off assigned at execution
+    sc::FieldLaunch f;      // part 0; ws assigned at execution
+    sc::ReduceLaunch rl;    // ws, off assigned at execution
+    const Table* tab = nullptr;  // its parts share f's points, omegas and splits
+    int n_parts = 1;
     int cls = 0, ppc = 1, pb = 1;
-    bool has1 = false;
-    size_t ws_elems = 0;    // float2 elements, both tables
+    size_t ws_elems = 0;    // float2 elements, every part (one section each)
 };
 
-// Split a chunk's surface tiles S ways; the first-order table (same nodes)
-// uses the same splits and a workspace section of its own after the first.
+// Split a chunk's surface tiles S ways.  Every table part (same nodes) uses
+// the same splits and a workspace section of its own.
 void set_splits(Chunk& c, int S, int tiles)
 {
     const int tps = (tiles + S - 1) / S;
     c.f.tiles_per_split = tps;
     c.f.n_splits = (tiles + tps - 1) / tps;
-    c.f1.tiles_per_split = tps;
-    c.f1.n_splits = c.f.n_splits;
     c.rl.n_splits = c.f.n_splits;
-    c.ws_elems = (size_t)(c.f.n_splits + 1) * c.f.n_pts * c.f.n_omega * sc::kAcc * (c.has1 ? 2 : 1);
+    c.ws_elems = (size_t)(c.f.n_splits + 1) * c.f.n_pts * c.f.n_omega * sc::kAcc * c.n_parts;
 }
 
 int heuristic_splits(int tiles, long long pb, int slots)
@@ -803,7 +1047,7 @@ sc_status choose_splits(sc_ctx* ctx, Lane& ln, Chunk& c, const Table* tab, int s
         *S_out = (tiles + tps - 1) / tps;
         return SC_OK;
     }
-    const auto key = std::make_tuple(c.cls, tiles, tab->n_rim_tiles, c.f.n_pts, c.f.n_omega, (int)c.has1);
+    const auto key = std::make_tuple(c.cls, tiles, tab->n_rim_tiles, c.f.n_pts, c.f.n_omega, c.n_parts);
     auto hit = ctx->tuned.find(key);
     if (hit != ctx->tuned.end()) {
         *S_out = hit->second;
@@ -824,7 +1068,7 @@ sc_status choose_splits(sc_ctx* ctx, Lane& ln, Chunk& c, const Table* tab, int s
         for (int s : cand) {
             const int tps = (tiles + s - 1) / s;
             const int ns = (tiles + tps - 1) / tps;
-            const size_t n = (size_t)(ns + 1) * c.f.n_pts * c.f.n_omega * sc::kAcc * (c.has1 ? 2 : 1);
+            const size_t n = (size_t)(ns + 1) * c.f.n_pts * c.f.n_omega * sc::kAcc * c.n_parts;
             if (n * sizeof(float2) <= ctx->ws_cap) {
                 fit.push_back(s);
                 need = std::max(need, n);
@@ -881,21 +1125,17 @@ sc_status plan_request(sc_ctx* ctx, Lane& ln, const Table* tab, const double* om
         c.rl.B = dB ? dB + (size_t)o0 * n_points * 3 : nullptr;
         c.rl.n_pts = n_points;
         c.rl.n_omega = no;
-        c.rl.ws1 = nullptr;
-        c.has1 = tab->d32_1 != nullptr;
-        if (c.has1) {
-            // the first-order table: surface nodes only (its rim term vanishes)
-            c.f1 = c.f;
-            c.f1.nodes = tab->d32_1;
-            c.f1.n_rim_tiles = 0;
-        }
+        c.tab = tab;
+        c.n_parts = (int)tab->parts.size();
+        c.rl.n_parts = c.n_parts;
+        c.rl.amp_stride = 2LL * n_omega;
         int S = 1;
         sc_status st = choose_splits(ctx, ln, c, tab, slots, &S);
         if (st != SC_OK) return st;
         set_splits(c, S, tab->n_surf_tiles);
         const int n_splits = c.f.n_splits;
         // point chunks bounded by the workspace cap
-        const size_t per_pt = (size_t)(n_splits + 1) * no * sc::kAcc * (c.has1 ? 2 : 1);
+        const size_t per_pt = (size_t)(n_splits + 1) * no * sc::kAcc * c.n_parts;
         long long pchunk = std::max<long long>(1, (long long)(ctx->ws_cap / sizeof(float2) / per_pt));
         if (pchunk < n_points) pchunk = std::max<long long>(c.ppc, pchunk / c.ppc * c.ppc);
         for (int p0 = 0; p0 < n_points; p0 += (int)pchunk) {
@@ -903,8 +1143,6 @@ sc_status plan_request(sc_ctx* ctx, Lane& ln, const Table* tab, const double* om
             Chunk d = c;
             d.f.pts = d_pts + 3 * (size_t)p0;
             d.f.n_pts = np;
-            d.f1.pts = d.f.pts;
-            d.f1.n_pts = np;
             d.pb = (np + c.ppc - 1) / c.ppc;
             d.rl.n_pts = np;
             d.rl.E = c.rl.E + (size_t)p0 * 3;
@@ -927,8 +1165,6 @@ sc_status launch_chunks(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch, float2* w
     for (auto& c : ch) {
         c.f.ws = ws + off;
         c.rl.ws = ws + off;
-        c.f1.ws = c.has1 ? ws + off + c.ws_elems / 2 : nullptr;
-        c.rl.ws1 = c.f1.ws;
         c.rl.off = roff;
         off += c.ws_elems;
         roff += (long long)c.rl.n_pts * c.rl.n_omega;
@@ -939,9 +1175,12 @@ sc_status launch_chunks(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch, float2* w
     std::vector<sc::WorkReq> reqs[kClasses];
     long long items[kClasses] = {};
     for (auto& c : ch)
-        for (int t = 0; t < (c.has1 ? 2 : 1); ++t) {
+        for (int t = 0; t < c.n_parts; ++t) {
             sc::WorkReq w;
-            w.f = t == 0 ? c.f : c.f1;
+            w.f = c.f;
+            w.f.nodes = c.tab->parts[t].d32;
+            w.f.n_rim_tiles = c.tab->parts[t].n_rim_tiles;
+            w.f.ws = c.f.ws + (size_t)t * (c.ws_elems / c.n_parts);
             w.pb = c.pb;
             w.cls = c.cls;
             w.item0 = items[c.cls];
@@ -1172,7 +1411,7 @@ sc_status launch_batch(sc_ctx* ctx, Server* srv, int L, const std::vector<uint64
     Lane& ln = srv->lanes[L];
     ctx->tick++;
     std::vector<double> amp_all, k_all;
-    std::vector<size_t> om_off;
+    std::vector<size_t> om_off, amp_off;
     for (uint64_t id : ids) {
         Ticket& t = srv->tickets[id];
         t.state = 1;
@@ -1198,8 +1437,9 @@ sc_status launch_batch(sc_ctx* ctx, Server* srv, int L, const std::vector<uint64
             t.B = t.B_user;
         }
         std::vector<double> a;
-        st = spectrum_amps(ctx, t.incident, t.omegas.data(), t.n_omega, a);
+        st = request_amps(ctx, t.incident, t.tab, t.omegas.data(), t.n_omega, a);
         if (st != SC_OK) return st;
+        amp_off.push_back(amp_all.size());
         om_off.push_back(k_all.size());
         amp_all.insert(amp_all.end(), a.begin(), a.end());
         for (double w : t.omegas) k_all.push_back(2.0 * kPi * w);
@@ -1215,7 +1455,7 @@ sc_status launch_batch(sc_ctx* ctx, Server* srv, int L, const std::vector<uint64
     for (size_t i = 0; i < ids.size(); ++i) {
         Ticket& t = srv->tickets[ids[i]];
         st = plan_request(ctx, ln, t.tab, t.omegas.data(), t.n_omega, t.dom, t.pts, t.n_points,
-                          (const double*)ln.amp.p + 2 * om_off[i], (const double*)ln.kval.p + om_off[i],
+                          (const double*)ln.amp.p + amp_off[i], (const double*)ln.kval.p + om_off[i],
                           (float2*)t.E, (float2*)t.B, ch);
         if (st != SC_OK) return st;
         ctx->ctr.evals += (double)t.n_points * t.tab->n_surf * t.n_omega;
@@ -1442,12 +1682,22 @@ sc_status sc_incident(sc_ctx* ctx, const sc_profile* prof, const sc_polarization
 {
     if (!out || !prof || !pol || !spec) return fail(ctx, SC_ERR_INVALID, "null argument");
     *out = nullptr;
-    if (prof->kind < 0 || prof->kind > 2 || !(prof->w0 > 0.0) ||
+    if (prof->kind < 0 || prof->kind > 4 || !(prof->w0 > 0.0) ||
         (prof->kind == SC_PROFILE_SUPERGAUSS && prof->sg_order < 1) || prof->n_zernike < 0 ||
         prof->n_zernike > 64 || (prof->n_zernike > 0 && !prof->zernike_noll_waves))
         return fail(ctx, SC_ERR_INVALID, "invalid beam profile");
-    if (prof->order < 0 || prof->order > 1 || (prof->order == 1 && prof->kind == SC_PROFILE_TOPHAT))
-        return fail(ctx, SC_ERR_INVALID, "beam order must be 0 or 1 (1 needs a smooth profile)");
+    if (prof->order < 0 || prof->order > 1 || (prof->order == 1 && prof->kind >= SC_PROFILE_TOPHAT))
+        return fail(ctx, SC_ERR_INVALID, "beam order must be 0 or 1 (1 needs a smooth collimated profile)");
+    if (prof->kind >= SC_PROFILE_LAGUERRE_GAUSS) {
+        if (!(prof->omega_lo > 0.0) || !(prof->omega_hi > prof->omega_lo))
+            return fail(ctx, SC_ERR_INVALID, "kinds 3-4 need a band 0 < omega_lo < omega_hi");
+        if (prof->kind == SC_PROFILE_LAGUERRE_GAUSS &&
+            (prof->lg_p < 0 || prof->lg_p > 32 || (pol && pol->kind != SC_POL_LINEAR && abs(prof->lg_l) != 1)))
+            return fail(ctx, SC_ERR_INVALID, "Laguerre-Gauss needs 0 <= p <= 32 and |l| = 1 when radial or azimuthal");
+        if (prof->kind == SC_PROFILE_ENVELOPE &&
+            (!prof->envelope || spec->kind == SC_SPEC_GAUSS_TIME || spec->kind == SC_SPEC_SUPERGAUSS_LAMBDA))
+            return fail(ctx, SC_ERR_INVALID, "an envelope beam needs a function and a SAMPLED or MONO spectrum");
+    }
     if (pol->kind < 0 || pol->kind > 2) return fail(ctx, SC_ERR_INVALID, "invalid polarization");
     if (spec->kind < 0 || spec->kind > 3) return fail(ctx, SC_ERR_INVALID, "invalid spectrum kind");
     if (!(spec->lambda_c > 0.0) && spec->kind != SC_SPEC_MONO && spec->kind != SC_SPEC_SAMPLED)
@@ -1466,6 +1716,14 @@ sc_status sc_incident(sc_ctx* ctx, const sc_profile* prof, const sc_polarization
     in->sg_order = prof->sg_order;
     in->order = prof->order;
     in->w0 = prof->w0;
+    in->lg_p = prof->lg_p;
+    in->lg_l = prof->lg_l;
+    in->z_waist = prof->z_waist;
+    in->env = prof->envelope;
+    in->env_user = prof->envelope_user;
+    in->om_lo = prof->omega_lo;
+    in->om_hi = prof->omega_hi;
+    in->fit_tol = prof->fit_tol > 0.0 ? prof->fit_tol : 1e-8;
     in->zern.assign(prof->zernike_noll_waves, prof->zernike_noll_waves + prof->n_zernike);
     in->pol = pol->kind;
     in->angle = pol->angle_rad;
@@ -1531,15 +1789,14 @@ sc_status sc_eval(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, co
     const bool timing_before = ctx->time_field;
     if (stats) ctx->time_field = true;
 
-    std::vector<double> amp;
-    sc_status st = spectrum_amps(ctx, in, omegas, n_omega, amp);
+    Table* tab = nullptr;
+    sc_status st = get_table(ctx, m, in, &tab, ctx->stream);
+    if (st != SC_OK) return st;
+    std::vector<double> amp;  // [part][omega][2]
+    st = request_amps(ctx, in, tab, omegas, n_omega, amp);
     if (st != SC_OK) return st;
     std::vector<double> kv(n_omega);
     for (int i = 0; i < n_omega; ++i) kv[i] = 2.0 * kPi * omegas[i];
-
-    Table* tab = nullptr;
-    st = get_table(ctx, m, in, &tab, ctx->stream);
-    if (st != SC_OK) return st;
 
     // points on the device
     const double* d_pts = points_xyz;
@@ -1578,34 +1835,36 @@ sc_status sc_eval(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, co
     const double evals = (double)n_points * (double)tab->n_surf * (double)n_omega;
 
     if (prec == SC_FP64) {
-        sc::Field64Launch a;
-        a.surf = tab->d64;
-        a.n_surf = tab->n_surf;
-        a.rim = tab->d64 + tab->n_surf;
-        a.n_rim = tab->n_rim;
-        a.surf1 = tab->d64_1;
-        a.n_surf1 = tab->d64_1 ? tab->n_surf : 0;
-        a.pts = d_pts;
-        a.n_pts = n_points;
-        a.kval = d_k;
-        a.n_omega = n_omega;
-        a.amp = d_amp;
-        a.E = (double2*)dE;
-        a.B = (double2*)dB;
         cudaEvent_t f0 = nullptr, f1 = nullptr;
         if (ctx->time_field) {
             f0 = take_event(ctx);
             f1 = take_event(ctx);
             cudaEventRecord(f0, ctx->stream);
         }
-        const int r = sc::launch_field_f64(a, ctx->stream);
-        if (r < 0) return cuda_fail(ctx, (cudaError_t)(-r), "FP64 field kernel launch");
+        for (size_t p = 0; p < tab->parts.size(); ++p) {
+            const TablePart& tp = tab->parts[p];
+            sc::Field64Launch a;
+            a.surf = tp.d64;
+            a.n_surf = tab->n_surf;
+            a.rim = tp.d64 + tab->n_surf;
+            a.n_rim = tp.n_rim;
+            a.pts = d_pts;
+            a.n_pts = n_points;
+            a.kval = d_k;
+            a.n_omega = n_omega;
+            a.amp = d_amp + p * 2 * (size_t)n_omega;
+            a.E = (double2*)dE;
+            a.B = (double2*)dB;
+            a.accumulate = p > 0;
+            const int r = sc::launch_field_f64(a, ctx->stream);
+            if (r < 0) return cuda_fail(ctx, (cudaError_t)(-r), "FP64 field kernel launch");
+            ctx->ctr.launches += r;
+            ctx->ctr.field_launches += 1;
+        }
         if (ctx->time_field) {
             cudaEventRecord(f1, ctx->stream);
             ctx->pending.push_back({f0, f1});
         }
-        ctx->ctr.launches += r;
-        ctx->ctr.field_launches += 1;
     } else {
         std::vector<Chunk> ch;
         st = plan_request(ctx, ctx->main, tab, omegas, n_omega, dom, d_pts, n_points, d_amp, d_k,
@@ -1636,6 +1895,7 @@ sc_status sc_eval(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, co
         stats->total_ms = ms;
         stats->field_ms = ctx->ctr.field_ms - field_ms_before;
         stats->launches = (int)(ctx->ctr.launches - launches_before);
+        stats->tables = (int)tab->parts.size();
         ctx->time_field = timing_before;
     }
     return SC_OK;
@@ -1675,25 +1935,26 @@ sc_status sc_eval_batch(sc_ctx* ctx, const sc_request* reqs, int n_req, sc_eval_
         cudaEventRecord(ev0, ctx->stream);
         ctx->time_field = true;
     }
-    // spectra and wavenumbers of all requests, one upload
-    std::vector<double> amp_all(2 * n_om_total), k_all(n_om_total);
-    std::vector<size_t> om_off(n_req);
-    size_t o = 0;
-    for (int r = 0; r < n_req; ++r) {
-        std::vector<double> a;
-        sc_status st = spectrum_amps(ctx, reqs[r].incident, reqs[r].omegas, reqs[r].n_omega, a);
-        if (st != SC_OK) return st;
-        om_off[r] = o;
-        std::copy(a.begin(), a.end(), amp_all.begin() + 2 * o);
-        for (int i = 0; i < reqs[r].n_omega; ++i) k_all[o + i] = 2.0 * kPi * reqs[r].omegas[i];
-        o += reqs[r].n_omega;
-    }
     std::vector<Table*> tabs(n_req);
     double evals = 0.0;
     for (int r = 0; r < n_req; ++r) {
         sc_status st = get_table(ctx, reqs[r].mirror, reqs[r].incident, &tabs[r], ctx->main.stream);
         if (st != SC_OK) return st;
         evals += (double)reqs[r].n_points * tabs[r]->n_surf * reqs[r].n_omega;
+    }
+    // per-part spectra and wavenumbers of all requests, one upload
+    std::vector<double> amp_all, k_all(n_om_total);
+    std::vector<size_t> amp_off(n_req), om_off(n_req);
+    size_t o = 0;
+    for (int r = 0; r < n_req; ++r) {
+        std::vector<double> a;
+        sc_status st = request_amps(ctx, reqs[r].incident, tabs[r], reqs[r].omegas, reqs[r].n_omega, a);
+        if (st != SC_OK) return st;
+        amp_off[r] = amp_all.size();
+        om_off[r] = o;
+        amp_all.insert(amp_all.end(), a.begin(), a.end());
+        for (int i = 0; i < reqs[r].n_omega; ++i) k_all[o + i] = 2.0 * kPi * reqs[r].omegas[i];
+        o += reqs[r].n_omega;
     }
     sc_status st;
     Lane& ln = ctx->main;
@@ -1707,7 +1968,7 @@ sc_status sc_eval_batch(sc_ctx* ctx, const sc_request* reqs, int n_req, sc_eval_
     for (int r = 0; r < n_req; ++r) {
         const sc_request& q = reqs[r];
         st = plan_request(ctx, ln, tabs[r], q.omegas, q.n_omega, dom[r], q.points_xyz, q.n_points,
-                          (const double*)ln.amp.p + 2 * om_off[r], (const double*)ln.kval.p + om_off[r],
+                          (const double*)ln.amp.p + amp_off[r], (const double*)ln.kval.p + om_off[r],
                           (float2*)q.E_out, (float2*)q.B_out, ch);
         if (st != SC_OK) return st;
     }
@@ -1728,6 +1989,8 @@ sc_status sc_eval_batch(sc_ctx* ctx, const sc_request* reqs, int n_req, sc_eval_
         stats->total_ms = ms;
         stats->field_ms = ctx->ctr.field_ms - field_ms_before;
         stats->launches = (int)(ctx->ctr.launches - launches_before);
+        stats->tables = 0;
+        for (const Table* t : tabs) stats->tables = std::max(stats->tables, (int)t->parts.size());
     }
     return SC_OK;
 }
@@ -1762,8 +2025,8 @@ sc_status sc_eval_fp32_static(sc_ctx* ctx, const sc_mirror_t* m, const sc_incide
     if (!tab)
         return fail(ctx, SC_ERR_INVALID,
                     "node table not resident: run sc_eval once for this mirror and incident first");
-    if (tab->d32_1)
-        return fail(ctx, SC_ERR_INVALID, "a first-order beam needs sc_eval (two node tables)");
+    if (tab->parts.size() > 1)
+        return fail(ctx, SC_ERR_INVALID, "a beam with %zu node tables needs sc_eval", tab->parts.size());
     ctx->tick++;
     void* scratch = nullptr;
     cudaError_t e = sc::static_scratch(ctx->device, &scratch);

@@ -3,7 +3,8 @@
 // field_f64_kernel: the same quadrature of Sec. II Eq. 11 as the FP32 kernel,
 // written the plain way: FP64 throughout, phase R - (z + 2f) + W formed by a
 // direct difference and one sincos per (point, node, omega).  It is both a
-// second parity check and the FP64 GPU baseline.
+// second parity check and the FP64 GPU baseline.  An incident with several
+// node tables runs one launch per table, the later ones adding to E and B.
 //
 // idft: Sec. III.B Eq. 13 for a real field sampled at positive k_n,
 // F(t_m) = 2 dk Re sum_n F_n e^{-i k_n t_m}, as a phasor table
@@ -27,10 +28,9 @@ __global__ void field_f64_kernel(Field64Launch a)
     const double k = a.kval[n];
     const double x = a.pts[3 * pt], y = a.pts[3 * pt + 1], z = a.pts[3 * pt + 2];
     double sE[6] = {0, 0, 0, 0, 0, 0}, sB[6] = {0, 0, 0, 0, 0, 0}, sR[6] = {0, 0, 0, 0, 0, 0};
-    double tE[6] = {0, 0, 0, 0, 0, 0}, tB[6] = {0, 0, 0, 0, 0, 0};  // first-order table
-    for (int pass = 0; pass < 3; ++pass) {
-        const Node64* nodes = pass == 0 ? a.surf : (pass == 1 ? a.rim : a.surf1);
-        const int nn = pass == 0 ? a.n_surf : (pass == 1 ? a.n_rim : a.n_surf1);
+    for (int pass = 0; pass < 2; ++pass) {
+        const Node64* nodes = pass == 0 ? a.surf : a.rim;
+        const int nn = pass == 0 ? a.n_surf : a.n_rim;
         for (int j = 0; j < nn; ++j) {
             const Node64 nd = nodes[j];
             const double dx = nd.px - x, dy = nd.py - y, dz = nd.pz - z;
@@ -47,14 +47,12 @@ __global__ void field_f64_kernel(Field64Launch a)
             const double v[3] = {av * rx, av * ry, av * rz};
             const double u[3] = {ux, uy, uz};
             const double w[3] = {uy * rz - uz * ry, uz * rx - ux * rz, ux * ry - uy * rx};
-            if (pass != 1) {
-                double* e = pass == 0 ? sE : tE;
-                double* bb = pass == 0 ? sB : tB;
+            if (pass == 0) {
                 for (int cc = 0; cc < 3; ++cc) {
-                    e[2 * cc] += u[cc] * qr + v[cc] * zr;
-                    e[2 * cc + 1] += u[cc] * qi + v[cc] * zi;
-                    bb[2 * cc] += w[cc] * zr;
-                    bb[2 * cc + 1] += w[cc] * zi;
+                    sE[2 * cc] += u[cc] * qr + v[cc] * zr;
+                    sE[2 * cc + 1] += u[cc] * qi + v[cc] * zi;
+                    sB[2 * cc] += w[cc] * zr;
+                    sB[2 * cc + 1] += w[cc] * zi;
                 }
             } else {
                 for (int cc = 0; cc < 3; ++cc) {
@@ -66,17 +64,21 @@ __global__ void field_f64_kernel(Field64Launch a)
     }
     const double ar = a.amp[2 * n], ai = a.amp[2 * n + 1], ik = 1.0 / k;
     double2* E = a.E + ((size_t)n * a.n_pts + pt) * 3;
+    // amp (S + (i/k) rim); later table parts add to the earlier ones
     for (int cc = 0; cc < 3; ++cc) {
-        // S + (i/k) rim - (i/k) S1  (the first-order table has no rim nodes)
-        const double er = sE[2 * cc] - ik * sR[2 * cc + 1] + ik * tE[2 * cc + 1];
-        const double ei = sE[2 * cc + 1] + ik * sR[2 * cc] - ik * tE[2 * cc];
-        E[cc] = make_double2(ar * er - ai * ei, ar * ei + ai * er);
+        const double er = sE[2 * cc] - ik * sR[2 * cc + 1];
+        const double ei = sE[2 * cc + 1] + ik * sR[2 * cc];
+        double2 v = make_double2(ar * er - ai * ei, ar * ei + ai * er);
+        if (a.accumulate) v = make_double2(v.x + E[cc].x, v.y + E[cc].y);
+        E[cc] = v;
     }
     if (a.B) {
         double2* B = a.B + ((size_t)n * a.n_pts + pt) * 3;
         for (int cc = 0; cc < 3; ++cc) {
-            const double br = sB[2 * cc] + ik * tB[2 * cc + 1], bi = sB[2 * cc + 1] - ik * tB[2 * cc];
-            B[cc] = make_double2(ar * br - ai * bi, ar * bi + ai * br);
+            const double br = sB[2 * cc], bi = sB[2 * cc + 1];
+            double2 v = make_double2(ar * br - ai * bi, ar * bi + ai * br);
+            if (a.accumulate) v = make_double2(v.x + B[cc].x, v.y + B[cc].y);
+            B[cc] = v;
         }
     }
 }

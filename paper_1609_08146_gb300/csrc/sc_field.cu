@@ -739,41 +739,31 @@ __device__ __forceinline__ void reduce_one(const ReduceLaunch& r, long long idx)
     const int pt = (int)(idx / r.n_omega), n = (int)(idx % r.n_omega);
     const size_t stride = (size_t)r.n_pts * r.n_omega * kAcc;
     const size_t at = ((size_t)pt * r.n_omega + n) * kAcc;
-    double s[kAcc], rim[6];
-    section_sums(r.ws, r.n_splits, stride, at, s, rim);
     const double ik = 1.0 / r.kval[n];
-    // T = S + (i/k) rim: the rim slot's E sum carries the factor i/k of the
-    // line integral
-    double er[3], ei[3], br[3], bi[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        er[c] = s[2 * c] - ik * rim[2 * c + 1];
-        ei[c] = s[2 * c + 1] + ik * rim[2 * c];
-        br[c] = s[6 + 2 * c];
-        bi[c] = s[6 + 2 * c + 1];
-    }
-    if (r.ws1) {
-        // first-order table: + (-i/k) T1, T1 = S1 + (i/k) rim1
-        section_sums(r.ws1, r.n_splits, stride, at, s, rim);
+    double er[3] = {0, 0, 0}, ei[3] = {0, 0, 0}, br[3] = {0, 0, 0}, bi[3] = {0, 0, 0};
+    for (int p = 0; p < r.n_parts; ++p) {
+        double s[kAcc], rim[6];
+        section_sums(r.ws + (size_t)p * (r.n_splits + 1) * stride, r.n_splits, stride, at, s, rim);
+        const double ar = r.amp[p * r.amp_stride + 2 * n], ai = r.amp[p * r.amp_stride + 2 * n + 1];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
+            // T = S + (i/k) rim: the rim slot's E sum carries the factor i/k
+            // of the line integral; the part adds amp_p T
             const double tr = s[2 * c] - ik * rim[2 * c + 1], ti = s[2 * c + 1] + ik * rim[2 * c];
-            er[c] += ik * ti;
-            ei[c] -= ik * tr;
-            br[c] += ik * s[6 + 2 * c + 1];
-            bi[c] -= ik * s[6 + 2 * c];
+            er[c] += ar * tr - ai * ti;
+            ei[c] += ar * ti + ai * tr;
+            const double ur = s[6 + 2 * c], ui = s[6 + 2 * c + 1];
+            br[c] += ar * ur - ai * ui;
+            bi[c] += ar * ui + ai * ur;
         }
     }
-    const double ar = r.amp[2 * n], ai = r.amp[2 * n + 1];
     float2* E = r.E + (size_t)n * r.out_pt_stride_omega + (size_t)pt * 3;
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-        E[c] = make_float2((float)(ar * er[c] - ai * ei[c]), (float)(ar * ei[c] + ai * er[c]));
+    for (int c = 0; c < 3; ++c) E[c] = make_float2((float)er[c], (float)ei[c]);
     if (r.B) {
         float2* B = r.B + (size_t)n * r.out_pt_stride_omega + (size_t)pt * 3;
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            B[c] = make_float2((float)(ar * br[c] - ai * bi[c]), (float)(ar * bi[c] + ai * br[c]));
+        for (int c = 0; c < 3; ++c) B[c] = make_float2((float)br[c], (float)bi[c]);
     }
 }
 

@@ -94,12 +94,13 @@ int launch_field_f32(const FieldLaunch& p, cudaStream_t s);
 // B = a_n S_B, written as float2 into out[n_omega_total][n_pts_total][3]
 // at (omega offset, point offset).
 struct ReduceLaunch {
-    const float2* ws;
-    const float2* ws1 = nullptr;  // partials of the first-order table (same layout), or null:
-                            // the result gains -i/k_n times their sum
+    const float2* ws;       // part 0's partials; part p's follow at p times
+                            // (n_splits + 1) * n_pts * n_omega * kAcc
+    int n_parts = 1;        // node tables summed, result = sum_p amp_p (S_p + (i/k) rim_p)
+    long long amp_stride = 0;  // doubles from one part's amplitudes to the next
     int n_splits;           // surface splits (the rim slot follows)
     int n_pts, n_omega;
-    const double* amp;      // [n_omega][2] of this chunk
+    const double* amp;      // [n_parts][..][2] of this chunk: a_n times the part's weight
     const double* kval;     // [n_omega] k_n of this chunk
     float2* E;              // output base (already offset to the chunk)
     float2* B;              // nullable
@@ -115,11 +116,10 @@ int launch_reduce_batch(const ReduceLaunch* reqs, int n_req, long long total, cu
 struct Field64Launch {
     const Node64* surf; int n_surf;
     const Node64* rim;  int n_rim;
-    const Node64* surf1 = nullptr;       // first-order table (sums times -i/k), or null
-    int n_surf1 = 0;
+    int accumulate = 0;                  // add to E, B instead of storing (later parts)
     const double* pts;  int n_pts;
     const double* kval; int n_omega;     // k_n per omega
-    const double* amp;                   // [n_omega][2]
+    const double* amp;                   // [n_omega][2]: a_n times the part's weight
     double2* E; double2* B;              // [n_omega][n_pts][3]
 };
 int launch_field_f64(const Field64Launch& p, cudaStream_t s);

@@ -66,6 +66,40 @@ def test_first_order_beam_validation():
             lib.sc_incident_free(h)
 
 
+def test_envelope_beam_validation():
+    """Kinds 3 (Laguerre-Gauss) and 4 (caller's envelope) need a band, valid
+    mode indices, a function and a spectrum that needs no beam power."""
+    lib = sc.load()
+    mono = sc.sc_spectrum(0, 1.0, 1.0, 0.1, 3, 1.0, 0, None, None, 0, None)
+    gtime = sc.sc_spectrum(1, 3.0, 1.0, 0.1, 3, 1.0, 0, None, None, 0, None)
+    fn = sc.ENVELOPE_FN(lambda user, n, xyz, k, e: None)
+    fptr = ctypes.cast(fn, ctypes.c_void_p)
+
+    def prof(kind, p=0, l=0, lo=0.8, hi=1.2, f=None, order=0):
+        return sc.sc_profile(kind, 5.0, 4, 0, None, order, p, l, -10.0, f, None, lo, hi, 0.0)
+
+    cases = [
+        (prof(3), 0, mono, sc.SC_OK),
+        (prof(3, 2, 3), 0, gtime, sc.SC_OK),
+        (prof(3, lo=0.0), 0, mono, sc.SC_ERR_INVALID),
+        (prof(3, lo=1.2, hi=1.1), 0, mono, sc.SC_ERR_INVALID),
+        (prof(3, -1), 0, mono, sc.SC_ERR_INVALID),
+        (prof(3, 0, 2), 1, mono, sc.SC_ERR_INVALID),   # radial needs |l| = 1
+        (prof(3, 0, -1), 2, mono, sc.SC_OK),
+        (prof(3, order=1), 0, mono, sc.SC_ERR_INVALID),
+        (prof(4), 0, mono, sc.SC_ERR_INVALID),         # no function
+        (prof(4, f=fptr), 0, mono, sc.SC_OK),
+        (prof(4, f=fptr), 0, gtime, sc.SC_ERR_INVALID),  # no beam power for Eq. 16
+    ]
+    for pr, polk, spec, want in cases:
+        h = ctypes.c_void_p()
+        pol = sc.sc_polarization(polk, 0.0)
+        st = lib.sc_incident(None, ctypes.byref(pr), ctypes.byref(pol), ctypes.byref(spec), ctypes.byref(h))
+        assert st == want, (pr.kind, pr.lg_p, pr.lg_l, polk, want)
+        if st == sc.SC_OK:
+            lib.sc_incident_free(h)
+
+
 def _incident(lib, beam, spec):
     keep = []
     prof = sc.sc_profile(sc.PROFILES[beam["profile"]], beam["w0"], beam.get("sg_order", 4), 0, None)
