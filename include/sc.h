@@ -186,8 +186,10 @@ typedef struct {
  *   azimuthal; |l| = 1).  As z_R -> oo it is the collimated beam above.
  *   Kind 4, the caller's envelope function.  Its spectrum must be SAMPLED
  *   or MONO (Eq. 16 has no beam power for it).
- * The node table holds a Chebyshev expansion of e_perp in k over
- * [2 pi omega_lo, 2 pi omega_hi], sum_m c_m(node) T_m(x(k)), truncated where
+ * The node table holds a Chebyshev expansion in k over [2 pi omega_lo,
+ * 2 pi omega_hi] of e_perp e^{-ik tau(node)}, sum_m c_m(node) T_m(x(k)),
+ * tau being each node's phase slope in k at the band centre (added to the
+ * node's optical path, so a pulse-front tilt costs nothing), truncated where
  * the remaining coefficients sum below fit_tol times the envelope's peak;
  * the real and imaginary parts of each c_m are tables of their own, so a
  * beam costs one field pass per table (see sc_eval_stats.tables).  An

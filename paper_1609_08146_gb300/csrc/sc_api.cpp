@@ -623,10 +623,14 @@ struct HostPart {
 // Kinds 3 and 4: Chebyshev expansion in k of the envelope e_perp over the
 // band [kc - kh, kc + kh], from kCheb samples at the Chebyshev points
 // x_j = cos(pi (j + 1/2) / kCheb): c_m = (2 - [m = 0]) / kCheb sum_j f(x_j)
-// T_m(x_j).  It keeps the first M terms, M the least with sum_{m >= M}
-// max |c_m| <= fit_tol max |f|; the real and imaginary parts of each kept
-// c_m become parts of their own (a part that is zero everywhere is left
-// out).  B~ = (-z) x E~ (order 0).
+// T_m(x_j).  Before the fit each node's phase slope in k at the band centre,
+// tau = d arg(e_perp) / dk from two nearby samples, is taken out of the
+// envelope (f = e_perp e^{-ik tau}) and put into the node's optical path W,
+// where the field kernel applies it exactly as e^{ik W}: what remains varies
+// less with k and needs fewer terms.  The fit keeps the first M terms, M
+// the least with sum_{m >= M} max |c_m| <= fit_tol max |f|; the real and
+// imaginary parts of each kept c_m become parts of their own (a part that
+// is zero everywhere is left out).  B~ = (-z) x E~ (order 0).
 constexpr int kCheb = 24;
 constexpr int kChebMaxTerms = 20;
 
@@ -660,12 +664,8 @@ sc_status build_cheb_parts(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_
     }
     kc = kPi * (in->om_lo + in->om_hi);
     kh = kPi * (in->om_hi - in->om_lo);
-    // coefficients c[m][node][4] (e_x re, im, e_y re, im)
-    std::vector<double> c((size_t)kCheb * n * 4, 0.0), e(4 * n);
-    double peak = 0.0;
-    for (int j = 0; j < kCheb; ++j) {
-        const double tj = kPi * (j + 0.5) / kCheb;
-        const double k = kc + kh * cos(tj);
+    std::vector<double> e(4 * n);
+    auto sample = [&](double k) -> bool {
         if (in->profile == SC_PROFILE_LAGUERRE_GAUSS) {
             for (size_t q = 0; q < n; ++q) lg_envelope(in, k, xyz[3 * q], xyz[3 * q + 1], xyz[3 * q + 2], &e[4 * q]);
         } else {
@@ -673,7 +673,43 @@ sc_status build_cheb_parts(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_
             in->env(in->env_user, (int)n, xyz.data(), k, e.data());
         }
         for (double v : e)
-            if (!std::isfinite(v)) return fail(ctx, SC_ERR_INVALID, "the envelope is not finite on the mirror");
+            if (!std::isfinite(v)) return false;
+        return true;
+    };
+    // per-node phase slope tau at the band centre
+    std::vector<double> tau(n, 0.0);
+    {
+        const double dk = 0.01 * kh;
+        if (!sample(kc - dk)) return fail(ctx, SC_ERR_INVALID, "the envelope is not finite on the mirror");
+        const std::vector<double> em = e;
+        if (!sample(kc + dk)) return fail(ctx, SC_ERR_INVALID, "the envelope is not finite on the mirror");
+        for (size_t q = 0; q < n; ++q) {
+            // arg of sum_c e_c(k + dk) conj(e_c(k - dk))
+            double sr = 0.0, si = 0.0;
+            for (int cpt = 0; cpt < 2; ++cpt) {
+                const double ar = e[4 * q + 2 * cpt], ai = e[4 * q + 2 * cpt + 1];
+                const double br = em[4 * q + 2 * cpt], bi = em[4 * q + 2 * cpt + 1];
+                sr += ar * br + ai * bi;
+                si += ai * br - ar * bi;
+            }
+            if (sr != 0.0 || si != 0.0) tau[q] = atan2(si, sr) / (2.0 * dk);
+        }
+    }
+    // coefficients c[m][node][4] (e_x re, im, e_y re, im) of e_perp e^{-ik tau}
+    std::vector<double> c((size_t)kCheb * n * 4, 0.0);
+    double peak = 0.0;
+    for (int j = 0; j < kCheb; ++j) {
+        const double tj = kPi * (j + 0.5) / kCheb;
+        const double k = kc + kh * cos(tj);
+        if (!sample(k)) return fail(ctx, SC_ERR_INVALID, "the envelope is not finite on the mirror");
+        for (size_t q = 0; q < n; ++q) {
+            const double cr = cos(k * tau[q]), ci = -sin(k * tau[q]);
+            for (int cpt = 0; cpt < 2; ++cpt) {
+                const double ar = e[4 * q + 2 * cpt], ai = e[4 * q + 2 * cpt + 1];
+                e[4 * q + 2 * cpt] = ar * cr - ai * ci;
+                e[4 * q + 2 * cpt + 1] = ar * ci + ai * cr;
+            }
+        }
         for (size_t q = 0; q < 4 * n; q += 2) peak = std::max(peak, std::hypot(e[q], e[q + 1]));
         for (int mm = 0; mm < kCheb; ++mm) {
             const double w = (mm == 0 ? 1.0 : 2.0) / kCheb * cos(mm * tj);
@@ -715,7 +751,7 @@ sc_status build_cheb_parts(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_
                 HostNode nd;
                 nd.px = x; nd.py = y; nd.pz = xyz[3 * q + 2];
                 nd.pn = r * r / (4.0 * f) + f;
-                nd.w = incident_opd(in, r, th, m->r_max);
+                nd.w = incident_opd(in, r, th, m->r_max) + tau[q];
                 if (q < n_surf) {
                     const double wq = gw[q / nt] * dth * r / (2.0 * kPi);
                     nd.jx = -by * wq;  // N x B~ with B~_z = 0, N_z = 1

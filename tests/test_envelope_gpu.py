@@ -98,6 +98,27 @@ def test_spatially_chirped_envelope_parity(ctx):
         assert max(err(E, E0), err(B, B0)) <= tol, (prec, st)
 
 
+def _tilt(xyz, k, alpha=3.0):
+    """Pulse-front tilt: a Gaussian whose phase alpha k x is linear in k."""
+    x, y = xyz[:, 0], xyz[:, 1]
+    e = np.zeros((len(xyz), 2), dtype=np.complex128)
+    e[:, 1] = np.exp(-(x * x + y * y) / 49.0) * np.exp(1j * alpha * k * x)
+    return e
+
+
+def test_pulse_front_tilt_is_one_table(ctx):
+    """A phase linear in k goes into the nodes' optical path before the fit,
+    so a tilt of hundreds of radians across the band costs one table."""
+    om = np.linspace(BAND[0], BAND[1], 7)
+    pts = np.vstack([np.zeros((1, 3)), wl.random_cube(5, 1.5, 8)])
+    cb = oracle.envelope_callback(_tilt)
+    E0, B0 = oracle.field(dict(MIRROR, rim=1), dict(profile="envelope", w0=7.0, env_fn=cb, r_norm=40.0), om, pts)
+    for prec, err, tol in (("fp32", _gate, 1e-5), ("fp64", _rel, 2e-8)):
+        E, B, st = _gpu(ctx, dict(profile="envelope", w0=7.0, envelope=_tilt), om, pts, prec)
+        assert st["tables"] == 1
+        assert max(err(E, E0), err(B, B0)) <= tol, (prec, st)
+
+
 def test_envelope_beams_alone_equal_mixed(ctx):
     reqs = []
     m = ctx.mirror(MIRROR["f"], 0.0, MIRROR["r_max"], 48, 48)
@@ -120,7 +141,8 @@ def test_envelope_errors(ctx):
     inc = ctx.incident(omega_band=BAND, **LG_BEAMS[0])
     with pytest.raises(RuntimeError):  # outside the band of the fit
         ctx.eval(m, inc, [1.3], pts)
-    rough = lambda xyz, k: np.column_stack([np.exp(3j * k * xyz[:, 0]), 0 * xyz[:, 0]])  # noqa: E731
+    # a phase quadratic in k (the linear part is factored out before the fit)
+    rough = lambda xyz, k: np.column_stack([np.exp(3j * k * k * xyz[:, 0]), 0 * xyz[:, 0]])  # noqa: E731
     inc = ctx.incident(omega_band=BAND, profile="envelope", w0=5.0, envelope=rough,
                        spectrum=dict(kind="mono"))
     with pytest.raises(RuntimeError):  # needs far more than 20 terms in k
