@@ -51,6 +51,8 @@ class _Mirror(ctypes.Structure):
         ("z0", ctypes.c_double),
         ("r_min", ctypes.c_double),
         ("r_max", ctypes.c_double),
+        ("c_ell", ctypes.c_double),
+        ("e_ell", ctypes.c_double),
     ]
 
 
@@ -70,6 +72,9 @@ class _Beam(ctypes.Structure):
         ("z_waist", ctypes.c_double),
         ("env_fn", ctypes.c_void_p),
         ("env_user", ctypes.c_void_p),
+        ("dip", ctypes.c_double * 3),
+        ("src", ctypes.c_double * 3),
+        ("phase_ref", ctypes.c_double),
     ]
 
 
@@ -89,7 +94,7 @@ def envelope_callback(fn):
     return ENVELOPE_FN(_cb)
 
 
-PROFILES = {"gauss": 0, "supergauss": 1, "tophat": 2, "laguerre_gauss": 3, "envelope": 4}
+PROFILES = {"gauss": 0, "supergauss": 1, "tophat": 2, "laguerre_gauss": 3, "envelope": 4, "dipole": 5}
 POLS = {"linear": 0, "radial": 1, "azimuthal": 2}
 SPECTRA = {"mono": 0, "gauss_time": 1, "supergauss_lambda": 2, "sampled": 3}
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -130,10 +135,11 @@ def _ptr(a):
 
 def _mirror(m: dict) -> _Mirror:
     return _Mirror(
-        surface={"paraboloid": 0, "flat": 1}[m.get("surface", "paraboloid")],
+        surface={"paraboloid": 0, "flat": 1, "ellipsoid": 2}[m.get("surface", "paraboloid")],
         n_r=int(m["n_r"]), n_theta=int(m["n_theta"]), rim=int(m.get("rim", 1)),
         f=float(m.get("f", 1.0)), z0=float(m.get("z0", 0.0)),
         r_min=float(m.get("r_min", 0.0)), r_max=float(m["r_max"]),
+        c_ell=float(m.get("c", 0.0)), e_ell=float(m.get("e", 0.0)),
     )
 
 
@@ -148,7 +154,17 @@ def _beam(b: dict, keep: list) -> _Beam:
         lg_p=int(b.get("lg_p", 0)), lg_l=int(b.get("lg_l", 0)), z_waist=float(b.get("z_waist", 0.0)),
         env_fn=ctypes.cast(b["env_fn"], ctypes.c_void_p) if b.get("env_fn") is not None else None,
         env_user=None,
+        dip=(ctypes.c_double * 3)(*b.get("dipole", (0.0, 0.0, 0.0))),
+        src=(ctypes.c_double * 3)(*b.get("src", (0.0, 0.0, 0.0))),
+        phase_ref=float(b.get("phase_ref", 0.0)),
     )
+
+
+def dipole_beam(mirror: dict, p=(1.0, 0.0, 0.0)) -> dict:
+    """The dipole of reading R16 at the upper focus F1 = (0, 0, 2e) of an
+    ellipsoidal mirror, phase referred to the path length 2c."""
+    return dict(profile="dipole", dipole=tuple(p), src=(0.0, 0.0, 2.0 * mirror["e"]),
+                phase_ref=2.0 * mirror["c"], w0=1.0)
 
 
 def gauss_legendre(n: int, a: float = -1.0, b: float = 1.0):

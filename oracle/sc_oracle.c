@@ -64,6 +64,20 @@
  *       z_ref)) is dropped, so t = 0 stays the geometric focal arrival.
  *       Profile 4 takes e_perp from a caller's function (measured maps,
  *       spatio-temporal couplings), sampled once per frequency and node.
+ *   R16 NEXT-4, an ellipsoidal mirror and a point source: surface 2 is the
+ *       lower cap of the ellipsoid of revolution with semi-axis c along z
+ *       and focal half-distance e < c, its lower focus F2 at the origin and
+ *       its upper focus F1 at (0, 0, 2e): z = e - c sqrt(1 - r^2/a^2),
+ *       a^2 = c^2 - e^2, vertex at z = -(c - e) (as e -> oo with c - e = f
+ *       fixed it is the paraboloid of focal length f, F1 going to infinity
+ *       above it).  Profile 5 is the exact field of an electric
+ *       dipole p at F1 (time factor exp(-i omega t), c = 1),
+ *         E = e^{ikr} [k^2 (n x p) x n / r + (3 n (n.p) - p)(1/r^3 - ik/r^2)],
+ *         B = e^{ikr} (n x p) (k^2/r + ik/r^2),
+ *       r = |P - F1|, n = (P - F1)/r, times exp(-ik 2c) (every ray F1 ->
+ *       mirror -> F2 has length 2c, so t = 0 is the focal arrival at F2).
+ *       Collimated beams on the ellipsoid use z_ref = -2 z_vertex = 2(c - e),
+ *       as z_ref = 2f for the paraboloid.
  *   R14 first-order incident field (beam order 1): the collimated beam of R4
  *       is not divergence-free at O(eps), eps = lambda / (pi w0) (Sec. III.A).
  *       Order 1 adds the longitudinal terms that make div E = div B = 0 and
@@ -102,6 +116,7 @@ typedef struct {
     double z0;        /* plane height of the flat test mirror                  */
     double r_min;
     double r_max;
+    double c_ell, e_ell; /* ellipsoid (surface 2): semi-axis along z, focal half-distance */
 } or_mirror;
 
 typedef struct {
@@ -119,6 +134,9 @@ typedef struct {
     /* profile 4: fn(user, n, xyz[n][3], k, e[n][2][2]) writes e_perp (re, im) */
     void (*env_fn)(void* user, int n, const double* xyz, double k, double* e);
     void* env_user;
+    double dip[3];    /* profile 5: dipole moment and position, and the path */
+    double src[3];    /* length removed from its phase (R16)                  */
+    double phase_ref;
 } or_beam;
 
 /* ------------------------------------------------------------------------ */
@@ -254,6 +272,26 @@ static double beam_opd(const or_beam* bm, double x, double y)
     return w;
 }
 
+/* Exact field of the dipole of profile 5 at (x, y, z) (R16), including its
+ * phase exp(ik (r - phase_ref)) and the extra phase exp(ik extra). */
+static void dipole_field(const or_beam* bm, double k, double x, double y, double z, double extra,
+                         cplx E[3], cplx B[3])
+{
+    const double d[3] = {x - bm->src[0], y - bm->src[1], z - bm->src[2]};
+    const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const double n[3] = {d[0] / r, d[1] / r, d[2] / r};
+    const double* p = bm->dip;
+    const double np = n[0] * p[0] + n[1] * p[1] + n[2] * p[2];
+    const double nxp[3] = {n[1] * p[2] - n[2] * p[1], n[2] * p[0] - n[0] * p[2], n[0] * p[1] - n[1] * p[0]};
+    const cplx ph = cexp(I * k * (r - bm->phase_ref + extra));
+    const cplx near = 1.0 / (r * r * r) - I * k / (r * r);
+    for (int c = 0; c < 3; ++c) {
+        const double far = p[c] - n[c] * np; /* (n x p) x n */
+        E[c] = ph * (k * k * far / r + (3.0 * n[c] * np - p[c]) * near);
+        B[c] = ph * nxp[c] * (k * k / r + I * k / (r * r));
+    }
+}
+
 /* generalised Laguerre polynomial L_p^a(x) by its three-term recurrence */
 static double laguerre(int p, int a, double x)
 {
@@ -331,7 +369,7 @@ static void longitudinal(const or_beam* bm, double k, double x, double y, cplx* 
  * trapezoid quadrature in rho on a fine grid -- deliberately numerical. */
 double or_beam_power(const or_beam* bm)
 {
-    if (bm->profile == 4) return -1.0; /* a caller's envelope has no defined power */
+    if (bm->profile >= 4) return -1.0; /* a caller's envelope or a dipole: no beam power */
     double rmax;
     if (bm->profile == 2) rmax = bm->w0;
     else rmax = 12.0 * bm->w0;
@@ -360,19 +398,30 @@ double or_beam_power(const or_beam* bm)
 
 static double surf_z(const or_mirror* m, double r)
 {
+    if (m->surface == 2) {
+        const double a2 = m->c_ell * m->c_ell - m->e_ell * m->e_ell;
+        return m->e_ell - m->c_ell * sqrt(1.0 - r * r / a2);
+    }
     return (m->surface == 0) ? (r * r / (4.0 * m->f) - m->f) : m->z0;
 }
 
 /* reference of the incident phase: E_inc ~ exp(-ik(z + z_ref)) */
 static double surf_zref(const or_mirror* m)
 {
+    if (m->surface == 2) return 2.0 * (m->c_ell - m->e_ell); /* -2 z_vertex */
     return (m->surface == 0) ? 2.0 * m->f : -m->z0;
 }
 
 /* unnormalised normal (-dz/dx, -dz/dy, 1); its length is the area factor */
 static void surf_normal(const or_mirror* m, double x, double y, double nvec[3])
 {
-    if (m->surface == 0) {
+    if (m->surface == 2) {
+        /* dz/dx = c x / (a^2 sqrt(1 - r^2/a^2)) */
+        const double a2 = m->c_ell * m->c_ell - m->e_ell * m->e_ell;
+        const double s = m->c_ell / (a2 * sqrt(1.0 - (x * x + y * y) / a2));
+        nvec[0] = -x * s;
+        nvec[1] = -y * s;
+    } else if (m->surface == 0) {
         nvec[0] = -x / (2.0 * m->f);
         nvec[1] = -y / (2.0 * m->f);
     } else {
@@ -447,6 +496,7 @@ static void field_at(const or_mirror* m, const or_beam* bm, int form, double k,
                 Einc[2] = ez * pp;
                 Binc[2] = bz * pp;
             }
+            if (bm->profile == 5) dipole_field(bm, k, x, y, z, R, Einc, Binc);
             cplx nh[3] = {nhat[0], nhat[1], nhat[2]};
             cplx J[3];
             ccross(nh, Binc, J); /* n x B_inc */
@@ -510,6 +560,10 @@ static void field_at(const or_mirror* m, const or_beam* bm, int form, double k,
                     longitudinal(bm, k, x, y, &ez, &bz);
                     Binc[2] = bz * cexp(I * k * (R - (z + zref)));
                 }
+                if (bm->profile == 5) {
+                    cplx Ed[3];
+                    dipole_field(bm, k, x, y, z, R, Ed, Binc);
+                }
                 cplx t1[3], t2[3];
                 ccross(nh, Binc, t1);
                 ccross(nh, t1, t2); /* n x (n x B_inc) */
@@ -565,6 +619,7 @@ int or_incident(const or_beam* bm, double zref, int n_omega, const double* omega
             beam_field(bm, x, y, es);
             cplx ph = cexp(I * k * (beam_opd(bm, x, y) - (z + zref)));
             cplx E[3] = {es[0] * ph, es[1] * ph, 0.0}, B[3] = {es[1] * ph, -es[0] * ph, 0.0};
+            if (bm->profile == 5) dipole_field(bm, k, x, y, z, 0.0, E, B);
             if (bm->order >= 1) {
                 cplx ez, bz;
                 longitudinal(bm, k, x, y, &ez, &bz);
@@ -597,6 +652,9 @@ int or_field(const or_mirror* m, const or_beam* bm, int form, int n_omega, const
 {
     if (m->n_r < 1 || m->n_theta < 1 || m->r_max <= m->r_min || m->r_min < 0.0) return 1;
     if (m->surface == 0 && m->f <= 0.0) return 1;
+    if (m->surface == 2 && !(m->e_ell > 0.0 && m->e_ell < m->c_ell &&
+                             m->r_max * m->r_max < m->c_ell * m->c_ell - m->e_ell * m->e_ell))
+        return 1;
     if (bm->order >= 1 && bm->profile >= 2) return 1; /* needs a smooth real profile (R14) */
     if (bm->profile == 4 && !bm->env_fn) return 1;
     double* gl_r = (double*)malloc(sizeof(double) * m->n_r);
@@ -606,7 +664,7 @@ int or_field(const or_mirror* m, const or_beam* bm, int form, int n_omega, const
      * on this thread (a caller's function is not called from worker threads) */
     const long n_s = (long)m->n_r * m->n_theta, n_rim = 2L * m->n_theta, n_nd = n_s + n_rim;
     cplx* env = NULL;
-    if (bm->profile >= 3) {
+    if (bm->profile == 3 || bm->profile == 4) {
         env = (cplx*)malloc(sizeof(cplx) * 2 * n_nd * n_omega);
         double* xyz = (double*)malloc(sizeof(double) * 3 * n_nd);
         double* e = (double*)malloc(sizeof(double) * 4 * n_nd);

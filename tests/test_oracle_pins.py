@@ -668,3 +668,69 @@ def test_faraday_holds_for_a_laguerre_gauss_beam():
     m = dict(f=f, r_max=16.0, n_r=48, n_theta=48, rim=1)
     E, B, cE, cB, dE = _curl(m, _lg("linear", 1, 1, 3.0, z_waist=-6.0), om, [0.31, -0.22, 0.17], 2e-3)
     assert np.linalg.norm(cE - 1j * k * B) / np.linalg.norm(1j * k * B) < 1e-7
+
+
+# --------------------------------------------------------------------------
+# Ellipsoidal mirror and a dipole at its upper focus (reading R16)
+
+ELLIPSOID = dict(surface="ellipsoid", c=14.0, e=6.0, r_max=12.0, n_r=96, n_theta=96, rim=1)  # f = c - e = 8
+
+
+@pytest.mark.parametrize("p", [(1.0, 0.0, 0.0), (0.0, 0.0, 1.0), (0.3, 0.5, 0.8)])
+def test_dipole_field_obeys_maxwell(p):
+    """The dipole field of R16 is an exact Maxwell solution: div E = div B = 0,
+    curl E = ik B and curl B = -ik E to the finite-difference error."""
+    r = _incident_residuals(oracle.dipole_beam(ELLIPSOID, p), 1.1, [2.0, -1.5, 0.5], h=1e-2)
+    assert max(r) < 2e-6
+
+
+def test_dipole_far_field_is_transverse():
+    """Far from F1: E -> k^2 (n x p) x n e^{ikr}/r and B -> n x E."""
+    b = oracle.dipole_beam(ELLIPSOID, (0.2, -0.4, 0.9))
+    k = K0 * 1.0
+    n = np.array([0.6, 0.0, -0.8])
+    P = np.array(b["src"]) + 4000.0 * n
+    E, B = oracle.incident(b, [1.0], P[None, :], zref=0.0)
+    p = np.array(b["dipole"])
+    far = k * k * np.cross(np.cross(n, p), n) / 4000.0 * np.exp(1j * k * (4000.0 - b["phase_ref"]))
+    assert np.max(np.abs(E[0, 0] - far)) < 2e-3 * np.max(np.abs(far))
+    assert np.max(np.abs(B[0, 0] - np.cross(n, E[0, 0]))) < 2e-3 * np.max(np.abs(far))
+
+
+@pytest.mark.parametrize("p", [(1.0, 0.0, 0.0), (0.0, 0.0, 1.0)])
+def test_ellipsoid_stokes_form_equals_double_gradient_form_for_a_dipole(p):
+    """Eq. 11 = Eq. 10 for a Maxwell incident field: on the ellipsoid this
+    pins its normal, area element and rim orientation (R16)."""
+    pts = np.array([[0.2, 0.1, 0.0], [-0.3, 0.25, 0.4], [0.0, 0.0, 0.0]])
+    b = oracle.dipole_beam(ELLIPSOID, p)
+    E1, B1 = oracle.field(ELLIPSOID, b, [0.9], pts, form="stokes")
+    E2, B2 = oracle.field(ELLIPSOID, b, [0.9], pts, form="dyadic")
+    assert np.max(np.abs(E1 - E2)) < 1e-11 * np.max(np.abs(E1))
+    assert np.max(np.abs(B1 - B2)) <= 1e-14 * np.max(np.abs(B1))
+    # by symmetry an axial or transverse dipole focuses along itself at F2
+    j = int(np.argmax(np.abs(p)))
+    assert np.max(np.abs(np.delete(E1[0, 2], j))) < 1e-10 * abs(E1[0, 2, j])
+
+
+def test_faraday_holds_on_the_ellipsoid():
+    om = 1.1
+    k = K0 * om
+    E, B, cE, cB, dE = _curl(ELLIPSOID, dict(profile="gauss", pol="linear", w0=5.0, r_norm=12.0), om,
+                             [0.31, -0.22, 0.17], 2e-3)
+    assert np.linalg.norm(cE - 1j * k * B) / np.linalg.norm(k * B) < 1e-7
+
+
+def test_ellipsoid_tends_to_the_paraboloid():
+    """With c - e = f fixed and e -> oo the ellipsoid (and z_ref = 2(c - e))
+    becomes the paraboloid of focal length f: the collimated beam's focal
+    field converges as 1/e."""
+    f = 8.0
+    pts = np.array([[0.2, 0.1, 0.0], [-0.3, 0.25, 0.4]])
+    beam = dict(profile="gauss", pol="linear", w0=6.0, r_norm=16.0)
+    E0, _ = oracle.field(dict(f=f, r_max=16.0, n_r=64, n_theta=64, rim=1), beam, [1.0], pts)
+    d = []
+    for e in (1e4, 1e5, 1e6):
+        m = dict(surface="ellipsoid", c=e + f, e=e, r_max=16.0, n_r=64, n_theta=64, rim=1)
+        E, _ = oracle.field(m, beam, [1.0], pts)
+        d.append(np.max(np.abs(E - E0)) / np.max(np.abs(E0)))
+    assert d[0] < 1e-2 and 8.0 < d[0] / d[1] < 12.0 and 8.0 < d[1] / d[2] < 12.0
