@@ -99,6 +99,25 @@ typedef struct {
  * n_theta < 1 or an unknown radial_kind.  The handle is host-side only;
  * device tables are built lazily per (mirror, incident) pair by sc_eval.
  */
+/*
+ * Ellipsoidal mirror (beyond paraboloids; Sec. III.C names the ellipsoid as
+ * a mirror where the paraboloid's phase cancellation fails): the lower cap
+ * z = e - c sqrt(1 - r^2/a^2), a^2 = c^2 - e^2, of the ellipsoid of
+ * revolution with semi-axis c along z and focal half-distance e, cut to
+ * r_min <= r <= r_max < a.  Its lower focus F2 is the origin, its upper
+ * focus F1 = (0, 0, 2e), its vertex at -(c - e); as e -> oo with c - e = f
+ * it becomes the paraboloid of focal length f.
+ *   Every ray from F1 reaches F2 over the path 2c, so a point source at F1
+ *   (SC_PROFILE_DIPOLE) keeps the compensated phase of the FP32 path
+ *   exact.  A collimated beam (kinds 0-4, phase reference z_ref =
+ *   2(c - e)) does not focus on the origin; its phase is exact only in
+ *   FP64, and the SC_FP32_COMP path rejects it.
+ * Errors: SC_ERR_INVALID when not 0 < e < c, r_min < 0, r_min >= r_max,
+ * r_max >= a, or a quadrature as for sc_mirror is invalid.
+ */
+sc_status sc_mirror_ellipsoid(sc_ctx* ctx, double c, double e, double r_min, double r_max,
+                              const sc_quadrature* q, sc_mirror_t** out);
+
 sc_status sc_mirror(sc_ctx* ctx, double f, double r_min, double r_max, const sc_quadrature* q,
                     sc_mirror_t** out);
 void sc_mirror_free(sc_mirror_t* m);
@@ -111,7 +130,8 @@ enum {
     SC_PROFILE_SUPERGAUSS = 1,
     SC_PROFILE_TOPHAT = 2,
     SC_PROFILE_LAGUERRE_GAUSS = 3, /* paraxial LG mode with finite Rayleigh range */
-    SC_PROFILE_ENVELOPE = 4        /* the caller's envelope function             */
+    SC_PROFILE_ENVELOPE = 4,       /* the caller's envelope function             */
+    SC_PROFILE_DIPOLE = 5          /* electric dipole at an ellipsoid's focus F1 */
 };
 
 /*
@@ -171,7 +191,19 @@ typedef struct {
     double omega_lo, omega_hi;  /* band of every omega later evaluated (kinds 3, 4) */
     double fit_tol;           /* truncation tolerance of the fit in k, relative to  */
                               /* the envelope's peak (<= 0: 1e-8)                   */
+    double dipole[3];         /* kind 5: the dipole moment p                        */
 } sc_profile;
+
+/*
+ * Kind 5, the exact field of an electric dipole p at the upper focus F1 of
+ * an ellipsoidal mirror (time factor e^{-i omega t}, c = 1):
+ *   E = e^{ikr} [k^2 (n x p) x n / r + (3 n (n.p) - p)(1/r^3 - ik/r^2)],
+ *   B = e^{ikr} (n x p)(k^2/r + ik/r^2),   r = |P - F1|, n = (P - F1)/r,
+ * times e^{-ik 2c} (t = 0 is the focal arrival at F2).  Its k-dependence
+ * is sum_m (ik)^m (E_m, B_m), m = 0, 1, 2: three node tables.  It needs an
+ * ellipsoidal mirror and a SAMPLED or MONO spectrum (Eq. 16 has no beam
+ * power for it); order 0 only.
+ */
 
 /*
  * Kinds 3 and 4: E_inc = e_perp(x, y, z; k) e^{-ik(z + 2f)} e^{ikW}, B_inc =
@@ -229,7 +261,8 @@ typedef struct {
 
 /* Copy the description of an incident beam.  Errors: SC_ERR_INVALID
  * (unknown kind, w0 <= 0, sg_order < 1, n_zernike outside 0..64, order not
- * 0 or 1, order 1 with a top-hat or kinds 3-4, lg_p < 0, |lg_l| != 1 for a
+ * 0 or 1, order 1 with a top-hat or kinds 3-5, a zero dipole (kind 5), kind
+ * 5 with a GAUSS_TIME or SUPERGAUSS_LAMBDA spectrum, lg_p < 0, |lg_l| != 1 for a
  * radial or azimuthal kind 3, kind 4 without a function, kinds 3-4 without
  * 0 < omega_lo < omega_hi, kind 4 with a GAUSS_TIME or SUPERGAUSS_LAMBDA
  * spectrum, a spectrum with non-positive width or lambda_c, SAMPLED with

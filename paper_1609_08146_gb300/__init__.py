@@ -27,7 +27,7 @@ __all__ = ["load", "ScError", "Context", "Mirror", "Incident"]
 SC_OK, SC_ERR_INVALID, SC_ERR_OOM, SC_ERR_CUDA, SC_ERR_TIMEOUT = 0, 1, 2, 3, 4
 SC_ERR_BUSY, SC_ERR_CANCELLED, SC_ERR_NOT_FOUND = 5, 6, 7
 SC_FP32_COMP, SC_FP64 = 0, 1
-PROFILES = {"gauss": 0, "supergauss": 1, "tophat": 2, "laguerre_gauss": 3, "envelope": 4}
+PROFILES = {"gauss": 0, "supergauss": 1, "tophat": 2, "laguerre_gauss": 3, "envelope": 4, "dipole": 5}
 POLS = {"linear": 0, "radial": 1, "azimuthal": 2}
 SPECTRA = {"mono": 0, "gauss_time": 1, "supergauss_lambda": 2, "sampled": 3}
 SC_OPT_TIME_FIELD, SC_OPT_NODES_PER_SPLIT, SC_OPT_WORKSPACE_CAP, SC_OPT_FLUSH_NODES = 1, 2, 3, 4
@@ -47,7 +47,8 @@ class sc_profile(ctypes.Structure):
                 ("n_zernike", ctypes.c_int), ("zernike_noll_waves", _DP), ("order", ctypes.c_int),
                 ("lg_p", ctypes.c_int), ("lg_l", ctypes.c_int), ("z_waist", ctypes.c_double),
                 ("envelope", ctypes.c_void_p), ("envelope_user", ctypes.c_void_p),
-                ("omega_lo", ctypes.c_double), ("omega_hi", ctypes.c_double), ("fit_tol", ctypes.c_double)]
+                ("omega_lo", ctypes.c_double), ("omega_hi", ctypes.c_double), ("fit_tol", ctypes.c_double),
+                ("dipole", ctypes.c_double * 3)]
 
 
 # sc_envelope_fn: (user, n, xyz[n][3], k, e[n][2][2])
@@ -89,6 +90,8 @@ SIGNATURES = {
     "sc_last_error": (ctypes.c_char_p, [_VP]),
     "sc_mirror": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                  ctypes.POINTER(sc_quadrature), ctypes.POINTER(_VP)]),
+    "sc_mirror_ellipsoid": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.POINTER(sc_quadrature), ctypes.POINTER(_VP)]),
     "sc_mirror_free": (None, [_VP]),
     "sc_incident": (ctypes.c_int, [_VP, ctypes.POINTER(sc_profile), ctypes.POINTER(sc_polarization),
                                    ctypes.POINTER(sc_spectrum), ctypes.POINTER(_VP)]),
@@ -157,12 +160,19 @@ def _addr(x):
 
 
 class Mirror:
-    def __init__(self, ctx, f, r_min, r_max, n_r, n_theta, rim=True):
+    def __init__(self, ctx, f, r_min, r_max, n_r, n_theta, rim=True, ellipsoid=None):
+        """Paraboloid of focal length f, or with ellipsoid=(c, e) the ellipsoidal
+        cap of semi-axis c and focal half-distance e (f is then c - e)."""
         self._lib = ctx._lib
         q = sc_quadrature(0, int(n_r), int(n_theta), 1 if rim else 0)
         h = _VP()
-        ctx._check(self._lib.sc_mirror(ctx._h, float(f), float(r_min), float(r_max), ctypes.byref(q),
-                                       ctypes.byref(h)))
+        if ellipsoid is None:
+            ctx._check(self._lib.sc_mirror(ctx._h, float(f), float(r_min), float(r_max), ctypes.byref(q),
+                                           ctypes.byref(h)))
+        else:
+            c, e = ellipsoid
+            ctx._check(self._lib.sc_mirror_ellipsoid(ctx._h, float(c), float(e), float(r_min), float(r_max),
+                                                     ctypes.byref(q), ctypes.byref(h)))
         self._h = h
         self.f, self.r_min, self.r_max, self.n_r, self.n_theta, self.rim = f, r_min, r_max, n_r, n_theta, rim
 
@@ -179,7 +189,7 @@ class Mirror:
 class Incident:
     def __init__(self, ctx, profile="gauss", w0=1.0, sg_order=4, zernike=(), pol="linear",
                  pol_angle=0.0, spectrum=None, order=0, lg_p=0, lg_l=0, z_waist=0.0,
-                 omega_band=(0.0, 0.0), fit_tol=0.0, envelope=None):
+                 omega_band=(0.0, 0.0), fit_tol=0.0, envelope=None, dipole=(0.0, 0.0, 0.0)):
         """profile "laguerre_gauss" (lg_p, lg_l, z_waist) or "envelope" (envelope:
         a function (xyz [n, 3], k) -> e_perp [n, 2] complex) need omega_band =
         (lo, hi) covering every omega evaluated later."""
@@ -198,7 +208,8 @@ class Incident:
         prof = sc_profile(PROFILES[profile], float(w0), int(sg_order), int(z.size),
                           _dptr(z) if z.size else None, int(order), int(lg_p), int(lg_l), float(z_waist),
                           ctypes.cast(self._cb, ctypes.c_void_p) if self._cb else None, None,
-                          float(omega_band[0]), float(omega_band[1]), float(fit_tol))
+                          float(omega_band[0]), float(omega_band[1]), float(fit_tol),
+                          (ctypes.c_double * 3)(*[float(v) for v in dipole]))
         pl = sc_polarization(POLS[pol], float(pol_angle))
         kind = SPECTRA[spectrum.get("kind", "mono")]
         om = amp = None
@@ -257,6 +268,9 @@ class Context:
 
     def mirror(self, f, r_min, r_max, n_r, n_theta, rim=True) -> Mirror:
         return Mirror(self, f, r_min, r_max, n_r, n_theta, rim)
+
+    def ellipsoid(self, c, e, r_min, r_max, n_r, n_theta, rim=True) -> Mirror:
+        return Mirror(self, c - e, r_min, r_max, n_r, n_theta, rim, ellipsoid=(c, e))
 
     def incident(self, **kw) -> Incident:
         return Incident(self, **kw)

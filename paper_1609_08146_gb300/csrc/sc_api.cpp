@@ -41,6 +41,8 @@ struct sc_mirror_t {
     uint64_t id;
     double f, r_min, r_max;
     sc_quadrature q;
+    int surface = 0;        // 0 paraboloid, 2 ellipsoid (semi-axis c, focal half-distance e)
+    double c = 0.0, e = 0.0;
 };
 
 struct sc_incident_t {
@@ -52,6 +54,7 @@ struct sc_incident_t {
     sc_envelope_fn env = nullptr;   // caller's envelope (profile 4)
     void* env_user = nullptr;
     double om_lo = 0.0, om_hi = 0.0, fit_tol = 1e-8;  // band and tolerance of the k fit
+    double dip[3] = {0.0, 0.0, 0.0};                  // dipole moment (profile 5)
     double w0, angle;
     std::vector<double> zern;
     int spec_kind;
@@ -71,8 +74,9 @@ struct DevBuf {
 // sums enter the result with a per-omega complex weight w_p(omega_n):
 //   PART_ONE 1,  PART_INV_K -i/k_n (the 1/k longitudinal terms of order 1),
 //   PART_CHEB_RE T_m(x_n),  PART_CHEB_IM i T_m(x_n)  (x_n = (k_n - kc) / kh,
-//   the Chebyshev expansion in k of a k-dependent envelope).
-enum { PART_ONE = 0, PART_INV_K = 1, PART_CHEB_RE = 2, PART_CHEB_IM = 3 };
+//   the Chebyshev expansion in k of a k-dependent envelope),
+//   PART_IK_POW (i k_n)^m (the terms of the dipole field).
+enum { PART_ONE = 0, PART_INV_K = 1, PART_CHEB_RE = 2, PART_CHEB_IM = 3, PART_IK_POW = 4 };
 
 struct TablePart {
     int kind = PART_ONE, m = 0;
@@ -90,6 +94,8 @@ struct Table {
     int n_surf = 0, n_rim = 0;
     std::vector<TablePart> parts;
     double kc = 0.0, kh = 1.0;     // Chebyshev band in k of the CHEB parts
+    bool fp32_ok = true;           // the incident wavefront focuses on the origin, so the
+                                   // compensated FP32 phase is exact (else FP64 only)
     size_t bytes = 0;
     uint64_t last_use = 0;
     int inflight = 0;              // serving batches on the GPU that read this table
@@ -515,6 +521,35 @@ sc_status spectrum_amps(sc_ctx* ctx, const sc_incident_t* in, const double* om, 
 }
 
 // ------------------------------------------------------------------------
+// Mirror surfaces of revolution z = F(r), focus (F2) at the origin.
+
+struct SurfPt {
+    double z, dzdr;  // F(r), F'(r): n dS = (-F' cos, -F' sin, 1) r dr dtheta
+    double pn;       // |P|, the distance to the focus
+    double extra;    // optical path added to W so that the kernel's phase
+                     // R - |P| + W equals R - (z + z_ref) + W (collimated beams)
+};
+
+SurfPt surf_at(const sc_mirror_t* m, double r)
+{
+    SurfPt p;
+    if (m->surface == 2) {
+        const double a2 = m->c * m->c - m->e * m->e, s = sqrt(1.0 - r * r / a2);
+        p.z = m->e - m->c * s;
+        p.dzdr = m->c * r / (a2 * s);
+        p.pn = sqrt(r * r + p.z * p.z);
+        p.extra = p.pn - (p.z + 2.0 * (m->c - m->e));  // z_ref = -2 z_vertex
+    } else {
+        // |P| = z + 2f on the paraboloid: the extra path vanishes identically
+        p.z = r * r / (4.0 * m->f) - m->f;
+        p.dzdr = r / (2.0 * m->f);
+        p.pn = r * r / (4.0 * m->f) + m->f;
+        p.extra = 0.0;
+    }
+    return p;
+}
+
+// ------------------------------------------------------------------------
 // Node tables (FP64 on the host; A1 of the hot path).
 
 struct HostNode {
@@ -556,17 +591,18 @@ void build_nodes(const sc_mirror_t* m, const sc_incident_t* in, std::vector<Host
     if (first) surf1.reserve((size_t)nr * nt);
     for (int i = 0; i < nr; ++i) {
         const double r = gr[i];
+        const SurfPt sp = surf_at(m, r);
         for (int l = 0; l < nt; ++l) {
             const double th = l * dth;
-            const double x = r * cos(th), y = r * sin(th), z = r * r / (4.0 * f) - f;
-            const double Nx = -x / (2.0 * f), Ny = -y / (2.0 * f), Nz = 1.0;
+            const double x = r * cos(th), y = r * sin(th), z = sp.z;
+            const double Nx = -sp.dzdr * cos(th), Ny = -sp.dzdr * sin(th), Nz = 1.0;
             double e[3], bv[3];
             fields(r, th, e, bv);
             const double wq = gw[i] * dth * r / (2.0 * kPi);
             HostNode nd;
             nd.px = x; nd.py = y; nd.pz = z;
-            nd.pn = r * r / (4.0 * f) + f;
-            nd.w = incident_opd(in, r, th, m->r_max);
+            nd.pn = sp.pn;
+            nd.w = incident_opd(in, r, th, m->r_max) + sp.extra;
             // J = N x B~, rho = N . E~
             nd.jx = (Ny * bv[2] - Nz * bv[1]) * wq;
             nd.jy = (Nz * bv[0] - Nx * bv[2]) * wq;
@@ -591,22 +627,23 @@ void build_nodes(const sc_mirror_t* m, const sc_incident_t* in, std::vector<Host
         const double r = edge == 0 ? m->r_max : m->r_min;
         const double sgn = edge == 0 ? 1.0 : -1.0;  // outward conormal of the surface
         if (r <= 0.0) continue;
-        const double nlen2 = 1.0 + r * r / (4.0 * f * f);
+        const SurfPt sp = surf_at(m, r);
+        const double nlen2 = 1.0 + sp.dzdr * sp.dzdr;
         for (int l = 0; l < nt; ++l) {
             const double th = l * dth;
             const double c = cos(th), s = sin(th);
-            const double x = r * c, y = r * s, z = r * r / (4.0 * f) - f;
-            const double Nx = -x / (2.0 * f), Ny = -y / (2.0 * f);
+            const double x = r * c, y = r * s, z = sp.z;
+            const double Nx = -sp.dzdr * c, Ny = -sp.dzdr * s;
             double e[3], bv[3];
             fields(r, th, e, bv);
             // N x B~ (N_z = 1)
             const double jx = Ny * bv[2] - bv[1], jy = bv[0] - Nx * bv[2], jz = Nx * bv[1] - Ny * bv[0];
-            // q = (J . m^) dl with J = (N x B~)/|N|, m^ = sgn (c, s, r/2f)/|N|, dl = r dth
-            const double q = sgn * (jx * c + jy * s + jz * r / (2.0 * f)) / nlen2 * r * dth;
+            // q = (J . m^) dl with J = (N x B~)/|N|, m^ = sgn (c, s, F')/|N|, dl = r dth
+            const double q = sgn * (jx * c + jy * s + jz * sp.dzdr) / nlen2 * r * dth;
             HostNode nd;
             nd.px = x; nd.py = y; nd.pz = z;
-            nd.pn = r * r / (4.0 * f) + f;
-            nd.w = incident_opd(in, r, th, m->r_max);
+            nd.pn = sp.pn;
+            nd.w = incident_opd(in, r, th, m->r_max) + sp.extra;
             nd.jx = nd.jy = nd.jz = 0.0;
             nd.rho = q / (2.0 * kPi);
             rim.push_back(nd);
@@ -657,10 +694,12 @@ sc_status build_cheb_parts(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_
         }
     const size_t n = pos.size();
     std::vector<double> xyz(3 * n);
+    std::vector<SurfPt> sp(n);
     for (size_t j = 0; j < n; ++j) {
+        sp[j] = surf_at(m, pos[j].r);
         xyz[3 * j] = pos[j].r * cos(pos[j].th);
         xyz[3 * j + 1] = pos[j].r * sin(pos[j].th);
-        xyz[3 * j + 2] = pos[j].r * pos[j].r / (4.0 * f) - f;
+        xyz[3 * j + 2] = sp[j].z;
     }
     kc = kPi * (in->om_lo + in->om_hi);
     kh = kPi * (in->om_hi - in->om_lo);
@@ -747,11 +786,11 @@ sc_status build_cheb_parts(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_
                 const double bx = ey, by = -ex;  // B~ = (-z) x E~
                 const double r = pos[q].r, th = pos[q].th;
                 const double x = xyz[3 * q], y = xyz[3 * q + 1];
-                const double Nx = -x / (2.0 * f), Ny = -y / (2.0 * f);
+                const double Nx = -sp[q].dzdr * cos(th), Ny = -sp[q].dzdr * sin(th);
                 HostNode nd;
                 nd.px = x; nd.py = y; nd.pz = xyz[3 * q + 2];
-                nd.pn = r * r / (4.0 * f) + f;
-                nd.w = incident_opd(in, r, th, m->r_max) + tau[q];
+                nd.pn = sp[q].pn;
+                nd.w = incident_opd(in, r, th, m->r_max) + tau[q] + sp[q].extra;
                 if (q < n_surf) {
                     const double wq = gw[q / nt] * dth * r / (2.0 * kPi);
                     nd.jx = -by * wq;  // N x B~ with B~_z = 0, N_z = 1
@@ -761,9 +800,9 @@ sc_status build_cheb_parts(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_
                     hp.surf.push_back(nd);
                 } else {
                     const double sgn = pos[q].edge == 0 ? 1.0 : -1.0;
-                    const double nlen2 = 1.0 + r * r / (4.0 * f * f);
+                    const double nlen2 = 1.0 + sp[q].dzdr * sp[q].dzdr;
                     const double jx = -by, jy = bx, jz = Nx * by - Ny * bx;
-                    const double qq = sgn * (jx * cos(th) + jy * sin(th) + jz * r / (2.0 * f)) / nlen2 * r * dth;
+                    const double qq = sgn * (jx * cos(th) + jy * sin(th) + jz * sp[q].dzdr) / nlen2 * r * dth;
                     nd.jx = nd.jy = nd.jz = 0.0;
                     nd.rho = qq / (2.0 * kPi);
                     hp.rim.push_back(nd);
@@ -807,6 +846,97 @@ void free_table(sc_ctx* ctx, Table& t)
 
 // Look up or build the table of (m, in).  Public calls advance ctx->tick once;
 // tables touched by the current call carry that tick and are never evicted by it.
+// Kind 5 on the ellipsoid (reading R16): the dipole field at the node,
+// without its phase e^{ik(r - 2c)} = e^{-ik|P|} (r + |P| = 2c on the
+// ellipsoid, so the kernel's compensated phase R - |P| is the whole phase),
+// is sum_m (ik)^m (E_m, B_m):
+//   m = 0: E = A2 / r^3, B = 0;  m = 1: E = -A2 / r^2, B = (n x p) / r^2;
+//   m = 2: E = -(n x p) x n / r, B = -(n x p) / r;  A2 = 3 n (n.p) - p.
+sc_status build_dipole_parts(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in,
+                             std::vector<HostPart>& parts)
+{
+    if (m->surface != 2)
+        return fail(ctx, SC_ERR_INVALID, "a dipole source needs an ellipsoidal mirror (it sits at its focus F1)");
+    const int nr = m->q.n_r, nt = m->q.n_theta;
+    std::vector<double> gr, gw;
+    gauss_legendre(nr, m->r_min, m->r_max, gr, gw);
+    const double dth = 2.0 * kPi / nt;
+    const double* p = in->dip;
+    parts.assign(3, HostPart());
+    for (int mm = 0; mm < 3; ++mm) {
+        parts[mm].kind = PART_IK_POW;
+        parts[mm].m = mm;
+    }
+    // E_m, B_m at a mirror point
+    auto terms = [&](double x, double y, double z, double E[3][3], double B[3][3]) {
+        const double d[3] = {x, y, z - 2.0 * m->e};
+        const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const double n[3] = {d[0] / r, d[1] / r, d[2] / r};
+        const double np = n[0] * p[0] + n[1] * p[1] + n[2] * p[2];
+        const double nxp[3] = {n[1] * p[2] - n[2] * p[1], n[2] * p[0] - n[0] * p[2], n[0] * p[1] - n[1] * p[0]};
+        for (int c = 0; c < 3; ++c) {
+            const double a2 = 3.0 * n[c] * np - p[c];
+            E[0][c] = a2 / (r * r * r);
+            B[0][c] = 0.0;
+            E[1][c] = -a2 / (r * r);
+            B[1][c] = nxp[c] / (r * r);
+            E[2][c] = -(p[c] - n[c] * np) / r;  // -(n x p) x n / r
+            B[2][c] = -nxp[c] / r;
+        }
+    };
+    for (int i = 0; i < nr; ++i) {
+        const double r = gr[i];
+        const SurfPt sp = surf_at(m, r);
+        for (int l = 0; l < nt; ++l) {
+            const double th = l * dth;
+            const double x = r * cos(th), y = r * sin(th);
+            const double N[3] = {-sp.dzdr * cos(th), -sp.dzdr * sin(th), 1.0};
+            const double wq = gw[i] * dth * r / (2.0 * kPi);
+            double E[3][3], B[3][3];
+            terms(x, y, sp.z, E, B);
+            for (int mm = 0; mm < 3; ++mm) {
+                HostNode nd;
+                nd.px = x; nd.py = y; nd.pz = sp.z;
+                nd.pn = sp.pn;
+                nd.w = 0.0;
+                nd.jx = (N[1] * B[mm][2] - N[2] * B[mm][1]) * wq;  // J = N x B~, rho = N . E~
+                nd.jy = (N[2] * B[mm][0] - N[0] * B[mm][2]) * wq;
+                nd.jz = (N[0] * B[mm][1] - N[1] * B[mm][0]) * wq;
+                nd.rho = (N[0] * E[mm][0] + N[1] * E[mm][1] + N[2] * E[mm][2]) * wq;
+                parts[mm].surf.push_back(nd);
+            }
+        }
+    }
+    if (!m->q.rim_term) return SC_OK;
+    for (int edge = 0; edge < 2; ++edge) {
+        const double r = edge == 0 ? m->r_max : m->r_min;
+        const double sgn = edge == 0 ? 1.0 : -1.0;
+        if (r <= 0.0) continue;
+        const SurfPt sp = surf_at(m, r);
+        const double nlen2 = 1.0 + sp.dzdr * sp.dzdr;
+        for (int l = 0; l < nt; ++l) {
+            const double th = l * dth, c = cos(th), s = sin(th);
+            const double x = r * c, y = r * s;
+            const double N[3] = {-sp.dzdr * c, -sp.dzdr * s, 1.0};
+            double E[3][3], B[3][3];
+            terms(x, y, sp.z, E, B);
+            for (int mm = 0; mm < 3; ++mm) {
+                const double jx = N[1] * B[mm][2] - N[2] * B[mm][1], jy = N[2] * B[mm][0] - N[0] * B[mm][2],
+                             jz = N[0] * B[mm][1] - N[1] * B[mm][0];
+                const double q = sgn * (jx * c + jy * s + jz * sp.dzdr) / nlen2 * r * dth;
+                HostNode nd;
+                nd.px = x; nd.py = y; nd.pz = sp.z;
+                nd.pn = sp.pn;
+                nd.w = 0.0;
+                nd.jx = nd.jy = nd.jz = 0.0;
+                nd.rho = q / (2.0 * kPi);
+                parts[mm].rim.push_back(nd);
+            }
+        }
+    }
+    return SC_OK;
+}
+
 sc_status get_table(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, Table** out,
                     cudaStream_t stream)
 {
@@ -820,7 +950,13 @@ sc_status get_table(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, 
     Table t;
     t.mid = m->id;
     t.iid = in->id;
-    if (in->profile >= SC_PROFILE_LAGUERRE_GAUSS) {
+    // the compensated FP32 phase needs the incident wavefront to focus on
+    // the origin: plane waves on the paraboloid, the F1 dipole on the ellipsoid
+    t.fp32_ok = (m->surface == 2) == (in->profile == SC_PROFILE_DIPOLE);
+    if (in->profile == SC_PROFILE_DIPOLE) {
+        sc_status st = build_dipole_parts(ctx, m, in, hp);
+        if (st != SC_OK) return st;
+    } else if (in->profile >= SC_PROFILE_LAGUERRE_GAUSS) {
         sc_status st = build_cheb_parts(ctx, m, in, hp, t.kc, t.kh);
         if (st != SC_OK) return st;
     } else {
@@ -921,6 +1057,9 @@ sc_status request_amps(sc_ctx* ctx, const sc_incident_t* in, const Table* tab, c
             if (tp.kind == PART_INV_K) {
                 wr = 0.0;
                 wi = -1.0 / k;
+            } else if (tp.kind == PART_IK_POW) {
+                wr = tp.m == 0 ? 1.0 : (tp.m == 2 ? -k * k : 0.0);
+                wi = tp.m == 1 ? k : 0.0;
             } else if (tp.kind != PART_ONE) {
                 const double x = (k - tab->kc) / tab->kh;
                 if (!(fabs(x) <= 1.0 + 1e-12))
@@ -993,8 +1132,10 @@ sc_status check_points_host(sc_ctx* ctx, const sc_mirror_t* m, const double* pts
             return fail(ctx, SC_ERR_INVALID, "point %d is not finite", i);
         const double r = sqrt(x * x + y * y + z * z);
         if (r < m->f - 1e-6) continue;
-        const double rho = sqrt(x * x + y * y), zs = rho * rho / (4.0 * m->f) - m->f;
-        if (rho >= m->r_min - 1e-6 && rho <= m->r_max + 1e-6 && fabs(z - zs) < 1e-6)
+        // |P| >= f = c - e on both surfaces
+        const double rho = sqrt(x * x + y * y);
+        if (rho >= m->r_min - 1e-6 && rho <= m->r_max + 1e-6 &&
+            fabs(z - surf_at(m, std::min(rho, m->r_max)).z) < 1e-6)
             return fail(ctx, SC_ERR_INVALID, "point %d lies on the mirror surface", i);
         (void)built;
     }
@@ -1130,6 +1271,10 @@ sc_status plan_request(sc_ctx* ctx, Lane& ln, const Table* tab, const double* om
                        double dom, const double* d_pts, int n_points, const double* d_amp,
                        const double* d_k, float2* dE, float2* dB, std::vector<Chunk>& out)
 {
+    if (!tab->fp32_ok)
+        return fail(ctx, SC_ERR_INVALID,
+                    "this mirror and beam do not focus on the origin (e.g. a collimated beam on an "
+                    "ellipsoid): the compensated FP32 phase does not apply, use SC_FP64");
     const int max_om_chunk = 2048;
     const int flush_tiles = (int)std::max<long long>(1, ctx->flush_nodes / sc::kTile);
     for (int o0 = 0; o0 < n_omega; o0 += max_om_chunk) {
@@ -1711,6 +1856,28 @@ sc_status sc_mirror(sc_ctx* ctx, double f, double r_min, double r_max, const sc_
     return SC_OK;
 }
 
+sc_status sc_mirror_ellipsoid(sc_ctx* ctx, double c, double e, double r_min, double r_max,
+                              const sc_quadrature* q, sc_mirror_t** out)
+{
+    if (!out || !q) return fail(ctx, SC_ERR_INVALID, "null argument");
+    *out = nullptr;
+    if (!(e > 0.0) || !(c > e) || !(r_min >= 0.0) || !(r_max > r_min) || !(r_max * r_max < c * c - e * e) ||
+        q->n_r < 1 || q->n_theta < 1 || q->radial_kind != SC_QUAD_GAUSS_LEGENDRE)
+        return fail(ctx, SC_ERR_INVALID, "invalid ellipsoidal mirror (c=%g e=%g r_min=%g r_max=%g)", c, e, r_min,
+                    r_max);
+    sc_mirror_t* m = new sc_mirror_t();
+    m->id = g_next_id++;
+    m->surface = 2;
+    m->c = c;
+    m->e = e;
+    m->f = c - e;
+    m->r_min = r_min;
+    m->r_max = r_max;
+    m->q = *q;
+    *out = m;
+    return SC_OK;
+}
+
 void sc_mirror_free(sc_mirror_t* m) { delete m; }
 
 sc_status sc_incident(sc_ctx* ctx, const sc_profile* prof, const sc_polarization* pol,
@@ -1718,13 +1885,17 @@ sc_status sc_incident(sc_ctx* ctx, const sc_profile* prof, const sc_polarization
 {
     if (!out || !prof || !pol || !spec) return fail(ctx, SC_ERR_INVALID, "null argument");
     *out = nullptr;
-    if (prof->kind < 0 || prof->kind > 4 || !(prof->w0 > 0.0) ||
+    if (prof->kind < 0 || prof->kind > 5 || !(prof->w0 > 0.0) ||
         (prof->kind == SC_PROFILE_SUPERGAUSS && prof->sg_order < 1) || prof->n_zernike < 0 ||
         prof->n_zernike > 64 || (prof->n_zernike > 0 && !prof->zernike_noll_waves))
         return fail(ctx, SC_ERR_INVALID, "invalid beam profile");
     if (prof->order < 0 || prof->order > 1 || (prof->order == 1 && prof->kind >= SC_PROFILE_TOPHAT))
         return fail(ctx, SC_ERR_INVALID, "beam order must be 0 or 1 (1 needs a smooth collimated profile)");
-    if (prof->kind >= SC_PROFILE_LAGUERRE_GAUSS) {
+    if (prof->kind == SC_PROFILE_DIPOLE &&
+        (!(prof->dipole[0] != 0.0 || prof->dipole[1] != 0.0 || prof->dipole[2] != 0.0) ||
+         spec->kind == SC_SPEC_GAUSS_TIME || spec->kind == SC_SPEC_SUPERGAUSS_LAMBDA))
+        return fail(ctx, SC_ERR_INVALID, "a dipole needs a nonzero moment and a SAMPLED or MONO spectrum");
+    if (prof->kind == SC_PROFILE_LAGUERRE_GAUSS || prof->kind == SC_PROFILE_ENVELOPE) {
         if (!(prof->omega_lo > 0.0) || !(prof->omega_hi > prof->omega_lo))
             return fail(ctx, SC_ERR_INVALID, "kinds 3-4 need a band 0 < omega_lo < omega_hi");
         if (prof->kind == SC_PROFILE_LAGUERRE_GAUSS &&
@@ -1760,6 +1931,7 @@ sc_status sc_incident(sc_ctx* ctx, const sc_profile* prof, const sc_polarization
     in->om_lo = prof->omega_lo;
     in->om_hi = prof->omega_hi;
     in->fit_tol = prof->fit_tol > 0.0 ? prof->fit_tol : 1e-8;
+    for (int c = 0; c < 3; ++c) in->dip[c] = prof->dipole[c];
     in->zern.assign(prof->zernike_noll_waves, prof->zernike_noll_waves + prof->n_zernike);
     in->pol = pol->kind;
     in->angle = pol->angle_rad;
@@ -2063,6 +2235,8 @@ sc_status sc_eval_fp32_static(sc_ctx* ctx, const sc_mirror_t* m, const sc_incide
                     "node table not resident: run sc_eval once for this mirror and incident first");
     if (tab->parts.size() > 1)
         return fail(ctx, SC_ERR_INVALID, "a beam with %zu node tables needs sc_eval", tab->parts.size());
+    if (!tab->fp32_ok)
+        return fail(ctx, SC_ERR_INVALID, "this mirror and beam need the FP64 path of sc_eval");
     ctx->tick++;
     void* scratch = nullptr;
     cudaError_t e = sc::static_scratch(ctx->device, &scratch);

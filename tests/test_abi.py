@@ -100,6 +100,30 @@ def test_envelope_beam_validation():
             lib.sc_incident_free(h)
 
 
+def test_ellipsoid_and_dipole_validation():
+    lib = sc.load()
+    q = sc.sc_quadrature(0, 8, 8, 1)
+    h = ctypes.c_void_p()
+    for c, e, rmax, want in [(14.0, 6.0, 12.0, sc.SC_OK), (14.0, 6.0, 12.9, sc.SC_ERR_INVALID),
+                             (6.0, 6.0, 1.0, sc.SC_ERR_INVALID), (14.0, 0.0, 1.0, sc.SC_ERR_INVALID)]:
+        st = lib.sc_mirror_ellipsoid(None, c, e, 0.0, rmax, ctypes.byref(q), ctypes.byref(h))
+        assert st == want, (c, e, rmax)
+        if st == sc.SC_OK:
+            lib.sc_mirror_free(h)
+    pol = sc.sc_polarization(0, 0.0)
+    mono = sc.sc_spectrum(0, 1.0, 1.0, 0.1, 3, 1.0, 0, None, None, 0, None)
+    gtime = sc.sc_spectrum(1, 3.0, 1.0, 0.1, 3, 1.0, 0, None, None, 0, None)
+    for dip, spec, order, want in [((1.0, 0.0, 0.0), mono, 0, sc.SC_OK), ((0.0, 0.0, 0.0), mono, 0, sc.SC_ERR_INVALID),
+                                   ((1.0, 0.0, 0.0), gtime, 0, sc.SC_ERR_INVALID),
+                                   ((0.0, 1.0, 0.0), mono, 1, sc.SC_ERR_INVALID)]:
+        prof = sc.sc_profile(5, 1.0, 4, 0, None, order, 0, 0, 0.0, None, None, 0.0, 0.0, 0.0,
+                             (ctypes.c_double * 3)(*dip))
+        st = lib.sc_incident(None, ctypes.byref(prof), ctypes.byref(pol), ctypes.byref(spec), ctypes.byref(h))
+        assert st == want, (dip, order)
+        if st == sc.SC_OK:
+            lib.sc_incident_free(h)
+
+
 def _incident(lib, beam, spec):
     keep = []
     prof = sc.sc_profile(sc.PROFILES[beam["profile"]], beam["w0"], beam.get("sg_order", 4), 0, None)
