@@ -183,6 +183,43 @@ def oracle_sample_rate(w, seconds: float, amp=True):
     return evals / dt, idx, dt, os.cpu_count(), E0, B0
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the record."""
+    import subprocess
+
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return platform.machine()
+
+
+def oracle_single_core_rate(w, n_omega: int = 32):
+    """The same oracle on one thread: one point x all nodes x the first
+    n_omega omegas.  Returns (evals/s, seconds)."""
+    import oracle
+    from paper_1609_08146_gb300 import workloads as wl
+
+    m, b = wl.oracle_args(w)
+    om = w["omegas"][:n_omega]
+    t0 = time.perf_counter()
+    oracle.field(m, b, om, w["points"][:1], threads=1)
+    dt = time.perf_counter() - t0
+    oracle.field(m, b, om[:1], w["points"][:1], threads=os.cpu_count())  # restore the thread count
+    return m["n_r"] * m["n_theta"] * len(om) / dt, dt
+
+
 def rel_l2(F, R):
     """max over omega of sqrt(mean_points sum_c |F - R|^2) / max_points |R|."""
     F = np.asarray(F, dtype=np.complex128)
@@ -334,7 +371,7 @@ def run_reference(args, rank, world, pg):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w["name"], "sampled": True},
         "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -463,9 +500,12 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, idx, dt, cores, E0, B0 = oracle_sample_rate(w, args.cpu_seconds)
+        r1, dt1 = oracle_single_core_rate(w)
         cpu = {"value": r, "unit": "evals/s", "cores": cores, "kind": "oracle",
                "sample": "%d of %d points x all %d nodes x %d omegas (%.1f s, FP64 OpenMP)"
-               % (len(idx), npts, n_nodes, len(om), dt)}
+               % (len(idx), npts, n_nodes, len(om), dt),
+               "cpu_model": cpu_model(), "single_core_value": r1,
+               "single_core_sample": "1 point x all nodes x 32 omegas on one thread (%.1f s)" % dt1}
         # the oracle's sampled outputs also give the error of both GPU forms
         ti = torch.tensor(idx, device=dev)
         Eg = E.index_select(1, ti).cpu().numpy()
