@@ -327,6 +327,27 @@ sc_status sc_time_domain(sc_ctx* ctx, sc_precision prec, const void* E_spec, con
                          int n_t, float* E_t, float* B_t);
 
 /*
+ * The time-domain field without the spectral field (Sec. III.B, Eq. 13 applied
+ * to the spectra of Eq. 11): the omegas are evaluated in chunks, and each
+ * chunk's spectra are transformed and added into E_t, B_t, so device memory
+ * holds one chunk of spectra at a time whatever n_omega is.  Equal to sc_eval
+ * followed by sc_time_domain up to the FP32 rounding of the chunk sums.
+ *   omegas        host, a uniform increasing grid (both precisions).
+ *   points_xyz    host or device, [n_points][3] doubles.
+ *   times         host, n_t values.
+ *   omega_chunk   omegas per chunk, or <= 0: the whole grid when its E and B
+ *                 spectra fit in 32 GiB, else the largest power of two that
+ *                 does.
+ *   E_t, B_t      host or device, float [n_t][n_points][3]; B_t may be NULL.
+ *   stats         nullable, as for sc_eval (synchronizes).
+ * Synchronizes the context stream.  Errors: as sc_eval and sc_time_domain.
+ */
+sc_status sc_eval_time_domain(sc_ctx* ctx, const sc_mirror_t* mirror, const sc_incident_t* inc,
+                              const double* omegas, int n_omega, const double* points_xyz, int n_points,
+                              sc_precision prec, const double* times, int n_t, int omega_chunk,
+                              float* E_t, float* B_t, sc_eval_stats* stats);
+
+/*
  * Allocation-free variant of sc_eval for the SC_FP32_COMP path.  The paper
  * has no counterpart: this entry point exists for callers that cannot call
  * cudaMalloc while they evaluate -- code running inside a global-mode stream

@@ -92,6 +92,9 @@ SIGNATURES = {
                                  ctypes.POINTER(sc_quadrature), ctypes.POINTER(_VP)]),
     "sc_mirror_ellipsoid": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_double, ctypes.POINTER(sc_quadrature), ctypes.POINTER(_VP)]),
+    "sc_eval_time_domain": (ctypes.c_int, [_VP, _VP, _VP, _DP, ctypes.c_int, _VP, ctypes.c_int, ctypes.c_int,
+                                           _DP, ctypes.c_int, ctypes.c_int, _VP, _VP,
+                                           ctypes.POINTER(sc_eval_stats)]),
     "sc_mirror_free": (None, [_VP]),
     "sc_incident": (ctypes.c_int, [_VP, ctypes.POINTER(sc_profile), ctypes.POINTER(sc_polarization),
                                    ctypes.POINTER(sc_spectrum), ctypes.POINTER(_VP)]),
@@ -323,6 +326,34 @@ class Context:
             return E, B, dict(evals=st.evals, field_ms=st.field_ms, total_ms=st.total_ms,
                               launches=st.launches, tables=st.tables)
         return E, B
+
+    def eval_time_domain(self, mirror: Mirror, inc: Incident, omegas, points, times, precision: str = "fp32",
+                         omega_chunk: int = 0, with_B: bool = True, stats: bool = False):
+        """E(t), B(t) float32 [n_t, n_pts, 3] straight from the mirror integrals,
+        holding one chunk of spectra at a time (sc_eval_time_domain).  ``points``:
+        torch tensor (cuda -> device outputs) or numpy array (host outputs)."""
+        import torch
+
+        om = np.ascontiguousarray(np.atleast_1d(omegas), dtype=np.float64)
+        tt = np.ascontiguousarray(np.atleast_1d(times), dtype=np.float64)
+        prec = SC_FP32_COMP if precision == "fp32" else SC_FP64
+        if isinstance(points, np.ndarray):
+            pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+            Et = np.empty((tt.size, pts.shape[0], 3), dtype=np.float32)
+            Bt = np.empty_like(Et) if with_B else None
+        else:
+            pts = points.contiguous().to(torch.float64)
+            Et = torch.empty((tt.size, pts.shape[0], 3), dtype=torch.float32, device=pts.device)
+            Bt = torch.empty_like(Et) if with_B else None
+        st = sc_eval_stats()
+        self._check(self._lib.sc_eval_time_domain(self._h, mirror._h, inc._h, _dptr(om), om.size, _addr(pts),
+                                                  pts.shape[0], prec, _dptr(tt), tt.size, int(omega_chunk),
+                                                  _addr(Et), _addr(Bt) if Bt is not None else None,
+                                                  ctypes.byref(st) if stats else None))
+        if stats:
+            return Et, Bt, dict(evals=st.evals, field_ms=st.field_ms, total_ms=st.total_ms,
+                                launches=st.launches, tables=st.tables)
+        return Et, Bt
 
     def time_domain(self, E, B, omegas, times, precision: str = "fp32", out=None):
         """Inverse transform of spectra [n_omega, n_pts, 3] -> float32

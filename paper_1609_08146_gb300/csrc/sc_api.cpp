@@ -132,6 +132,7 @@ struct sc_ctx {
     std::list<Table> tables;
     uint64_t tick = 0;
     DevBuf pts, outE, outB, tkval, tvals, phasor, specE, specB, tE, tB;
+    DevBuf fpts, fspecE, fspecB, ftE, ftB;  // sc_eval_time_domain: points, chunk spectra, E(t), B(t)
     int* d_err = nullptr;
     int* h_err = nullptr;          // pinned
     sc_counters ctr{};
@@ -1821,7 +1822,8 @@ sc_status sc_destroy(sc_ctx* ctx)
     settle_events(ctx);
     for (auto& t : ctx->tables) free_table(ctx, t);
     for (DevBuf* b : {&ctx->pts, &ctx->outE, &ctx->outB, &ctx->tkval, &ctx->tvals, &ctx->phasor,
-                      &ctx->specE, &ctx->specB, &ctx->tE, &ctx->tB})
+                      &ctx->specE, &ctx->specB, &ctx->tE, &ctx->tB, &ctx->fpts, &ctx->fspecE,
+                      &ctx->fspecB, &ctx->ftE, &ctx->ftB})
         if (b->p) cudaFree(b->p);
     free_lane(ctx->main);
     for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
@@ -1963,24 +1965,13 @@ sc_status sc_spectrum_eval(sc_ctx* ctx, const sc_incident_t* inc, const double* 
     return SC_OK;
 }
 
-sc_status sc_eval(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, const double* omegas,
-                  int n_omega, const double* points_xyz, int n_points, sc_precision prec,
-                  void* E_out, void* B_out, sc_eval_stats* stats)
+// sc_eval after validation, with ctx->mu held and the device set (dom: the
+// omega step of the uniform grid the FP32 path needs).
+static sc_status eval_unlocked(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in,
+                               const double* omegas, int n_omega, const double* points_xyz,
+                               int n_points, sc_precision prec, double dom, void* E_out,
+                               void* B_out, sc_eval_stats* stats)
 {
-    if (!ctx) return SC_ERR_INVALID;
-    if (!m || !in || !omegas || !points_xyz || !E_out || n_omega < 1 || n_points < 1)
-        return fail(ctx, SC_ERR_INVALID, "invalid argument");
-    if (prec != SC_FP32_COMP && prec != SC_FP64) return fail(ctx, SC_ERR_INVALID, "bad precision");
-    for (int i = 0; i < n_omega; ++i)
-        if (!(omegas[i] > 0.0) || !std::isfinite(omegas[i]))
-            return fail(ctx, SC_ERR_INVALID, "omega[%d] must be positive", i);
-    double dom = 0.0;
-    if (prec == SC_FP32_COMP && !uniform_grid(omegas, n_omega, dom))
-        return fail(ctx, SC_ERR_INVALID, "SC_FP32_COMP needs a uniform, increasing omega grid");
-    std::lock_guard<std::mutex> lock(ctx->mu);
-    SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
-    ctx->tick++;
-
     const bool pts_dev = is_device_ptr(points_xyz);
     const bool e_dev = is_device_ptr(E_out);
     const bool b_dev = B_out ? is_device_ptr(B_out) : e_dev;
@@ -2107,6 +2098,140 @@ sc_status sc_eval(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, co
         ctx->time_field = timing_before;
     }
     return SC_OK;
+}
+
+sc_status sc_eval(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, const double* omegas,
+                  int n_omega, const double* points_xyz, int n_points, sc_precision prec,
+                  void* E_out, void* B_out, sc_eval_stats* stats)
+{
+    if (!ctx) return SC_ERR_INVALID;
+    if (!m || !in || !omegas || !points_xyz || !E_out || n_omega < 1 || n_points < 1)
+        return fail(ctx, SC_ERR_INVALID, "invalid argument");
+    if (prec != SC_FP32_COMP && prec != SC_FP64) return fail(ctx, SC_ERR_INVALID, "bad precision");
+    for (int i = 0; i < n_omega; ++i)
+        if (!(omegas[i] > 0.0) || !std::isfinite(omegas[i]))
+            return fail(ctx, SC_ERR_INVALID, "omega[%d] must be positive", i);
+    double dom = 0.0;
+    if (prec == SC_FP32_COMP && !uniform_grid(omegas, n_omega, dom))
+        return fail(ctx, SC_ERR_INVALID, "SC_FP32_COMP needs a uniform, increasing omega grid");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    ctx->tick++;
+
+    return eval_unlocked(ctx, m, in, omegas, n_omega, points_xyz, n_points, prec, dom, E_out, B_out, stats);
+}
+
+static sc_status time_domain_unlocked(sc_ctx* ctx, sc_precision prec, const void* E_spec,
+                                      const void* B_spec, const double* omegas, int n_omega,
+                                      int n_points, const double* times, int n_t, float* E_t,
+                                      float* B_t, double dk, int accumulate);
+
+sc_status sc_eval_time_domain(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in,
+                              const double* omegas, int n_omega, const double* points_xyz, int n_points,
+                              sc_precision prec, const double* times, int n_t, int omega_chunk, float* E_t,
+                              float* B_t, sc_eval_stats* stats)
+{
+    if (!ctx) return SC_ERR_INVALID;
+    if (!m || !in || !omegas || !points_xyz || !times || !E_t || n_omega < 1 || n_points < 1 || n_t < 1)
+        return fail(ctx, SC_ERR_INVALID, "invalid argument");
+    if (prec != SC_FP32_COMP && prec != SC_FP64) return fail(ctx, SC_ERR_INVALID, "bad precision");
+    for (int i = 0; i < n_omega; ++i)
+        if (!(omegas[i] > 0.0) || !std::isfinite(omegas[i]))
+            return fail(ctx, SC_ERR_INVALID, "omega[%d] must be positive", i);
+    double dom = 0.0;
+    if (!uniform_grid(omegas, n_omega, dom))
+        return fail(ctx, SC_ERR_INVALID, "the inverse transform needs a uniform omega grid");
+    const bool out_dev = is_device_ptr(E_t);
+    if (B_t && is_device_ptr(B_t) != out_dev)
+        return fail(ctx, SC_ERR_INVALID, "E_t and B_t must both be host or both device");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    ctx->tick++;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (stats) {
+        ev0 = take_event(ctx);
+        ev1 = take_event(ctx);
+        cudaEventRecord(ev0, ctx->stream);
+    }
+    const double field_ms_before = ctx->ctr.field_ms;
+    const uint64_t launches_before = ctx->ctr.launches;
+    const bool timing_before = ctx->time_field;
+    if (stats) ctx->time_field = true;
+    sc_status st;
+    // points on the device, once
+    const double* d_pts = points_xyz;
+    if (!is_device_ptr(points_xyz)) {
+        st = check_points_host(ctx, m, points_xyz, n_points);
+        if (st != SC_OK) return st;
+        if ((st = ensure(ctx, ctx->fpts, (size_t)n_points * 3 * sizeof(double))) != SC_OK) return st;
+        SC_CUDA(cudaMemcpyAsync(ctx->fpts.p, points_xyz, (size_t)n_points * 3 * sizeof(double),
+                                cudaMemcpyHostToDevice, ctx->stream), "upload points");
+        d_pts = (const double*)ctx->fpts.p;
+    }
+    // time-domain sums on the device
+    const size_t out_bytes = (size_t)n_t * n_points * 3 * sizeof(float);
+    float* dEt = E_t;
+    float* dBt = B_t;
+    if (!out_dev) {
+        if ((st = ensure(ctx, ctx->ftE, out_bytes)) != SC_OK) return st;
+        if (B_t && (st = ensure(ctx, ctx->ftB, out_bytes)) != SC_OK) return st;
+        dEt = (float*)ctx->ftE.p;
+        dBt = B_t ? (float*)ctx->ftB.p : nullptr;
+    }
+    // omega chunks: by default as many omegas as keep a chunk's E and B spectra
+    // within 32 GiB, rounded down to a power of two (the field kernels' omega
+    // classes) when the grid does not fit whole
+    const size_t elem = prec == SC_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t per_omega = (size_t)n_points * 3 * elem;
+    int chunk = omega_chunk;
+    if (chunk <= 0) {
+        const size_t fit = std::max<size_t>(1, (size_t(32) << 30) / (2 * per_omega));
+        if (fit >= (size_t)n_omega) {
+            chunk = n_omega;
+        } else {
+            chunk = 1;
+            while ((size_t)chunk * 2 <= fit) chunk *= 2;
+        }
+    }
+    chunk = std::min(chunk, n_omega);
+    if ((st = ensure(ctx, ctx->fspecE, (size_t)chunk * per_omega)) != SC_OK) return st;
+    if (B_t && (st = ensure(ctx, ctx->fspecB, (size_t)chunk * per_omega)) != SC_OK) return st;
+    const double dk = n_omega > 1 ? 2.0 * kPi * dom : 1.0;
+    double evals = 0.0;
+    for (int o0 = 0; o0 < n_omega; o0 += chunk) {
+        const int c = std::min(chunk, n_omega - o0);
+        st = eval_unlocked(ctx, m, in, omegas + o0, c, d_pts, n_points, prec, dom, ctx->fspecE.p,
+                           B_t ? ctx->fspecB.p : nullptr, nullptr);
+        if (st != SC_OK) return st;
+        st = time_domain_unlocked(ctx, prec, ctx->fspecE.p, B_t ? ctx->fspecB.p : nullptr, omegas + o0, c,
+                                  n_points, times, n_t, dEt, dBt, dk, o0 > 0);
+        if (st != SC_OK) return st;
+        for (const auto& t : ctx->tables)
+            if (t.mid == m->id && t.iid == in->id) evals += (double)n_points * t.n_surf * c;
+    }
+    if (!out_dev) {
+        SC_CUDA(cudaMemcpyAsync(E_t, dEt, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "download E(t)");
+        if (B_t) SC_CUDA(cudaMemcpyAsync(B_t, dBt, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "download B(t)");
+    }
+    if (stats) cudaEventRecord(ev1, ctx->stream);
+    st = check_device_error(ctx);
+    if (stats) {
+        ctx->time_field = timing_before;
+        if (st != SC_OK) return st;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        ctx->pool.push_back(ev0);
+        ctx->pool.push_back(ev1);
+        settle_events(ctx);
+        stats->evals = evals;
+        stats->total_ms = ms;
+        stats->field_ms = ctx->ctr.field_ms - field_ms_before;
+        stats->launches = (int)(ctx->ctr.launches - launches_before);
+        stats->tables = 0;
+        for (const auto& t : ctx->tables)
+            if (t.mid == m->id && t.iid == in->id) stats->tables = (int)t.parts.size();
+    }
+    return st;
 }
 
 sc_status sc_eval_batch(sc_ctx* ctx, const sc_request* reqs, int n_req, sc_eval_stats* stats)
@@ -2291,25 +2416,21 @@ sc_status sc_eval_fp32_static(sc_ctx* ctx, const sc_mirror_t* m, const sc_incide
     return SC_OK;
 }
 
-sc_status sc_time_domain(sc_ctx* ctx, sc_precision prec, const void* E_spec, const void* B_spec,
-                         const double* omegas, int n_omega, int n_points, const double* times,
-                         int n_t, float* E_t, float* B_t)
+// sc_time_domain after validation, with ctx->mu held and the device set: dk
+// is the step of the full uniform grid (the omegas may be one chunk of it);
+// accumulate adds to E_t, B_t (device outputs only) instead of storing.
+static sc_status time_domain_unlocked(sc_ctx* ctx, sc_precision prec, const void* E_spec,
+                                      const void* B_spec, const double* omegas, int n_omega,
+                                      int n_points, const double* times, int n_t, float* E_t,
+                                      float* B_t, double dk, int accumulate)
 {
-    if (!ctx) return SC_ERR_INVALID;
-    if (!E_spec || !E_t || !omegas || !times || n_omega < 1 || n_points < 1 || n_t < 1 ||
-        (B_spec == nullptr) != (B_t == nullptr))
-        return fail(ctx, SC_ERR_INVALID, "invalid argument");
-    double dom = 0.0;
-    if (!uniform_grid(omegas, n_omega, dom))
-        return fail(ctx, SC_ERR_INVALID, "the inverse transform needs a uniform omega grid");
-    std::lock_guard<std::mutex> lock(ctx->mu);
-    SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
     const size_t elem = prec == SC_FP64 ? sizeof(double2) : sizeof(float2);
     const long long n_vals = (long long)n_points * 3;
     const size_t spec_bytes = (size_t)n_omega * n_vals * elem;
     const size_t out_bytes = (size_t)n_t * n_vals * sizeof(float);
     const bool in_dev = is_device_ptr(E_spec);
     const bool out_dev = is_device_ptr(E_t);
+    if (accumulate && !out_dev) return fail(ctx, SC_ERR_INVALID, "accumulation needs device outputs");
     sc_status st;
     std::vector<double> kv(n_omega);
     for (int i = 0; i < n_omega; ++i) kv[i] = 2.0 * kPi * omegas[i];
@@ -2337,7 +2458,6 @@ sc_status sc_time_domain(sc_ctx* ctx, sc_precision prec, const void* E_spec, con
     }
     SC_CUDA(cudaMemcpyAsync(ctx->tkval.p, kv.data(), kv.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload wavenumbers");
     SC_CUDA(cudaMemcpyAsync(ctx->tvals.p, times, (size_t)n_t * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload times");
-    const double dk = n_omega > 1 ? 2.0 * kPi * dom : 1.0;
     for (int pass = 0; pass < (B_spec ? 2 : 1); ++pass) {
         sc::IdftLaunch l;
         l.F = pass == 0 ? dEs : dBs;
@@ -2350,6 +2470,7 @@ sc_status sc_time_domain(sc_ctx* ctx, sc_precision prec, const void* E_spec, con
         l.dk = dk;
         l.out = pass == 0 ? dEt : dBt;
         l.phasor = (float2*)ctx->phasor.p;
+        l.accumulate = accumulate;
         const int r = sc::launch_idft(l, ctx->stream);
         if (r < 0) return cuda_fail(ctx, (cudaError_t)(-r), "inverse transform launch");
         ctx->ctr.launches += r;
@@ -2360,6 +2481,24 @@ sc_status sc_time_domain(sc_ctx* ctx, sc_precision prec, const void* E_spec, con
         SC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
     }
     return SC_OK;
+}
+
+sc_status sc_time_domain(sc_ctx* ctx, sc_precision prec, const void* E_spec, const void* B_spec,
+                         const double* omegas, int n_omega, int n_points, const double* times,
+                         int n_t, float* E_t, float* B_t)
+{
+    if (!ctx) return SC_ERR_INVALID;
+    if (!E_spec || !E_t || !omegas || !times || n_omega < 1 || n_points < 1 || n_t < 1 ||
+        (B_spec == nullptr) != (B_t == nullptr))
+        return fail(ctx, SC_ERR_INVALID, "invalid argument");
+    double dom = 0.0;
+    if (!uniform_grid(omegas, n_omega, dom))
+        return fail(ctx, SC_ERR_INVALID, "the inverse transform needs a uniform omega grid");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const double dk = n_omega > 1 ? 2.0 * kPi * dom : 1.0;
+    return time_domain_unlocked(ctx, prec, E_spec, B_spec, omegas, n_omega, n_points, times, n_t, E_t, B_t,
+                                dk, 0);
 }
 
 sc_status sc_submit(sc_ctx* ctx, const sc_request* req, uint64_t* ticket)

@@ -106,7 +106,7 @@ __device__ __forceinline__ float2 load_c(const double2* F, size_t i)
 template <typename T>
 __global__ void __launch_bounds__(256) idft_kernel(const T* F, int n_omega, long long n_vals,
                                                    const float2* M, int n_t, float scale,
-                                                   float* out)
+                                                   float* out, int accumulate)
 {
     __shared__ float2 Ms[8][64];
     __shared__ float2 Fs[8][64];
@@ -151,7 +151,10 @@ __global__ void __launch_bounds__(256) idft_kernel(const T* F, int n_omega, long
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const long long v = v0 + tx + 16 * j;
-            if (v < n_vals) out[(size_t)m * n_vals + v] = scale * acc[i][j];
+            if (v < n_vals) {
+                float* o = out + (size_t)m * n_vals + v;
+                *o = accumulate ? *o + scale * acc[i][j] : scale * acc[i][j];
+            }
         }
     }
 }
@@ -177,10 +180,10 @@ int launch_idft(const IdftLaunch& p, cudaStream_t s)
     const float scale = (float)(2.0 * p.dk);
     if (p.f64)
         idft_kernel<double2><<<grid, 256, 0, s>>>((const double2*)p.F, p.n_omega, p.n_vals,
-                                                  p.phasor, p.n_t, scale, p.out);
+                                                  p.phasor, p.n_t, scale, p.out, p.accumulate);
     else
         idft_kernel<float2><<<grid, 256, 0, s>>>((const float2*)p.F, p.n_omega, p.n_vals,
-                                                 p.phasor, p.n_t, scale, p.out);
+                                                 p.phasor, p.n_t, scale, p.out, p.accumulate);
     e = cudaGetLastError();
     return e == cudaSuccess ? 2 : -(int)e;
 }

@@ -136,6 +136,7 @@ struct IdftLaunch {
     double dk;
     float* out;             // [n_t][n_vals]
     float2* phasor;         // scratch [n_omega][n_t]
+    int accumulate = 0;     // add to out (a later chunk of omegas) instead of storing
 };
 int launch_idft(const IdftLaunch& p, cudaStream_t s);
 
