@@ -271,6 +271,19 @@ sc_status sc_incident(sc_ctx* ctx, const sc_profile* prof, const sc_polarization
                       const sc_spectrum* spec, sc_incident_t** out);
 void sc_incident_free(sc_incident_t* inc);
 
+/*
+ * How a (mirror, incident) pair will be evaluated, on the host only (no device
+ * work; ctx may be NULL): the number of node tables, i.e. of field passes per
+ * evaluation (1 for a collimated beam, 2 at order 1, the Chebyshev terms of a
+ * k-dependent envelope, 3 for a dipole), and whether the compensated FP32
+ * path applies (1) or only SC_FP64 does (0).  fp32_ok may be NULL.  Builds
+ * the tables' FP64 nodes to count them, so it costs what a table build costs
+ * on the host.  Errors: SC_ERR_INVALID (null arguments, a dipole without an
+ * ellipsoid, an envelope too rough to fit).
+ */
+sc_status sc_table_count(sc_ctx* ctx, const sc_mirror_t* mirror, const sc_incident_t* inc, int* n_tables,
+                         int* fp32_ok);
+
 /* Evaluate a_n (Eqs. 16 and 18) at n host omegas into host amp_re_im[2n]. */
 sc_status sc_spectrum_eval(sc_ctx* ctx, const sc_incident_t* inc, const double* omegas, int n,
                            double* amp_re_im);

@@ -95,6 +95,7 @@ SIGNATURES = {
     "sc_eval_time_domain": (ctypes.c_int, [_VP, _VP, _VP, _DP, ctypes.c_int, _VP, ctypes.c_int, ctypes.c_int,
                                            _DP, ctypes.c_int, ctypes.c_int, _VP, _VP,
                                            ctypes.POINTER(sc_eval_stats)]),
+    "sc_table_count": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "sc_mirror_free": (None, [_VP]),
     "sc_incident": (ctypes.c_int, [_VP, ctypes.POINTER(sc_profile), ctypes.POINTER(sc_polarization),
                                    ctypes.POINTER(sc_spectrum), ctypes.POINTER(_VP)]),

@@ -938,6 +938,32 @@ sc_status build_dipole_parts(sc_ctx* ctx, const sc_mirror_t* m, const sc_inciden
     return SC_OK;
 }
 
+// The compensated FP32 phase needs the incident wavefront to focus on the
+// origin: plane waves on the paraboloid, the F1 dipole on the ellipsoid.
+bool focuses_on_origin(const sc_mirror_t* m, const sc_incident_t* in)
+{
+    return (m->surface == 2) == (in->profile == SC_PROFILE_DIPOLE);
+}
+
+// The host nodes of every node table of (m, in), FP64 (no device work).
+sc_status build_host_parts(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in,
+                           std::vector<HostPart>& hp, double& kc, double& kh)
+{
+    hp.clear();
+    if (in->profile == SC_PROFILE_DIPOLE) return build_dipole_parts(ctx, m, in, hp);
+    if (in->profile >= SC_PROFILE_LAGUERRE_GAUSS) return build_cheb_parts(ctx, m, in, hp, kc, kh);
+    hp.resize(1);
+    std::vector<HostNode> surf1;
+    build_nodes(m, in, hp[0].surf, hp[0].rim, surf1);
+    if (!surf1.empty()) {
+        HostPart p1;
+        p1.kind = PART_INV_K;
+        p1.surf = std::move(surf1);
+        hp.push_back(std::move(p1));
+    }
+    return SC_OK;
+}
+
 sc_status get_table(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, Table** out,
                     cudaStream_t stream)
 {
@@ -951,26 +977,9 @@ sc_status get_table(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, 
     Table t;
     t.mid = m->id;
     t.iid = in->id;
-    // the compensated FP32 phase needs the incident wavefront to focus on
-    // the origin: plane waves on the paraboloid, the F1 dipole on the ellipsoid
-    t.fp32_ok = (m->surface == 2) == (in->profile == SC_PROFILE_DIPOLE);
-    if (in->profile == SC_PROFILE_DIPOLE) {
-        sc_status st = build_dipole_parts(ctx, m, in, hp);
-        if (st != SC_OK) return st;
-    } else if (in->profile >= SC_PROFILE_LAGUERRE_GAUSS) {
-        sc_status st = build_cheb_parts(ctx, m, in, hp, t.kc, t.kh);
-        if (st != SC_OK) return st;
-    } else {
-        hp.resize(1);
-        std::vector<HostNode> surf1;
-        build_nodes(m, in, hp[0].surf, hp[0].rim, surf1);
-        if (!surf1.empty()) {
-            HostPart p1;
-            p1.kind = PART_INV_K;
-            p1.surf = std::move(surf1);
-            hp.push_back(std::move(p1));
-        }
-    }
+    t.fp32_ok = focuses_on_origin(m, in);
+    sc_status hst = build_host_parts(ctx, m, in, hp, t.kc, t.kh);
+    if (hst != SC_OK) return hst;
     // FP32 tiles and FP64 records of every part, part after part
     std::vector<float> t32;
     std::vector<sc::Node64> h64;
@@ -1953,6 +1962,19 @@ sc_status sc_incident(sc_ctx* ctx, const sc_profile* prof, const sc_polarization
 }
 
 void sc_incident_free(sc_incident_t* in) { delete in; }
+
+sc_status sc_table_count(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, int* n_tables,
+                         int* fp32_ok)
+{
+    if (!m || !in || !n_tables) return fail(ctx, SC_ERR_INVALID, "null argument");
+    std::vector<HostPart> hp;
+    double kc = 0.0, kh = 1.0;
+    sc_status st = build_host_parts(ctx, m, in, hp, kc, kh);
+    if (st != SC_OK) return st;
+    *n_tables = (int)hp.size();
+    if (fp32_ok) *fp32_ok = focuses_on_origin(m, in) ? 1 : 0;
+    return SC_OK;
+}
 
 sc_status sc_spectrum_eval(sc_ctx* ctx, const sc_incident_t* inc, const double* omegas, int n,
                            double* amp_re_im)
