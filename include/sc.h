@@ -372,8 +372,9 @@ sc_status sc_eval_time_domain(sc_ctx* ctx, const sc_mirror_t* mirror, const sc_i
  * until the process exits.
  *   Preconditions: the node table of (mirror, inc) is already resident in
  *   ctx, i.e. sc_eval ran once for this pair (that call may allocate), and
- *   inc has order 0 (a first-order beam, with its second table, is
- *   rejected with SC_ERR_INVALID: use sc_eval).
+ *   the pair needs a single node table on the FP32 path (sc_table_count
+ *   gives 1 table and fp32_ok 1: a collimated beam of order 0 on the
+ *   paraboloid).  Other pairs are rejected with SC_ERR_INVALID: use sc_eval.
  *   omega_n = omega0 + n * domega, n < n_omega (<= 2048), omega0 > 0.
  *   amp_re_im   host, [n_omega][2], e.g. from sc_spectrum_eval.
  *   points_xyz  device, [n_points][3] doubles.
