@@ -57,9 +57,11 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched and serving legs")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="broadband", choices=["broadband", "profile", "c5"],
+    ap.add_argument("--workload", default="broadband", choices=["broadband", "profile", "small_omega", "c5"],
                     help="broadband: the benchmark workload; profile: the same kernel "
-                         "configuration at 128 x 128 nodes, for ncu captures; c5: the largest "
+                         "configuration at 128 x 128 nodes, for ncu captures; small_omega: the "
+                         "broadband mirror, pulse and points at 256 x 256 nodes and 8 omegas (the "
+                         "direct kernel of small requests); c5: the largest "
                          "serving request (1024^2 nodes, GRID^3 points over +-3, 512 omegas, "
                          "512 times) through the fused time-domain path, timed once")
     ap.add_argument("--grid", type=int, default=128, help="points per axis of the c5 workload")
@@ -441,7 +443,12 @@ def main():
     if args.workload == "c5":
         run_c5(args, ctx, sc, torch, dev, stream, wl)
         return
-    w = wl.broadband() if args.workload == "broadband" else wl.broadband(n_nodes=128)
+    if args.workload == "broadband":
+        w = wl.broadband()
+    elif args.workload == "small_omega":
+        w = wl.broadband(n_nodes=256, n_omega=8)
+    else:
+        w = wl.broadband(n_nodes=128)
     mc = w["mirror"]
     m = ctx.mirror(mc["f"], mc["r_min"], mc["r_max"], mc["n_r"], mc["n_theta"], rim=mc["rim"])
     inc = ctx.incident(profile=w["beam"]["profile"], w0=w["beam"]["w0"], pol=w["beam"]["pol"],
@@ -520,8 +527,10 @@ def main():
     peak = sms * 128 * max_mhz * 1e6 * 1e-12  # TOP/s of FP32 lane-ops at the maximum SM clock
     achieved = field_evals * OPS_PER_EVAL / (field_ms / 1000.0) * 1e-12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s",
-            "frac": achieved / peak, "traffic": profile_traffic(),
-            "kernel": FIELD_KERNEL, "ops_per_eval": OPS_PER_EVAL,
+            "frac": achieved / peak,
+            "traffic": profile_traffic() if args.workload != "small_omega" else None,
+            "kernel": FIELD_KERNEL if args.workload != "small_omega" else "field_direct_kernel<8, 1>",
+            "ops_per_eval": OPS_PER_EVAL,
             "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (max SM clock)" % (sms, max_mhz),
             "kernel_ms": field_ms}
     if clk.get("sm_mhz"):
