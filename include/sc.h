@@ -408,7 +408,8 @@ sc_status sc_eval_fp32_static(sc_ctx* ctx, const sc_mirror_t* mirror, const sc_i
  *   omegas      host; points_xyz, E_out, B_out device (B_out may be NULL);
  *               layouts as for sc_eval with SC_FP32_COMP.
  * Asynchronous on the context stream unless stats is given.
- * Errors: as sc_eval; SC_ERR_INVALID names the failing request.
+ * Errors: as sc_eval; SC_ERR_INVALID names the failing request (checked
+ * before any work, including the FP32 precondition of each request).
  */
 typedef struct {
     const sc_mirror_t* mirror;
@@ -440,6 +441,11 @@ sc_status sc_eval_batch(sc_ctx* ctx, const sc_request* reqs, int n_req, sc_eval_
  *             sc_fetch; else caller-owned device outputs (float2 layout of
  *             sc_eval).  Caller-owned buffers must stay valid until done.
  *             SC_ERR_BUSY: the request alone exceeds the budget.
+ *             SC_ERR_INVALID at once when the (mirror, incident) pair does
+ *             not focus on the origin (the FP32 path's precondition).  A
+ *             request whose node tables cannot be built (an envelope too
+ *             rough to fit, a failed table allocation) fails its own ticket
+ *             with that status; the rest of its batch runs.
  * sc_poll     *done = 1 once finished, failed or cancelled (the status says
  *             which: SC_OK, the failure, or SC_ERR_CANCELLED).
  * sc_wait     blocks up to timeout_s; SC_ERR_TIMEOUT if still running.

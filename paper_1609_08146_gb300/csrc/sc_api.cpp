@@ -1596,21 +1596,33 @@ size_t ticket_bytes(const Ticket& t)
     return b;
 }
 
-// Run one batch of admitted tickets on lane L (ctx->mu held).
-sc_status launch_batch(sc_ctx* ctx, Server* srv, int L, const std::vector<uint64_t>& ids)
+// Run one batch of admitted tickets on lane L (ctx->mu held).  A ticket
+// whose node tables cannot be built (an envelope too rough to fit, a device
+// allocation that failed) fails alone and leaves ids; the others run.
+sc_status launch_batch(sc_ctx* ctx, Server* srv, int L, std::vector<uint64_t>& ids)
 {
     Lane& ln = srv->lanes[L];
     ctx->tick++;
     std::vector<double> amp_all, k_all;
     std::vector<size_t> om_off, amp_off;
+    std::vector<uint64_t> run;
     for (uint64_t id : ids) {
         Ticket& t = srv->tickets[id];
-        t.state = 1;
         t.lane = L;
         t.t_start = srv->now();
-        sc_status st = get_table(ctx, t.mirror, t.incident, &t.tab, ln.stream);
-        if (st != SC_OK) return st;
+        std::vector<double> a;
+        sc_status tst = get_table(ctx, t.mirror, t.incident, &t.tab, ln.stream);
+        if (tst == SC_OK) tst = request_amps(ctx, t.incident, t.tab, t.omegas.data(), t.n_omega, a);
+        if (tst != SC_OK) {
+            t.tab = nullptr;
+            t.state = 3;
+            t.status = tst;
+            t.t_done = srv->now();
+            continue;
+        }
+        t.state = 1;
         t.tab->inflight++;
+        run.push_back(id);
         if (t.own_pts) {
             SC_CUDA(cudaMallocAsync((void**)&t.pts, (size_t)t.n_points * 3 * sizeof(double), ln.stream),
                     "serving points");
@@ -1627,14 +1639,13 @@ sc_status launch_batch(sc_ctx* ctx, Server* srv, int L, const std::vector<uint64
             t.E = t.E_user;
             t.B = t.B_user;
         }
-        std::vector<double> a;
-        st = request_amps(ctx, t.incident, t.tab, t.omegas.data(), t.n_omega, a);
-        if (st != SC_OK) return st;
         amp_off.push_back(amp_all.size());
         om_off.push_back(k_all.size());
         amp_all.insert(amp_all.end(), a.begin(), a.end());
         for (double w : t.omegas) k_all.push_back(2.0 * kPi * w);
     }
+    ids.swap(run);
+    if (ids.empty()) return SC_OK;
     sc_status st;
     if ((st = ensure(ctx, ln.amp, amp_all.size() * sizeof(double), ln.stream)) != SC_OK) return st;
     if ((st = ensure(ctx, ln.kval, k_all.size() * sizeof(double), ln.stream)) != SC_OK) return st;
@@ -1711,6 +1722,10 @@ void serve(sc_ctx* ctx)
             }
             if (ids.empty()) break;
             const sc_status st = launch_batch(ctx, srv, L, ids);
+            if (st == SC_OK && ids.empty()) {
+                changed = true;
+                continue;
+            }
             if (st != SC_OK) {
                 cudaStreamSynchronize(srv->lanes[L].stream);
                 for (uint64_t id : ids) {
@@ -2275,6 +2290,9 @@ sc_status sc_eval_batch(sc_ctx* ctx, const sc_request* reqs, int n_req, sc_eval_
         if (!is_device_ptr(q.points_xyz) || !is_device_ptr(q.E_out) ||
             (q.B_out && !is_device_ptr(q.B_out)))
             return fail(ctx, SC_ERR_INVALID, "request %d: points and outputs must be device buffers", r);
+        if (!focuses_on_origin(q.mirror, q.incident))
+            return fail(ctx, SC_ERR_INVALID, "request %d: the FP32 path needs an incident wavefront focused "
+                                             "on the origin", r);
         n_om_total += q.n_omega;
     }
     std::lock_guard<std::mutex> lock(ctx->mu);
@@ -2536,6 +2554,9 @@ sc_status sc_submit(sc_ctx* ctx, const sc_request* req, uint64_t* ticket)
     std::lock_guard<std::mutex> lock(ctx->mu);
     if (!uniform_grid(req->omegas, req->n_omega, dom))
         return fail(ctx, SC_ERR_INVALID, "serving needs a uniform, increasing omega grid");
+    if (!focuses_on_origin(req->mirror, req->incident))
+        return fail(ctx, SC_ERR_INVALID, "serving runs the FP32 path, whose compensated phase needs an "
+                                         "incident wavefront focused on the origin");
     SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
     Ticket t;
     t.mirror = req->mirror;
