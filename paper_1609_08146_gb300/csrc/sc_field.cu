@@ -192,20 +192,26 @@ __device__ __forceinline__ float pair_coefs(const float* nb, int j, float4 pt, f
 // One (point, node, omega) evaluation, packed: accumulators as (re, im) pairs
 // and coefficients pre-duplicated as (c, c) pairs, so the 18 accumulation
 // FMAs issue as 9 FFMA2 and z as one more: 22 FP32 lane-ops in 12 issued
-// instructions, plus the phasor step.  The U q term is added before the V z
-// term so that it does not wait for z: the chain from the phasor to the last
-// update of an E accumulator is three dependent steps instead of four.
+// instructions, plus the phasor step.  QFIRST adds the U q term before the
+// V z term so that it does not wait for z (the chain from the phasor to the
+// last update of an E accumulator is three dependent steps instead of four):
+// 2% faster in the grouped kernel, 10% slower in the direct kernel, whose
+// register allocation it changes, so each kernel takes its faster order.
 struct AccX2 {
     float2 v[6];  // E_x, E_y, E_z, B_x, B_y, B_z as (re, im)
 };
 
+template <bool QFIRST>
 __device__ __forceinline__ void eval_x2(AccX2& a, const float2* cp, float k, float2 ph)
 {
     const float2 q = make_float2(-k * ph.y, k * ph.x);  // q = ik ph
     const float2 z = __ffma2_rn(cp[9], ph, q);           // z = q - ph/R  (cp[9] = (-1/R, -1/R))
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        a.v[c] = __ffma2_rn(cp[3 + c], z, __ffma2_rn(cp[c], q, a.v[c]));
+        if (QFIRST)
+            a.v[c] = __ffma2_rn(cp[3 + c], z, __ffma2_rn(cp[c], q, a.v[c]));
+        else
+            a.v[c] = __ffma2_rn(cp[c], q, __ffma2_rn(cp[3 + c], z, a.v[c]));
         a.v[3 + c] = __ffma2_rn(cp[6 + c], z, a.v[3 + c]);
     }
 }
@@ -463,12 +469,12 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
                     // and fold() takes the sign back out of those slots
                     float2 p0 = sb[j * L::SROW];
                     float2 p1 = cmul(p0, rot);
-                    eval_x2(acc[0], cp, kv[0], p0);
-                    eval_x2(acc[1], cp, kv[1], p1);
+                    eval_x2<true>(acc[0], cp, kv[0], p0);
+                    eval_x2<true>(acc[1], cp, kv[1], p1);
 #pragma unroll
                     for (int jj = 2; jj < kB; ++jj) {
                         const float2 pn = __ffma2_rn((jj & 1) ? cc : ncc, p1, p0);
-                        eval_x2(acc[jj], cp, kv[jj], pn);
+                        eval_x2<true>(acc[jj], cp, kv[jj], pn);
                         p0 = p1;
                         p1 = pn;
                     }
@@ -662,19 +668,19 @@ __global__ void __launch_bounds__(256, 1) field_direct_kernel(BatchLaunch b)
                                        make_float2(co[8], co[8]), make_float2(-co[9], -co[9])};
                 float2 pe = phasor_2wphi(wgh, wgl, phi);
                 if (NB == 1) {
-                    eval_x2(acc[0], cp, kv[0], pe);
+                    eval_x2<false>(acc[0], cp, kv[0], pe);
                 } else {
                     const float2 rot = phasor_2wphi(d1h, d1l, phi);
                     const float2 cc = make_float2(2.f * rot.x, 2.f * rot.x);
                     const float2 ncc = make_float2(-2.f * rot.x, -2.f * rot.x);
                     float2 p0 = pe;
                     float2 p1 = cmul(pe, rot);
-                    eval_x2(acc[0], cp, kv[0], p0);
-                    eval_x2(acc[1], cp, kv[1], p1);
+                    eval_x2<false>(acc[0], cp, kv[0], p0);
+                    eval_x2<false>(acc[1], cp, kv[1], p1);
 #pragma unroll
                     for (int jj = 2; jj < NB; ++jj) {
                         const float2 pn = __ffma2_rn((jj & 1) ? cc : ncc, p1, p0);
-                        eval_x2(acc[jj], cp, kv[jj], pn);
+                        eval_x2<false>(acc[jj], cp, kv[jj], pn);
                         p0 = p1;
                         p1 = pn;
                     }
