@@ -542,6 +542,17 @@ def main():
             "kernel_ms": field_ms}
     if clk.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = achieved / (sms * 128 * clk["sm_mhz"] * 1e6 * 1e-12)
+    # what the FMA and MUFU pipes sustain on pure instruction streams (after the timed region)
+    probes = ctx.measure_alu_peaks()
+    fma_t = probes["fp32_lane_ops_per_s"] * 1e-12
+    fma2_t = probes["fp32x2_lane_ops_per_s"] * 1e-12
+    roof["measured_pipes"] = {
+        "fp32_fma_TOPs": fma_t, "fp32_ffma2_TOPs": fma2_t,
+        "mufu_Tops": probes["mufu_ops_per_s"] * 1e-12,
+        "fma_frac_of_peak": max(fma_t, fma2_t) / peak,
+        "basis": "sc_measure_alu_peaks: independent FFMA, FFMA2 and MUFU rsqrt streams on every SM, "
+                 "best of 3 launches, clocks not pinned"}
+    roof["frac_of_measured_fma"] = achieved / max(fma_t, fma2_t)
 
     # ---- plain FP64 GPU form of the same sum, on a point subsample
     sub = torch.tensor(w["points"][::65], device=dev)  # 64 points

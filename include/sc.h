@@ -480,6 +480,19 @@ typedef struct {
 } sc_counters;
 
 /*
+ * Measured throughput of the arithmetic pipes that bound the field sum (the
+ * per-evaluation FMA work of Eq. 11 and the per-pair rsqrt, rcp and sincos
+ * of the phase, Sec. III.C): streams of independent FP32 FMAs, of packed
+ * FFMA2 (two lane-ops each) and of MUFU rsqrt.approx, on every SM of the
+ * context's device, best of three timed launches after one warm-up, about
+ * 0.1 s of GPU work in all.  Outputs are operations per second (lane-ops
+ * for the FMA forms).  Synchronizes the context stream.
+ * Errors: SC_ERR_INVALID on a NULL argument; SC_ERR_CUDA if a launch fails.
+ */
+sc_status sc_measure_alu_peaks(sc_ctx* ctx, double* fp32_lane_ops_per_s, double* fp32x2_lane_ops_per_s,
+                               double* mufu_ops_per_s);
+
+/*
  * Failure-path self-test (no counterpart in the paper).  Launches one bounded
  * wait, of the kind every field kernel uses for its bulk copies and table
  * hand-overs, on an mbarrier that nothing completes.  The wait gives up

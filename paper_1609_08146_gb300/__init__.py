@@ -118,6 +118,7 @@ SIGNATURES = {
     "sc_ticket_times": (ctypes.c_int, [_VP, ctypes.c_uint64, _DP, _DP, _DP]),
     "sc_selftest_wait": (ctypes.c_int, [_VP]),
     "sc_get_counters": (ctypes.c_int, [_VP, ctypes.POINTER(sc_counters)]),
+    "sc_measure_alu_peaks": (ctypes.c_int, [_VP, _DP, _DP, _DP]),
     "sc_reset_counters": (ctypes.c_int, [_VP]),
     "sc_set_option": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_longlong]),
 }
@@ -466,6 +467,13 @@ class Context:
         self._check(self._lib.sc_get_counters(self._h, ctypes.byref(c)))
         return dict(launches=c.launches, field_launches=c.field_launches, field_ms=c.field_ms,
                     evals=c.evals, graph_captures=c.graph_captures, graph_replays=c.graph_replays)
+
+    def measure_alu_peaks(self):
+        """Measured FP32 FMA, packed FFMA2 and MUFU throughput of this device
+        (operations per second; lane-ops for the FMA forms)."""
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.sc_measure_alu_peaks(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return dict(fp32_lane_ops_per_s=a.value, fp32x2_lane_ops_per_s=b.value, mufu_ops_per_s=c.value)
 
     def reset_counters(self):
         self._check(self._lib.sc_reset_counters(self._h))

@@ -22,7 +22,7 @@ OBJDIR = os.path.join(ROOT, "_build", "sc")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
-SOURCES = ["sc_api.cpp", "sc_field.cu", "sc_reduce.cu", "sc_f64_idft.cu", "sc_static_scratch.cu"]
+SOURCES = ["sc_api.cpp", "sc_field.cu", "sc_reduce.cu", "sc_f64_idft.cu", "sc_static_scratch.cu", "sc_peaks.cu"]
 
 
 def _nvcc() -> str:

@@ -2721,6 +2721,53 @@ sc_status sc_selftest_wait(sc_ctx* ctx)
     return check_device_error(ctx);
 }
 
+sc_status sc_measure_alu_peaks(sc_ctx* ctx, double* fp32_lane_ops_per_s, double* fp32x2_lane_ops_per_s,
+                               double* mufu_ops_per_s)
+{
+    if (!ctx || !fp32_lane_ops_per_s || !fp32x2_lane_ops_per_s || !mufu_ops_per_s)
+        return fail(ctx, SC_ERR_INVALID, "null argument");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const int iters[3] = {16384, 8192, 2048};
+    double* outs[3] = {fp32_lane_ops_per_s, fp32x2_lane_ops_per_s, mufu_ops_per_s};
+    int grids[3];
+    int max_grid = 1;
+    for (int k = 0; k < 3; ++k) max_grid = std::max(max_grid, grids[k] = sc::alu_probe_grid(k, ctx->device));
+    float* sink = nullptr;
+    SC_CUDA(cudaMallocAsync((void**)&sink, (size_t)max_grid * 512 * sizeof(float), ctx->stream), "probe sink");
+    cudaEvent_t e0 = take_event(ctx), e1 = take_event(ctx);
+    sc_status st = SC_OK;
+    for (int k = 0; k < 3 && st == SC_OK; ++k) {
+        float best = 0.f;
+        for (int rep = 0; rep < 4 && st == SC_OK; ++rep) {  // the first launch warms up
+            cudaEventRecord(e0, ctx->stream);
+            const int r = sc::launch_alu_probe(k, iters[k], sink, grids[k], 512, ctx->stream);
+            cudaEventRecord(e1, ctx->stream);
+            if (r < 0) {
+                st = cuda_fail(ctx, (cudaError_t)(-r), "ALU probe launch");
+                break;
+            }
+            ctx->ctr.launches++;
+            const cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                st = cuda_fail(ctx, e, "ALU probe");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && (best == 0.f || ms < best)) best = ms;
+        }
+        const double ops = (double)grids[k] * 512.0 * (double)sc::alu_probe_ops_per_thread(iters[k]);
+        *outs[k] = best > 0.f ? ops / (1e-3 * best) : 0.0;
+    }
+    cudaFreeAsync(sink, ctx->stream);
+    ctx->pool.push_back(e0);
+    ctx->pool.push_back(e1);
+    if (st != SC_OK) return st;
+    SC_CUDA(cudaStreamSynchronize(ctx->stream), "ALU probes");
+    return SC_OK;
+}
+
 sc_status sc_get_counters(sc_ctx* ctx, sc_counters* out)
 {
     if (!ctx || !out) return SC_ERR_INVALID;

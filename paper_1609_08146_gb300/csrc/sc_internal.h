@@ -143,6 +143,13 @@ int launch_idft(const IdftLaunch& p, cudaStream_t s);
 // Failure-path self-test: one bounded mbarrier wait that nothing completes.
 int launch_wait_selftest(int* err, cudaStream_t s);
 
+// Arithmetic-pipe probes (sc_peaks.cu): kind 0 FP32 FMA, 1 packed FFMA2, 2
+// MUFU rsqrt; each thread performs alu_probe_ops_per_thread(iters) of them
+// (an FFMA2 counts as two lane-ops).  sink is never written.
+int launch_alu_probe(int kind, int iters, float* sink, int grid, int block, cudaStream_t s);
+long long alu_probe_ops_per_thread(int iters);
+int alu_probe_grid(int kind, int device);  // resident 512-thread blocks on all SMs
+
 // Fixed device scratch of the allocation-free entry point: 64 MiB of static
 // device memory per GPU.  static_scratch() returns its device address on
 // `device` (looked up once per device with that device current).
