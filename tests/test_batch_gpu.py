@@ -2,9 +2,9 @@
 
 A request's result must be bitwise the same alone (sc_eval) and inside a
 mixed batch (sc_eval_batch): its tiling depends only on its own shape and
-the reduction order is fixed.  Batches span both kernel families (up to 24
+the reduction order is fixed.  Batches span both kernel families (up to 32
 omegas: the direct kernel with 1, 2 or 4 threads per point; more: grouped
-kernels of 4..256 threads per point), several mirrors and beams, ragged point
+kernels of 8..256 threads per point), several mirrors and beams, ragged point
 counts, and match the FP64 oracle.
 """
 import numpy as np
