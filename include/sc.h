@@ -40,6 +40,12 @@
 #include <stddef.h>
 #include <stdint.h>
 
+/* The library is built with hidden symbols; everything declared here is its
+ * exported interface. */
+#if defined(__GNUC__) && !defined(__CUDA_ARCH__)
+#pragma GCC visibility push(default)
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -521,6 +527,10 @@ sc_status sc_set_option(sc_ctx* ctx, int option, long long value);
 
 #ifdef __cplusplus
 }
+#endif
+
+#if defined(__GNUC__) && !defined(__CUDA_ARCH__)
+#pragma GCC visibility pop
 #endif
 
 #endif /* SC_H */

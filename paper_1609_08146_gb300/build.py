@@ -21,8 +21,11 @@ LIB = os.path.join(LIBDIR, "libsc.so")
 OBJDIR = os.path.join(ROOT, "_build", "sc")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
-SOURCES = ["sc_api.cpp", "sc_field.cu", "sc_reduce.cu", "sc_f64_idft.cu", "sc_static_scratch.cu", "sc_peaks.cu"]
+# host symbols are hidden: the library exports only the extern "C" API of sc.h
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
+         "-I" + INCLUDE, "-I" + CSRC]
+SOURCES = ["sc_api.cpp", "sc_tables.cpp", "sc_batch.cpp", "sc_serve.cpp", "sc_field.cu", "sc_reduce.cu",
+           "sc_f64_idft.cu", "sc_static_scratch.cu", "sc_peaks.cu"]
 
 
 def _nvcc() -> str:
@@ -37,7 +40,7 @@ def _sources():
 
 
 def _deps():
-    files = _sources() + [os.path.join(CSRC, "sc_internal.h"), os.path.join(INCLUDE, "sc.h")]
+    files = _sources() + [os.path.join(CSRC, h) for h in ("sc_internal.h", "sc_host.h")] + [os.path.join(INCLUDE, "sc.h")]
     return max(os.path.getmtime(f) for f in files)
 
 

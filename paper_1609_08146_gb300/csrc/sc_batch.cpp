@@ -1,0 +1,372 @@
+// sc_batch.cpp -- batched FP32 execution (A8): chunks, the split autotuner,
+// persistent launches per kernel class, CUDA graphs and the batched reduce.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "sc_host.h"
+
+namespace sch {
+
+// ------------------------------------------------------------------------
+// Batched FP32 execution (A8): requests are cut into chunks (<= 2048 omegas,
+// points bounded by the workspace cap); chunks of one kernel class run in one
+// persistent launch whose CTAs take (chunk, point block, split) items from a
+// device queue; one batched FP64 reduce finishes every chunk.  The field
+// launches of a batch are captured into a CUDA graph and replayed while the
+// launch signature repeats.  Each chunk's split count comes from the
+// autotuner cache (or the heuristic), never from the rest of the batch, so a
+// request gives bitwise the same result alone or in a mix.
+
+// Split a chunk's surface tiles S ways.  Every table part (same nodes) uses
+// the same splits and a workspace section of its own.
+void set_splits(Chunk& c, int S, int tiles)
+{
+    const int tps = (tiles + S - 1) / S;
+    c.f.tiles_per_split = tps;
+    c.f.n_splits = (tiles + tps - 1) / tps;
+    c.rl.n_splits = c.f.n_splits;
+    c.ws_elems = (size_t)(c.f.n_splits + 1) * c.f.n_pts * c.f.n_omega * sc::kAcc * c.n_parts;
+}
+
+int heuristic_splits(int tiles, long long pb, int slots)
+{
+    // enough items for dynamic balance (about 16 per resident CTA), items of
+    // at least 32 node tiles, at most 64 splits
+    long long s = (16LL * slots + pb - 1) / pb;
+    s = std::min<long long>(s, std::max(1, tiles / 32));
+    return (int)std::max<long long>(1, std::min<long long>(64, s));
+}
+
+sc_status launch_chunks_direct(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch, float2* ws, size_t ws_n);
+
+// Time one chunk with split count S (the chunk's outputs are overwritten later).
+float time_chunk(sc_ctx* ctx, Lane& ln, Chunk c, int S, const Table* tab, float2* ws)
+{
+    set_splits(c, S, tab->n_surf_tiles);
+    std::vector<Chunk> one{c};
+    cudaEvent_t a = take_event(ctx), b = take_event(ctx);
+    cudaEventRecord(a, ln.stream);
+    sc_status st = launch_chunks_direct(ctx, ln, one, ws, c.ws_elems);
+    cudaEventRecord(b, ln.stream);
+    float ms = 1e30f;
+    if (st == SC_OK && cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+    cudaGetLastError();
+    ctx->pool.push_back(a);
+    ctx->pool.push_back(b);
+    return ms;
+}
+
+// Split count for a chunk shape: explicit option, tuned value, or heuristic
+// (tuned on first sight when the autotuner is on).
+sc_status choose_splits(sc_ctx* ctx, Lane& ln, Chunk& c, const Table* tab, int slots, int* S_out)
+{
+    const int tiles = tab->n_surf_tiles;
+    if (ctx->nodes_per_split > 0) {
+        const int tps = (int)std::max<long long>(1, ctx->nodes_per_split / sc::kTile);
+        *S_out = (tiles + tps - 1) / tps;
+        return SC_OK;
+    }
+    const auto key = std::make_tuple(c.cls, tiles, tab->n_rim_tiles, c.f.n_pts, c.f.n_omega, c.n_parts);
+    auto hit = ctx->tuned.find(key);
+    if (hit != ctx->tuned.end()) {
+        *S_out = hit->second;
+        return SC_OK;
+    }
+    const int s0 = heuristic_splits(tiles, c.pb, slots);
+    int best = s0;
+    if (ctx->autotune) {
+        // candidates around the heuristic, each timed once on the real chunk
+        std::vector<int> cand;
+        for (int s : {s0 / 2, s0, 2 * s0, 4 * s0})
+            if (s >= 1 && s <= std::min(64, tiles) &&
+                std::find(cand.begin(), cand.end(), s) == cand.end())
+                cand.push_back(s);
+        // only candidates whose whole-request workspace fits under the cap
+        size_t need = 0;
+        std::vector<int> fit;
+        for (int s : cand) {
+            const int tps = (tiles + s - 1) / s;
+            const int ns = (tiles + tps - 1) / tps;
+            const size_t n = (size_t)(ns + 1) * c.f.n_pts * c.f.n_omega * sc::kAcc * c.n_parts;
+            if (n * sizeof(float2) <= ctx->ws_cap) {
+                fit.push_back(s);
+                need = std::max(need, n);
+            }
+        }
+        if (fit.size() > 1) {
+            sc_status st = ensure(ctx, ln.ws, need * sizeof(float2), ln.stream);
+            if (st != SC_OK) return st;
+            float best_ms = 1e30f;
+            for (int s : fit) {
+                const float ms = time_chunk(ctx, ln, c, s, tab, (float2*)ln.ws.p);
+                if (ms < best_ms) { best_ms = ms; best = s; }
+            }
+        }
+    }
+    ctx->tuned[key] = best;
+    *S_out = best;
+    return SC_OK;
+}
+
+// Cut one request into chunks.  d_amp / d_k point at this request's a_n, k_n.
+sc_status plan_request(sc_ctx* ctx, Lane& ln, const Table* tab, const double* omegas, int n_omega,
+                       double dom, const double* d_pts, int n_points, const double* d_amp,
+                       const double* d_k, float2* dE, float2* dB, std::vector<Chunk>& out)
+{
+    if (!tab->fp32_ok)
+        return fail(ctx, SC_ERR_INVALID,
+                    "this mirror and beam do not focus on the origin (e.g. a collimated beam on an "
+                    "ellipsoid): the compensated FP32 phase does not apply, use SC_FP64");
+    const int max_om_chunk = 2048;
+    const int flush_tiles = (int)std::max<long long>(1, ctx->flush_nodes / sc::kTile);
+    for (int o0 = 0; o0 < n_omega; o0 += max_om_chunk) {
+        const int no = std::min(max_om_chunk, n_omega - o0);
+        Chunk c;
+        c.cls = sc::field_class(no);
+        int slots = 1;
+        sc::field_shape(c.cls, ctx->device, &c.ppc, &slots);
+        const double w0 = omegas[o0];
+        c.f.nodes = tab->d32;
+        c.f.n_surf_tiles = tab->n_surf_tiles;
+        c.f.n_rim_tiles = tab->n_rim_tiles;
+        c.f.flush_tiles = flush_tiles;
+        c.f.n_omega = no;
+        c.f.om_hi0 = (float)w0;
+        c.f.om_lo0 = (float)(w0 - (double)c.f.om_hi0);
+        c.f.dom_hi = (float)dom;
+        c.f.dom_lo = (float)(dom - (double)c.f.dom_hi);
+        c.f.err = ctx->d_err;
+        c.f.ws = nullptr;
+        // the split count is chosen on the whole request's point count
+        c.f.pts = d_pts;
+        c.f.n_pts = n_points;
+        c.pb = (n_points + c.ppc - 1) / c.ppc;
+        c.rl.amp = d_amp + 2 * (size_t)o0;
+        c.rl.kval = d_k + o0;
+        c.rl.out_pt_stride_omega = (long long)n_points * 3;
+        c.rl.E = dE + (size_t)o0 * n_points * 3;
+        c.rl.B = dB ? dB + (size_t)o0 * n_points * 3 : nullptr;
+        c.rl.n_pts = n_points;
+        c.rl.n_omega = no;
+        c.tab = tab;
+        c.n_parts = (int)tab->parts.size();
+        c.rl.n_parts = c.n_parts;
+        c.rl.amp_stride = 2LL * n_omega;
+        int S = 1;
+        sc_status st = choose_splits(ctx, ln, c, tab, slots, &S);
+        if (st != SC_OK) return st;
+        set_splits(c, S, tab->n_surf_tiles);
+        const int n_splits = c.f.n_splits;
+        // point chunks bounded by the workspace cap
+        const size_t per_pt = (size_t)(n_splits + 1) * no * sc::kAcc * c.n_parts;
+        long long pchunk = std::max<long long>(1, (long long)(ctx->ws_cap / sizeof(float2) / per_pt));
+        if (pchunk < n_points) pchunk = std::max<long long>(c.ppc, pchunk / c.ppc * c.ppc);
+        for (int p0 = 0; p0 < n_points; p0 += (int)pchunk) {
+            const int np = (int)std::min<long long>(pchunk, n_points - p0);
+            Chunk d = c;
+            d.f.pts = d_pts + 3 * (size_t)p0;
+            d.f.n_pts = np;
+            d.pb = (np + c.ppc - 1) / c.ppc;
+            d.rl.n_pts = np;
+            d.rl.E = c.rl.E + (size_t)p0 * 3;
+            d.rl.B = c.rl.B ? c.rl.B + (size_t)p0 * 3 : nullptr;
+            d.ws_elems = per_pt * np;
+            out.push_back(d);
+        }
+    }
+    return SC_OK;
+}
+
+// Launch a group of chunks whose workspaces fit in ws, with or without a
+// CUDA graph.  Field kernels (one persistent launch per class present) go
+// in the graph; the batched reduce follows on the stream.
+sc_status launch_chunks(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch, float2* ws, size_t ws_n, bool graph)
+{
+    // workspace offsets and reduce offsets
+    size_t off = 0;
+    long long roff = 0;
+    for (auto& c : ch) {
+        c.f.ws = ws + off;
+        c.rl.ws = ws + off;
+        c.rl.off = roff;
+        off += c.ws_elems;
+        roff += (long long)c.rl.n_pts * c.rl.n_omega;
+    }
+    if (off > ws_n) return fail(ctx, SC_ERR_OOM, "workspace plan exceeds its buffer");
+    // per-class descriptor arrays
+    constexpr int kClasses = sc::kNumClasses;
+    std::vector<sc::WorkReq> reqs[kClasses];
+    long long items[kClasses] = {};
+    for (auto& c : ch)
+        for (int t = 0; t < c.n_parts; ++t) {
+            sc::WorkReq w;
+            w.f = c.f;
+            w.f.nodes = c.tab->parts[t].d32;
+            w.f.n_rim_tiles = c.tab->parts[t].n_rim_tiles;
+            w.f.ws = c.f.ws + (size_t)t * (c.ws_elems / c.n_parts);
+            w.pb = c.pb;
+            w.cls = c.cls;
+            w.item0 = items[c.cls];
+            items[c.cls] += (long long)c.pb * (w.f.n_splits + 1);
+            reqs[c.cls].push_back(w);
+        }
+    std::vector<sc::ReduceLaunch> rls;
+    for (auto& c : ch) rls.push_back(c.rl);
+    // arena: queues (64 B each) | WorkReq arrays | ReduceLaunch array
+    size_t bytes = kClasses * 64;
+    size_t req_off[kClasses];
+    for (int k = 0; k < kClasses; ++k) {
+        req_off[k] = bytes;
+        bytes += (reqs[k].size() * sizeof(sc::WorkReq) + 255) / 256 * 256;
+    }
+    const size_t rl_off = bytes;
+    bytes += rls.size() * sizeof(sc::ReduceLaunch);
+    sc_status st = ensure(ctx, ln.desc, bytes, ln.stream);
+    if (st != SC_OK) return st;
+    unsigned char* arena = (unsigned char*)ln.desc.p;
+    for (int k = 0; k < kClasses; ++k)
+        if (!reqs[k].empty())
+            SC_CUDA(cudaMemcpyAsync(arena + req_off[k], reqs[k].data(), reqs[k].size() * sizeof(sc::WorkReq),
+                                    cudaMemcpyHostToDevice, ln.stream), "upload work descriptors");
+    SC_CUDA(cudaMemcpyAsync(arena + rl_off, rls.data(), rls.size() * sizeof(sc::ReduceLaunch),
+                            cudaMemcpyHostToDevice, ln.stream), "upload reduce descriptors");
+
+    struct L { int cls; sc::BatchLaunch b; int grid; };
+    std::vector<L> launches;
+    for (int k = 0; k < kClasses; ++k) {
+        if (reqs[k].empty()) continue;
+        int ppc = 1, slots = 1;
+        sc::field_shape(k, ctx->device, &ppc, &slots);
+        sc::BatchLaunch b{};
+        b.reqs = (const sc::WorkReq*)(arena + req_off[k]);
+        b.n_req = (int)reqs[k].size();
+        b.n_items = items[k];
+        b.queue = (int*)(arena + 64 * k);
+        b.err = ctx->d_err;
+        launches.push_back({k, b, (int)std::min<long long>(slots, items[k])});
+    }
+    auto issue = [&](cudaStream_t s) -> sc_status {
+        SC_CUDA(cudaMemsetAsync(arena, 0, kClasses * 64, s), "reset work queues");
+        for (auto& l : launches) {
+            const int r = sc::launch_field_batch(l.cls, l.b, l.grid, s);
+            if (r < 0) return cuda_fail(ctx, (cudaError_t)(-r), "field kernel launch");
+        }
+        return SC_OK;
+    };
+    cudaEvent_t f0 = nullptr, f1 = nullptr;
+    if (ctx->time_field) {
+        f0 = take_event(ctx);
+        f1 = take_event(ctx);
+        cudaEventRecord(f0, ln.stream);
+    }
+    if (graph) {
+        // signature: everything the captured launches depend on
+        std::vector<unsigned char> sig;
+        auto put = [&](const void* p, size_t n) {
+            const unsigned char* q = (const unsigned char*)p;
+            sig.insert(sig.end(), q, q + n);
+        };
+        put(&arena, sizeof arena);
+        for (auto& l : launches) {
+            put(&l.cls, sizeof l.cls);
+            put(&l.grid, sizeof l.grid);
+            put(&l.b, sizeof l.b);
+        }
+        cudaGraphExec_t exec = nullptr;
+        for (auto& g : ln.graphs)
+            if (g.sig == sig) {
+                exec = g.exec;
+                g.last = ++ctx->graph_tick;
+                ctx->graph_replays++;
+            }
+        if (!exec) {
+            if (!ln.cap_stream)
+                SC_CUDA(cudaStreamCreateWithFlags(&ln.cap_stream, cudaStreamNonBlocking), "capture stream");
+            SC_CUDA(cudaStreamBeginCapture(ln.cap_stream, cudaStreamCaptureModeRelaxed), "begin capture");
+            st = issue(ln.cap_stream);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(ln.cap_stream, &g);
+            if (st != SC_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+            e = cudaGraphInstantiate(&exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+            if (ln.graphs.size() >= 8) {
+                auto it = std::min_element(ln.graphs.begin(), ln.graphs.end(),
+                                           [](const GraphEntry& a, const GraphEntry& b) {
+                                               return a.last < b.last;
+                                           });
+                cudaGraphExecDestroy(it->exec);
+                ln.graphs.erase(it);
+            }
+            ln.graphs.push_back({sig, exec, ++ctx->graph_tick});
+            ctx->graph_captures++;
+        }
+        SC_CUDA(cudaGraphLaunch(exec, ln.stream), "graph launch");
+    } else {
+        st = issue(ln.stream);
+        if (st != SC_OK) return st;
+    }
+    if (ctx->time_field) {
+        cudaEventRecord(f1, ln.stream);
+        ctx->pending.push_back({f0, f1});
+    }
+    ctx->ctr.launches += launches.size();
+    ctx->ctr.field_launches += launches.size();
+    const int r = sc::launch_reduce_batch((const sc::ReduceLaunch*)(arena + rl_off), (int)rls.size(),
+                                          roff, ln.stream);
+    if (r < 0) return cuda_fail(ctx, (cudaError_t)(-r), "reduce launch");
+    ctx->ctr.launches += r;
+    return SC_OK;
+}
+
+sc_status launch_chunks_direct(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch, float2* ws, size_t ws_n)
+{
+    const bool t = ctx->time_field;
+    ctx->time_field = false;
+    sc_status st = launch_chunks(ctx, ln, ch, ws, ws_n, false);
+    ctx->time_field = t;
+    return st;
+}
+
+// Run chunks in groups whose workspace fits under the cap.
+sc_status run_chunks(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch)
+{
+    const size_t cap = std::max<size_t>(ctx->ws_cap / sizeof(float2), 1);
+    size_t i = 0;
+    while (i < ch.size()) {
+        size_t j = i, tot = 0;
+        while (j < ch.size() && (j == i || tot + ch[j].ws_elems <= cap)) tot += ch[j++].ws_elems;
+        sc_status st = ensure(ctx, ln.ws, tot * sizeof(float2), ln.stream);
+        if (st != SC_OK) return st;
+        std::vector<Chunk> part(ch.begin() + i, ch.begin() + j);
+        st = launch_chunks(ctx, ln, part, (float2*)ln.ws.p, tot, ctx->use_graphs);
+        if (st != SC_OK) return st;
+        i = j;
+    }
+    return SC_OK;
+}
+
+void free_lane(Lane& ln)
+{
+    if (ln.stream) cudaStreamSynchronize(ln.stream);
+    for (DevBuf* b : {&ln.ws, &ln.desc, &ln.amp, &ln.kval})
+        if (b->p) {
+            cudaFree(b->p);
+            b->p = nullptr;
+            b->n = 0;
+        }
+    for (auto& g : ln.graphs) cudaGraphExecDestroy(g.exec);
+    ln.graphs.clear();
+    if (ln.cap_stream) cudaStreamDestroy(ln.cap_stream);
+    ln.cap_stream = nullptr;
+    if (ln.own_stream && ln.stream) cudaStreamDestroy(ln.stream);
+    ln.stream = nullptr;
+}
+
+}  // namespace sch
