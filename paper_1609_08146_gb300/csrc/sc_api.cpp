@@ -115,6 +115,7 @@ sc_status sc_create(int device, void* cuda_stream, size_t hbm_budget_bytes, sc_c
         cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         if (ctx->d_err) cudaFree(ctx->d_err);
+        if (ctx->h_err) cudaFreeHost(ctx->h_err);
         delete ctx;
         return SC_ERR_CUDA;
     }

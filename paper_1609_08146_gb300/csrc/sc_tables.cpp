@@ -817,10 +817,17 @@ sc_status get_table(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, 
         tp.n_rim = (int)hp[i].rim.size();
         t.parts.push_back(tp);
     }
-    SC_CUDA(cudaMemcpyAsync(t.d32, t32.data(), b32, cudaMemcpyHostToDevice, stream), "upload node tables");
-    SC_CUDA(cudaMemcpyAsync(t.d64, h64.data(), b64, cudaMemcpyHostToDevice, stream), "upload FP64 tables");
+    e = cudaMemcpyAsync(t.d32, t32.data(), b32, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t.d64, h64.data(), b64, cudaMemcpyHostToDevice, stream);
     // the host vectors die at return: make the copies complete first
-    SC_CUDA(cudaStreamSynchronize(stream), "node table upload");
+    const cudaError_t es = cudaStreamSynchronize(stream);
+    if (e == cudaSuccess) e = es;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(t.d32);
+        cudaFree(t.d64);
+        return cuda_fail(ctx, e, "node table upload");
+    }
     ctx->held += t.bytes;
     t.last_use = ctx->tick;
     ctx->tables.push_back(t);
