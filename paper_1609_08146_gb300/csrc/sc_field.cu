@@ -603,9 +603,10 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
 }
 
 // ------------------------------------------------------------------------
-// Direct kernel: n_omega <= 24.  GP threads per point (1, 2 or 4), each
-// owning NB = ceil(n_omega / GP) consecutive omegas (so no omega slot is
-// wasted beyond the last thread's); every thread computes the geometry and the
+// Direct kernel: n_omega <= 48.  GP threads per point (1, 2, 4 or 8), each
+// owning NB consecutive omegas (NB = ceil(n_omega / GP) up to 24 omegas, so
+// no omega slot is wasted beyond the last thread's; 8 for 25..32, 5 or 6 for
+// 33..48); every thread computes the geometry and the
 // phasors of its pairs itself (no pair table: with so few omegas per pair a
 // shared table would not pay for its producers), and the CTA shares the
 // bulk-copied node tiles.  256 threads, 256 / GP points per item.  The
@@ -788,13 +789,16 @@ int field_class(int n_omega)
     // 14     direct, 4 threads per point, NB = 8 (25..32 omegas; at two
     //        CTAs per SM it is 10% faster here than the grouped kernel with
     //        4 threads per point)
-    // 15..20 grouped, TPP = 8, 16, ..., 256 threads per point
+    // 15..16 direct, 8 threads per point, NB = 5, 6 (33..48 omegas, where
+    //        the grouped kernel would leave 2 or 3 of its 8 threads idle)
+    // 17..22 grouped, TPP = 8, 16, ..., 256 threads per point
     if (n_omega <= 8) return std::max(1, n_omega) - 1;
     if (n_omega <= 16) return 8 + (n_omega + 1) / 2 - 5;
     if (n_omega <= 24) return 12 + (n_omega + 3) / 4 - 5;
     if (n_omega <= 32) return 14;
+    if (n_omega <= 48) return 15 + (n_omega + 7) / 8 - 5;
     const int G = (n_omega + kB - 1) / kB;
-    int cls = 15, tpp = 8;
+    int cls = 17, tpp = 8;
     while (tpp < G) { tpp *= 2; ++cls; }
     return cls;
 }
@@ -828,11 +832,13 @@ void field_shape(int cls, int device, int* ppc, int* slots)
     case 12: return direct_shape<5, 4>(device, ppc, slots);
     case 13: return direct_shape<6, 4>(device, ppc, slots);
     case 14: return direct_shape<8, 4>(device, ppc, slots);
-    case 15: return grouped_shape<8>(device, ppc, slots);
-    case 16: return grouped_shape<16>(device, ppc, slots);
-    case 17: return grouped_shape<32>(device, ppc, slots);
-    case 18: return grouped_shape<64>(device, ppc, slots);
-    case 19: return grouped_shape<128>(device, ppc, slots);
+    case 15: return direct_shape<5, 8>(device, ppc, slots);
+    case 16: return direct_shape<6, 8>(device, ppc, slots);
+    case 17: return grouped_shape<8>(device, ppc, slots);
+    case 18: return grouped_shape<16>(device, ppc, slots);
+    case 19: return grouped_shape<32>(device, ppc, slots);
+    case 20: return grouped_shape<64>(device, ppc, slots);
+    case 21: return grouped_shape<128>(device, ppc, slots);
     default: return grouped_shape<256>(device, ppc, slots);
     }
 }
@@ -856,12 +862,14 @@ int launch_field_batch(int cls, const BatchLaunch& b, int grid, cudaStream_t s)
     case 12: return launch_direct<5, 4>(b, grid, s);
     case 13: return launch_direct<6, 4>(b, grid, s);
     case 14: return launch_direct<8, 4>(b, grid, s);
-    case 15: return launch_grouped<8>(b, grid, s);
-    case 16: return launch_grouped<16>(b, grid, s);
-    case 17: return launch_grouped<32>(b, grid, s);
-    case 18: return launch_grouped<64>(b, grid, s);
-    case 19: return launch_grouped<128>(b, grid, s);
-    case 20: return launch_grouped<256>(b, grid, s);
+    case 15: return launch_direct<5, 8>(b, grid, s);
+    case 16: return launch_direct<6, 8>(b, grid, s);
+    case 17: return launch_grouped<8>(b, grid, s);
+    case 18: return launch_grouped<16>(b, grid, s);
+    case 19: return launch_grouped<32>(b, grid, s);
+    case 20: return launch_grouped<64>(b, grid, s);
+    case 21: return launch_grouped<128>(b, grid, s);
+    case 22: return launch_grouped<256>(b, grid, s);
     default: return -(int)cudaErrorInvalidValue;
     }
 }

@@ -75,10 +75,10 @@ struct BatchLaunch {
     int* err;
 };
 
-// Kernel class for a chunk of n_omega (<= 2048) omegas: 0..13 the direct
-// kernel (1, 2 or 4 threads per point, 1..8 omegas per thread), 14..20 the
-// grouped kernel with 4 ... 256 threads per point.
-constexpr int kNumClasses = 21;
+// Kernel class for a chunk of n_omega (<= 2048) omegas: 0..16 the direct
+// kernel (1, 2, 4 or 8 threads per point, 1..8 omegas per thread, up to 48
+// omegas), 17..22 the grouped kernel with 8 ... 256 threads per point.
+constexpr int kNumClasses = 23;
 int field_class(int n_omega);
 // Observation points per work item and resident CTAs on the device.
 void field_shape(int cls, int device, int* points_per_item, int* resident_ctas);

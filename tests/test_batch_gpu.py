@@ -2,8 +2,8 @@
 
 A request's result must be bitwise the same alone (sc_eval) and inside a
 mixed batch (sc_eval_batch): its tiling depends only on its own shape and
-the reduction order is fixed.  Batches span both kernel families (up to 32
-omegas: the direct kernel with 1, 2 or 4 threads per point; more: grouped
+the reduction order is fixed.  Batches span both kernel families (up to 48
+omegas: the direct kernel with 1, 2, 4 or 8 threads per point; more: grouped
 kernels of 8..256 threads per point), several mirrors and beams, ragged point
 counts, and match the FP64 oracle.
 """
