@@ -110,6 +110,25 @@ sc_status choose_splits(sc_ctx* ctx, Lane& ln, Chunk& c, const Table* tab, int s
     return SC_OK;
 }
 
+// Omega count of the next chunk of a request with n omegas left.  A chunk is
+// at most 2048 omegas.  Above 64 the grouped kernel gives every point a
+// power of two threads of 8 omegas, so its capacity is the next power of two
+// cap >= n; a chunk that would leave more than a quarter of those slots idle
+// (n <= 3 cap / 4, e.g. 65..96 omegas on 16 threads) is cut to the full
+// cap / 2 instead, and the rest becomes a chunk of its own.  The cut depends
+// only on the request, so a request is chunked the same way alone or in a
+// batch.
+int next_chunk(int n)
+{
+    int c = std::min(n, 2048);
+    if (c > 64) {
+        int cap = 128;
+        while (cap < c) cap *= 2;
+        if (4 * c <= 3 * cap) c = cap / 2;
+    }
+    return c;
+}
+
 // Cut one request into chunks.  d_amp / d_k point at this request's a_n, k_n.
 sc_status plan_request(sc_ctx* ctx, Lane& ln, const Table* tab, const double* omegas, int n_omega,
                        double dom, const double* d_pts, int n_points, const double* d_amp,
@@ -119,10 +138,9 @@ sc_status plan_request(sc_ctx* ctx, Lane& ln, const Table* tab, const double* om
         return fail(ctx, SC_ERR_INVALID,
                     "this mirror and beam do not focus on the origin (e.g. a collimated beam on an "
                     "ellipsoid): the compensated FP32 phase does not apply, use SC_FP64");
-    const int max_om_chunk = 2048;
     const int flush_tiles = (int)std::max<long long>(1, ctx->flush_nodes / sc::kTile);
-    for (int o0 = 0; o0 < n_omega; o0 += max_om_chunk) {
-        const int no = std::min(max_om_chunk, n_omega - o0);
+    for (int o0 = 0, no = 0; o0 < n_omega; o0 += no) {
+        no = next_chunk(n_omega - o0);
         Chunk c;
         c.cls = sc::field_class(no);
         int slots = 1;

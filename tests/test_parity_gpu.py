@@ -115,11 +115,12 @@ def test_ragged_tiles_splits_groups(ctx, beam):
         ctx.set_option(sc.SC_OPT_FLUSH_NODES, 2048)
 
 
-@pytest.mark.parametrize("n_omega", [1, 2, 3, 4, 5, 6, 7, 8, 9, 11, 13, 16, 17, 21, 25, 32, 33, 40, 41, 48, 49, 64, 100,
-                                     256, 600])
+@pytest.mark.parametrize("n_omega", [1, 2, 3, 4, 5, 6, 7, 8, 9, 11, 13, 16, 17, 21, 25, 32, 33, 40, 41, 48, 49, 64, 65,
+                                     80, 100, 129, 200, 256, 600])
 def test_omega_counts(ctx, n_omega):
     # every kernel class: direct (<= 48 omegas; 1, 2, 4 or 8 threads per point
-    # with 1..8 omegas each) and grouped (8..256 threads per point)
+    # with 1..8 omegas each) and grouped (8..256 threads per point), and
+    # requests cut into a full grouped chunk and a rest (65, 80, 129, 200, 600)
     mirror = dict(f=62500.0, r_max=125000.0, n_r=24, n_theta=32, rim=True)
     beam = dict(profile="gauss", w0=37500.0, pol="linear")
     om = wl.uniform_omegas(n_omega)
