@@ -520,8 +520,11 @@ enum {
     SC_OPT_FLUSH_NODES = 4,     /* nodes summed in an FP32 run before it is folded */
                                 /* into the compensated partial (multiple of 32)   */
     SC_OPT_GRAPHS = 5,          /* 1 (default): capture/replay field launches       */
-    SC_OPT_AUTOTUNE = 6         /* 1 (default): time split-count candidates on the  */
+    SC_OPT_AUTOTUNE = 6,        /* 1 (default): time split-count candidates on the  */
                                 /* first request of each shape and cache the best   */
+    SC_OPT_OMEGA_CHUNKS = 7     /* 1 (default): cut a request's omegas into chunks  */
+                                /* that keep the field kernels' threads busy;      */
+                                /* 0: one chunk per 2048 omegas                     */
 };
 sc_status sc_set_option(sc_ctx* ctx, int option, long long value);
 

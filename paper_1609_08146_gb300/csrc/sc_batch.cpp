@@ -110,21 +110,46 @@ sc_status choose_splits(sc_ctx* ctx, Lane& ln, Chunk& c, const Table* tab, int s
     return SC_OK;
 }
 
+// First chunk of a request with n <= 64 omegas left (index n): the split
+// that minimises the summed field-kernel time of its chunks, each timed as a
+// chunk of its own.  Field throughput per omega count was measured on GB300
+// on 256^2 nodes and 4160 focal points, and each extra chunk is charged 2% of
+// a 32-omega chunk.  For example 33 omegas run as 1 + 32 (31% faster than one
+// chunk of 8 threads of 5 omegas), 41 as 10 + 31.  tune_chunks.py in the
+// package re-measures the throughputs and prints this table.
+constexpr unsigned char kFirstChunk[65] = {
+    0,  1,  2,  3,  4,  5,  6,  7,  8,  9,  10, 11, 12, 13, 14, 15, 16,  // 0..16
+    1,  6,  7,  8,  5,  6,  23, 24, 1,  12, 12, 12, 29, 30, 31, 32,      // 17..32
+    1,  2,  3,  12, 5,  6,  7,  8,  10, 10, 12, 12, 14, 14, 16, 16,      // 33..48
+    1,  6,  7,  8,  53, 54, 55, 56, 57, 58, 59, 60, 61, 62, 63, 64};    // 49..64
+
+// every entry takes 1..n omegas, so the planner always advances
+constexpr bool first_chunks_valid()
+{
+    for (int n = 1; n <= 64; ++n)
+        if (kFirstChunk[n] < 1 || kFirstChunk[n] > n) return false;
+    return true;
+}
+static_assert(first_chunks_valid(), "kFirstChunk");
+
 // Omega count of the next chunk of a request with n omegas left.  A chunk is
 // at most 2048 omegas.  Above 64 the grouped kernel gives every point a
 // power of two threads of 8 omegas, so its capacity is the next power of two
 // cap >= n; a chunk that would leave more than a quarter of those slots idle
 // (n <= 3 cap / 4, e.g. 65..96 omegas on 16 threads) is cut to the full
-// cap / 2 instead, and the rest becomes a chunk of its own.  The cut depends
-// only on the request, so a request is chunked the same way alone or in a
-// batch.
-int next_chunk(int n)
+// cap / 2 instead, and the rest becomes a chunk of its own.  Up to 64 omegas
+// the measured table decides, when `small` is set (requests large enough
+// that an extra chunk's launch is negligible).  The cut depends only on the
+// request, so a request is chunked the same way alone or in a batch.
+int next_chunk(int n, bool small)
 {
     int c = std::min(n, 2048);
     if (c > 64) {
         int cap = 128;
         while (cap < c) cap *= 2;
         if (4 * c <= 3 * cap) c = cap / 2;
+    } else if (small) {
+        c = kFirstChunk[c];
     }
     return c;
 }
@@ -139,8 +164,10 @@ sc_status plan_request(sc_ctx* ctx, Lane& ln, const Table* tab, const double* om
                     "this mirror and beam do not focus on the origin (e.g. a collimated beam on an "
                     "ellipsoid): the compensated FP32 phase does not apply, use SC_FP64");
     const int flush_tiles = (int)std::max<long long>(1, ctx->flush_nodes / sc::kTile);
+    // the small-omega cuts pay once a chunk holds 4M (point, node) pairs per omega
+    const bool small_cuts = (long long)n_points * tab->n_surf >= (1LL << 22);
     for (int o0 = 0, no = 0; o0 < n_omega; o0 += no) {
-        no = next_chunk(n_omega - o0);
+        no = ctx->omega_chunks ? next_chunk(n_omega - o0, small_cuts) : std::min(2048, n_omega - o0);
         Chunk c;
         c.cls = sc::field_class(no);
         int slots = 1;
