@@ -290,6 +290,23 @@ void sc_incident_free(sc_incident_t* inc);
 sc_status sc_table_count(sc_ctx* ctx, const sc_mirror_t* mirror, const sc_incident_t* inc, int* n_tables,
                          int* fp32_ok);
 
+/*
+ * How the FP32 path cuts a request of n_omega uniform omegas into chunks, on
+ * the host only (ctx may be NULL: planning on).  Each chunk is one pass of a
+ * field kernel over the node tables.  The sizes minimise the summed field
+ * time of the chunks under field throughputs per omega count measured on
+ * GB300, each extra chunk charged 2% of a 32-omega chunk: e.g. 65 omegas run
+ * as 64 + 1 (on 16 threads of 8 omegas, 7 would idle), 33 as 1 + 32.
+ * pairs_per_omega = points x surface nodes of the request; below 2^22 only
+ * full grouped capacities (64, 128, ... omegas) are cut off.  With
+ * SC_OPT_OMEGA_CHUNKS = 0 on ctx: one chunk per 2048 omegas.  Writes up to
+ * max_sizes chunk sizes in order and their count to *n_sizes.
+ * Errors: SC_ERR_INVALID (n_omega < 1, negative pairs, NULL n_sizes, or more
+ * chunks than max_sizes; *n_sizes is set in that case).
+ */
+sc_status sc_plan_omega_chunks(sc_ctx* ctx, int n_omega, long long pairs_per_omega, int* sizes, int max_sizes,
+                               int* n_sizes);
+
 /* Evaluate a_n (Eqs. 16 and 18) at n host omegas into host amp_re_im[2n]. */
 sc_status sc_spectrum_eval(sc_ctx* ctx, const sc_incident_t* inc, const double* omegas, int n,
                            double* amp_re_im);

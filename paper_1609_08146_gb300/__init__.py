@@ -119,6 +119,8 @@ SIGNATURES = {
     "sc_selftest_wait": (ctypes.c_int, [_VP]),
     "sc_get_counters": (ctypes.c_int, [_VP, ctypes.POINTER(sc_counters)]),
     "sc_measure_alu_peaks": (ctypes.c_int, [_VP, _DP, _DP, _DP]),
+    "sc_plan_omega_chunks": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "sc_reset_counters": (ctypes.c_int, [_VP]),
     "sc_set_option": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_longlong]),
 }
@@ -145,6 +147,18 @@ def load(path: str | None = None):
     _lib = lib
     globals().update({name: getattr(lib, name) for name in SIGNATURES})
     return lib
+
+
+def plan_omega_chunks(n_omega: int, pairs_per_omega: int, ctx=None):
+    """Omega chunk sizes the FP32 path uses for a request (no GPU needed)."""
+    lib = load()
+    sizes = (ctypes.c_int * (n_omega + 1))()
+    n = ctypes.c_int()
+    st = lib.sc_plan_omega_chunks(ctx._h if ctx is not None else None, int(n_omega), int(pairs_per_omega),
+                                  sizes, n_omega + 1, ctypes.byref(n))
+    if st != SC_OK:
+        raise ScError(st, "sc_plan_omega_chunks failed")
+    return list(sizes[: n.value])
 
 
 class ScError(RuntimeError):
@@ -474,6 +488,10 @@ class Context:
         a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         self._check(self._lib.sc_measure_alu_peaks(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return dict(fp32_lane_ops_per_s=a.value, fp32x2_lane_ops_per_s=b.value, mufu_ops_per_s=c.value)
+
+    def plan_omega_chunks(self, n_omega: int, pairs_per_omega: int):
+        """Omega chunk sizes of a request (host planning, see sc_plan_omega_chunks)."""
+        return plan_omega_chunks(n_omega, pairs_per_omega, self)
 
     def reset_counters(self):
         self._check(self._lib.sc_reset_counters(self._h))

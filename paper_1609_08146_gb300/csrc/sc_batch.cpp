@@ -110,49 +110,90 @@ sc_status choose_splits(sc_ctx* ctx, Lane& ln, Chunk& c, const Table* tab, int s
     return SC_OK;
 }
 
-// First chunk of a request with n <= 64 omegas left (index n): the split
-// that minimises the summed field-kernel time of its chunks, each timed as a
-// chunk of its own.  Field throughput per omega count was measured on GB300
-// on 256^2 nodes and 4160 focal points, and each extra chunk is charged 2% of
-// a 32-omega chunk.  For example 33 omegas run as 1 + 32 (31% faster than one
-// chunk of 8 threads of 5 omegas), 41 as 10 + 31.  tune_chunks.py in the
-// package re-measures the throughputs and prints this table.
-constexpr unsigned char kFirstChunk[65] = {
-    0,  1,  2,  3,  4,  5,  6,  7,  8,  9,  10, 11, 12, 13, 14, 15, 16,  // 0..16
-    1,  6,  7,  8,  5,  6,  23, 24, 1,  12, 12, 12, 29, 30, 31, 32,      // 17..32
-    1,  2,  3,  12, 5,  6,  7,  8,  10, 10, 12, 12, 14, 14, 16, 16,      // 33..48
-    1,  6,  7,  8,  53, 54, 55, 56, 57, 58, 59, 60, 61, 62, 63, 64};    // 49..64
+// Field-kernel throughput of one chunk, in 1e11 (point, node, omega)
+// evaluations per second, measured on GB300 on the broadband mirror and beam
+// at 256^2 nodes and 4160 focal points (tune_chunks.py in the package
+// re-measures both tables): every omega count 1..64, and full grouped chunks
+// of 64, 128, ..., 2048 omegas.  A grouped chunk of n > 64 omegas gives every
+// point a power of two threads of 8 omegas, so it takes as long as a full
+// chunk of its capacity (the next power of two >= n).
+constexpr double kRateSmall[65] = {
+    0.0,
+    3.493, 3.856, 4.961, 5.612, 6.351, 7.100, 7.120, 7.285,  // 1..8
+    6.465, 7.182, 7.520, 8.184, 7.379, 7.943, 7.926, 8.406,  // 9..16
+    6.345, 6.713, 7.084, 7.459, 7.204, 7.541, 7.889, 8.216,  // 17..24
+    6.810, 7.087, 7.357, 7.610, 7.889, 8.156, 8.436, 8.662,  // 25..32
+    6.196, 6.379, 6.571, 6.757, 6.941, 7.127, 7.309, 7.502,  // 33..40
+    7.144, 7.317, 7.493, 7.655, 7.839, 8.014, 8.174, 8.353,  // 41..48
+    7.578, 7.724, 7.884, 8.027, 8.185, 8.334, 8.488, 8.623,  // 49..56
+    8.752, 8.895, 9.050, 9.197, 9.357, 9.502, 9.650, 9.768}; // 57..64
+constexpr double kRateFull[6] = {9.782, 10.59, 11.10, 10.78, 10.99, 10.81};  // 64 .. 2048
 
-// every entry takes 1..n omegas, so the planner always advances
-constexpr bool first_chunks_valid()
+constexpr int kMaxChunk = 2048;
+
+// Relative field time of one chunk of c omegas (per point-node pair).
+double chunk_cost(int c)
 {
-    for (int n = 1; n <= 64; ++n)
-        if (kFirstChunk[n] < 1 || kFirstChunk[n] > n) return false;
-    return true;
+    if (c <= 64) return c / kRateSmall[c];
+    int cap = 128, i = 1;
+    while (cap < c) {
+        cap *= 2;
+        ++i;
+    }
+    return cap / kRateFull[i];
 }
-static_assert(first_chunks_valid(), "kFirstChunk");
 
-// Omega count of the next chunk of a request with n omegas left.  A chunk is
-// at most 2048 omegas.  Above 64 the grouped kernel gives every point a
-// power of two threads of 8 omegas, so its capacity is the next power of two
-// cap >= n; a chunk that would leave more than a quarter of those slots idle
-// (n <= 3 cap / 4, e.g. 65..96 omegas on 16 threads) is cut to the full
-// cap / 2 instead, and the rest becomes a chunk of its own.  Up to 64 omegas
-// the measured table decides, when `small` is set (requests large enough
-// that an extra chunk's launch is negligible).  The cut depends only on the
-// request, so a request is chunked the same way alone or in a batch.
+// The omega chunks of a request: for every n <= 2048 the split that
+// minimises the summed chunk times, charging each extra chunk 2% of a
+// 32-omega chunk, as the first chunk of that split (the rest is looked up
+// again).  Splits at any count up to 64 are allowed for requests large enough
+// that an extra chunk's launch does not matter (`small`); otherwise only
+// full grouped capacities (64, 128, ...) are cut off.  Computed once per
+// process from the tables above; the result depends only on the request.
+struct ChunkPlan {
+    unsigned short first[2][kMaxChunk + 1];
+};
+
+const ChunkPlan& chunk_plan()
+{
+    static const ChunkPlan plan = [] {
+        ChunkPlan p{};
+        std::vector<double> best(kMaxChunk + 1, 0.0);
+        const double extra = 0.02 * chunk_cost(32);
+        for (int small = 0; small < 2; ++small) {
+            for (int m = 1; m <= kMaxChunk; ++m) {
+                double b = chunk_cost(m);
+                int f = m;
+                auto consider = [&](int c) {
+                    const double v = chunk_cost(c) + best[m - c] + extra;
+                    if (v < b) {
+                        b = v;
+                        f = c;
+                    }
+                };
+                if (small)
+                    for (int c = 1; c <= std::min(m - 1, 64); ++c) consider(c);
+                else if (m > 64)
+                    consider(64);
+                for (int c = 128; c < m; c *= 2) consider(c);
+                best[m] = b;
+                p.first[small][m] = (unsigned short)f;
+            }
+        }
+        return p;
+    }();
+    return plan;
+}
+
+// Omega count of the next chunk of a request with n omegas left.
 int next_chunk(int n, bool small)
 {
-    int c = std::min(n, 2048);
-    if (c > 64) {
-        int cap = 128;
-        while (cap < c) cap *= 2;
-        if (4 * c <= 3 * cap) c = cap / 2;
-    } else if (small) {
-        c = kFirstChunk[c];
-    }
-    return c;
+    return chunk_plan().first[small ? 1 : 0][std::min(n, kMaxChunk)];
 }
+
+// requests of at least this many (point, node) pairs per omega take the
+// splits at small omega counts
+constexpr long long kSmallCutPairs = 1LL << 22;
 
 // Cut one request into chunks.  d_amp / d_k point at this request's a_n, k_n.
 sc_status plan_request(sc_ctx* ctx, Lane& ln, const Table* tab, const double* omegas, int n_omega,
@@ -164,10 +205,9 @@ sc_status plan_request(sc_ctx* ctx, Lane& ln, const Table* tab, const double* om
                     "this mirror and beam do not focus on the origin (e.g. a collimated beam on an "
                     "ellipsoid): the compensated FP32 phase does not apply, use SC_FP64");
     const int flush_tiles = (int)std::max<long long>(1, ctx->flush_nodes / sc::kTile);
-    // the small-omega cuts pay once a chunk holds 4M (point, node) pairs per omega
-    const bool small_cuts = (long long)n_points * tab->n_surf >= (1LL << 22);
+    const bool small_cuts = (long long)n_points * tab->n_surf >= kSmallCutPairs;
     for (int o0 = 0, no = 0; o0 < n_omega; o0 += no) {
-        no = ctx->omega_chunks ? next_chunk(n_omega - o0, small_cuts) : std::min(2048, n_omega - o0);
+        no = ctx->omega_chunks ? next_chunk(n_omega - o0, small_cuts) : std::min(kMaxChunk, n_omega - o0);
         Chunk c;
         c.cls = sc::field_class(no);
         int slots = 1;
@@ -415,3 +455,19 @@ void free_lane(Lane& ln)
 }
 
 }  // namespace sch
+
+extern "C" sc_status sc_plan_omega_chunks(sc_ctx* ctx, int n_omega, long long pairs_per_omega, int* sizes,
+                                          int max_sizes, int* n_sizes)
+{
+    if (n_omega < 1 || pairs_per_omega < 0 || !n_sizes || (max_sizes > 0 && !sizes))
+        return sch::fail(ctx, SC_ERR_INVALID, "invalid argument");
+    const bool plan = ctx ? ctx->omega_chunks : true;
+    const bool small = pairs_per_omega >= sch::kSmallCutPairs;
+    int k = 0;
+    for (int o0 = 0, no = 0; o0 < n_omega; o0 += no, ++k) {
+        no = plan ? sch::next_chunk(n_omega - o0, small) : std::min(sch::kMaxChunk, n_omega - o0);
+        if (k < max_sizes) sizes[k] = no;
+    }
+    *n_sizes = k;
+    return k <= max_sizes ? SC_OK : sch::fail(ctx, SC_ERR_INVALID, "%d chunks do not fit in %d entries", k, max_sizes);
+}

@@ -1,21 +1,31 @@
-"""Re-measure the small-omega chunk table of the FP32 path on this GPU.
+"""Re-measure the omega-chunk tables of the FP32 path on this GPU.
 
-For every omega count n = 1..64 it times the field kernel of one chunk of n
-uniform omegas (chunk planning off), on the broadband mirror and beam at
-256 x 256 nodes and 4160 focal points, then finds for every n the split into
-chunks that minimises the summed field time, charging each extra chunk 2% of
-a 32-omega chunk.  It prints the first chunk of each best split as the
-kFirstChunk table of csrc/sc_batch.cpp.
+The FP32 path cuts a request's uniform omega grid into chunks, each one pass
+of a field kernel over the node tables.  It chooses the cut that minimises
+the summed field time of the chunks, from the field throughput of one chunk
+of n omegas.  This tool measures that throughput with chunk planning off, on
+the broadband mirror and beam at 256 x 256 nodes and 4160 focal points:
+
+* for every n = 1..64;
+* for full grouped chunks of 64, 128, ..., 2048 omegas.  A grouped chunk of
+  n > 64 omegas takes as long as a full one of its capacity, the next power
+  of two >= n.
+
+It prints both tables in the form of csrc/sc_batch.cpp (kRateSmall,
+kRateFull), in units of 1e11 evaluations per second.  `first_chunks` is the
+same split search as the library's, written again here for the tests.
 
     python -m paper_1609_08146_gb300.tune_chunks
 """
 from __future__ import annotations
 
-import numpy as np
+MAX_CHUNK = 2048
+FULL = (64, 128, 256, 512, 1024, 2048)
 
 
-def measure(n_max: int = 64, reps: int = 3) -> dict:
-    """Field-kernel throughput (evals/s) of one chunk of n omegas."""
+def measure(reps: int = 3):
+    """(small, full): field throughput in 1e11 evals/s of one chunk of n
+    omegas, n = 1..64, and of full chunks of 64 .. 2048 omegas."""
     import torch
 
     import paper_1609_08146_gb300 as sc
@@ -30,8 +40,8 @@ def measure(n_max: int = 64, reps: int = 3) -> dict:
         inc = ctx.incident(profile=b["profile"], w0=b["w0"], pol=b["pol"], spectrum=w["spectrum"])
         pts = torch.tensor(w["points"], device="cuda")
         ctx.set_option(sc.SC_OPT_OMEGA_CHUNKS, 0)
-        rate = {}
-        for n in range(1, n_max + 1):
+
+        def rate(n):
             om = wl.uniform_omegas(n)
             for _ in range(2):
                 ctx.eval(mir, inc, om, pts)
@@ -42,32 +52,64 @@ def measure(n_max: int = 64, reps: int = 3) -> dict:
             c = ctx.counters()
             ctx.set_option(sc.SC_OPT_TIME_FIELD, 0)
             evals = reps * len(w["points"]) * m["n_r"] * m["n_theta"] * n
-            rate[n] = evals / (c["field_ms"] * 1e-3)
-        return rate
+            return evals / (c["field_ms"] * 1e-3) * 1e-11
+
+        small = [0.0] + [rate(n) for n in range(1, 65)]
+        full = [rate(n) for n in FULL]
+        return small, full
     finally:
         ctx.close()
 
 
-def first_chunks(rate: dict, penalty: float = 0.02) -> list:
-    """First chunk of the cheapest split of every n (index n; 0 unused)."""
-    n_max = max(rate)
-    cost = {c: c / rate[c] for c in rate}
-    extra = penalty * cost[32]
-    best = np.zeros(n_max + 1)
-    first = [0] * (n_max + 1)
-    for n in range(1, n_max + 1):
-        opts = [(cost[c] + best[n - c] + (extra if c < n else 0.0), c) for c in range(1, n + 1)]
-        best[n], first[n] = min(opts)  # ties: the smaller first chunk
+def chunk_cost(c: int, small, full) -> float:
+    """Relative field time of one chunk of c omegas."""
+    if c <= 64:
+        return c / small[c]
+    cap, i = 128, 1
+    while cap < c:
+        cap, i = cap * 2, i + 1
+    return cap / full[i]
+
+
+def first_chunks(small, full, small_cuts: bool = True, penalty: float = 0.02) -> list:
+    """First chunk of the cheapest split of every n <= 2048 (index n): splits
+    at any count up to 64 when small_cuts, else only at full grouped
+    capacities; each extra chunk costs `penalty` of a 32-omega chunk."""
+    extra = penalty * chunk_cost(32, small, full)
+    best = [0.0] * (MAX_CHUNK + 1)
+    first = [0] * (MAX_CHUNK + 1)
+    for m in range(1, MAX_CHUNK + 1):
+        b, f = chunk_cost(m, small, full), m
+        cands = list(range(1, min(m - 1, 64) + 1)) if small_cuts else ([64] if m > 64 else [])
+        c = 128
+        while c < m:
+            cands.append(c)
+            c *= 2
+        for c in cands:
+            v = chunk_cost(c, small, full) + best[m - c] + extra
+            if v < b:
+                b, f = v, c
+        best[m], first[m] = b, f
     return first
 
 
+def plan(n_omega: int, first: list) -> list:
+    """Chunk sizes of a request of n_omega omegas under a first-chunk table."""
+    out = []
+    while n_omega > 0:
+        c = first[min(n_omega, MAX_CHUNK)]
+        out.append(c)
+        n_omega -= c
+    return out
+
+
 def main():
-    rate = measure()
-    first = first_chunks(rate)
-    for n in sorted(rate):
-        print("%3d omegas: %.3e evals/s" % (n, rate[n]))
-    print("constexpr unsigned char kFirstChunk[65] = {")
-    print("    0, " + ", ".join(str(v) for v in first[1:]) + "};")
+    small, full = measure()
+    print("constexpr double kRateSmall[65] = {\n    0.0,")
+    for i in range(1, 65, 8):
+        print("    " + ", ".join("%.3f" % v for v in small[i:i + 8]) + ",  // %d..%d" % (i, i + 7))
+    print("};")
+    print("constexpr double kRateFull[6] = {" + ", ".join("%.4g" % v for v in full) + "};  // 64 .. 2048")
 
 
 if __name__ == "__main__":
