@@ -158,10 +158,11 @@ __device__ __forceinline__ float2 phasor_2wphi(float w_hi, float w_lo, float phi
 
 // The same phasor from the MUFU sine and cosine (__sincosf, absolute error
 // about 4e-7 on [-pi, pi], where the reduced argument pi r lies).  Used only
-// for a seed that multiplies one pair's terms once: its error does not
-// compound along the recurrence, unlike the rotation's, which stays on
-// sincospif.  In the direct kernel the seed is a large share of the per-pair
-// work; this makes its small-omega classes 2-27% faster.
+// for seeds, whose error is a constant factor on the phasors derived from
+// them: it does not compound along the recurrence, unlike the rotation's,
+// which stays on sincospif.  In the direct kernel the seed is a large share
+// of the per-pair work (its small-omega classes got 2-27% faster); in the
+// grouped kernel's producers the direct seed of every 32 groups (1-2%).
 __device__ __forceinline__ float2 phasor_2wphi_mufu(float w_hi, float w_lo, float phi)
 {
     const float a = 2.0f * w_hi;
@@ -537,8 +538,8 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
                     const int pq = q / L::TC, j = q % L::TC;
                     float co[10];
                     const float phi = pair_coefs(nb, sub * L::TC + j, spts[pq], co);
+                    const float2 rot = phasor_2wphi(d1h, d1l, phi);
                     if (seg == 0) {
-                        const float2 rot = phasor_2wphi(d1h, d1l, phi);
                         const float c2 = 2.f * rot.x;
                         float4* c4 = reinterpret_cast<float4*>(cb + (size_t)q * L::COEF);
                         c4[0] = make_float4(co[0], co[0], co[1], co[1]);
@@ -553,15 +554,14 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
                     const int g0 = seg * 32, g1 = min(G, g0 + 32);
                     if (g0 < g1) {
                         // e^{i 8 dk Phi} as the cube of squarings of e^{i dk Phi}
-                        float2 rotB = phasor_2wphi(d1h, d1l, phi);
-                        rotB = cmul(rotB, rotB);
+                        float2 rotB = cmul(rot, rot);
                         rotB = cmul(rotB, rotB);
                         rotB = cmul(rotB, rotB);
                         float2 sd = make_float2(1.f, 0.f);
                         for (int gg = g0; gg < g1; ++gg) {
                             if ((gg & 31) == 0) {  // one direct seed per 32 groups
                                 const float2 wv = soms[gg >> 4];
-                                sd = phasor_2wphi(wv.x, wv.y, phi);
+                                sd = phasor_2wphi_mufu(wv.x, wv.y, phi);
                             } else {
                                 sd = cmul(sd, rotB);
                             }
