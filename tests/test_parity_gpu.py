@@ -136,6 +136,27 @@ def test_omega_chunks_beyond_2048(ctx):
     check(ctx, mirror, beam, om, pts, fp64=False)
 
 
+def test_chunk_planning_on_and_off(ctx):
+    # 65 omegas: planned as 64 + 1 (grouped and direct kernels), or one chunk
+    # on 16 threads per point with SC_OPT_OMEGA_CHUNKS = 0; both within the
+    # gate against the oracle, and the plan reported for the context follows
+    # the option
+    mirror = dict(f=1000.0, r_max=2000.0, n_r=40, n_theta=48, rim=True)
+    beam = dict(profile="gauss", w0=600.0, pol="radial")
+    om = wl.uniform_omegas(65)
+    pts = wl.random_cube(30, 1.5, seed=65)
+    assert sorted(ctx.plan_omega_chunks(65, 1000)) == [1, 64]
+    e_on = check(ctx, mirror, beam, om, pts, fp64=False)
+    ctx.set_option(sc.SC_OPT_OMEGA_CHUNKS, 0)
+    try:
+        assert ctx.plan_omega_chunks(65, 1000) == [65]
+        assert ctx.plan_omega_chunks(5000, 1000) == [2048, 2048, 904]
+        e_off = check(ctx, mirror, beam, om, pts, fp64=False)
+    finally:
+        ctx.set_option(sc.SC_OPT_OMEGA_CHUNKS, 1)
+    assert max(e_on, e_off) <= TOL32
+
+
 def test_inner_rim_and_no_rim(ctx):
     beam = dict(profile="gauss", w0=300.0, pol="radial")
     om = np.linspace(0.8, 1.2, 20)
