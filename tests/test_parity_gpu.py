@@ -157,6 +157,21 @@ def test_chunk_planning_on_and_off(ctx):
     assert max(e_on, e_off) <= TOL32
 
 
+@pytest.mark.parametrize("n_omega", [17, 33, 41, 49])
+def test_small_count_cuts_on_a_large_request(ctx, n_omega):
+    # 64 x 64 nodes and 1030 points: above 4M pairs per omega, so small counts
+    # are cut too (e.g. 33 as 1 + 32); a sample of the points against the oracle
+    mirror = dict(f=1000.0, r_max=2000.0, n_r=64, n_theta=64, rim=True)
+    beam = dict(profile="supergauss", w0=1200.0, pol="azimuthal")
+    om = wl.uniform_omegas(n_omega)
+    pts = wl.random_cube(1030, 1.5, seed=n_omega)
+    assert len(ctx.plan_omega_chunks(n_omega, 1030 * 64 * 64)) > 1
+    E, B = run_gpu(ctx, mirror, beam, om, pts)
+    sel = np.arange(0, 1030, 26)
+    E0, B0 = run_oracle(mirror, beam, om, pts[sel])
+    assert max(rel_err(E[:, sel], E0), rel_err(B[:, sel], B0)) <= TOL32
+
+
 def test_inner_rim_and_no_rim(ctx):
     beam = dict(profile="gauss", w0=300.0, pol="radial")
     om = np.linspace(0.8, 1.2, 20)
