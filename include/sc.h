@@ -535,7 +535,8 @@ enum {
                                 /* to pick the split count for load balance       */
     SC_OPT_WORKSPACE_CAP = 3,   /* max workspace bytes per launch chunk           */
     SC_OPT_FLUSH_NODES = 4,     /* nodes summed in an FP32 run before it is folded */
-                                /* into the compensated partial (multiple of 32)   */
+                                /* into the compensated partial (multiple of 32;   */
+                                /* default 2048, at most 512 for beams fitted in k)*/
     SC_OPT_GRAPHS = 5,          /* 1 (default): capture/replay field launches       */
     SC_OPT_AUTOTUNE = 6,        /* 1 (default): time split-count candidates on the  */
                                 /* first request of each shape and cache the best   */

@@ -119,15 +119,15 @@ sc_status choose_splits(sc_ctx* ctx, Lane& ln, Chunk& c, const Table* tab, int s
 // chunk of its capacity (the next power of two >= n).
 constexpr double kRateSmall[65] = {
     0.0,
-    3.497, 3.859, 4.967, 5.614, 6.360, 7.100, 7.117, 7.291,  // 1..8
-    6.464, 7.176, 7.529, 8.196, 7.375, 7.942, 7.931, 8.413,  // 9..16
-    6.349, 6.717, 7.088, 7.463, 7.210, 7.547, 7.892, 8.219,  // 17..24
-    6.814, 7.089, 7.357, 7.610, 7.892, 8.165, 8.436, 8.669,  // 25..32
-    6.196, 6.379, 6.571, 6.757, 6.940, 7.126, 7.309, 7.500,  // 33..40
-    7.143, 7.317, 7.491, 7.658, 7.841, 8.016, 8.176, 8.353,  // 41..48
-    7.713, 7.863, 8.025, 8.171, 8.332, 8.482, 8.639, 8.777,  // 49..56
-    8.913, 9.057, 9.215, 9.364, 9.526, 9.675, 9.826, 9.947}; // 57..64
-constexpr double kRateFull[6] = {9.946, 10.75, 11.23, 10.89, 11.1, 10.9};  // 64 .. 2048
+    3.493, 3.856, 4.961, 5.612, 6.351, 7.100, 7.120, 7.285,  // 1..8
+    6.465, 7.182, 7.520, 8.184, 7.379, 7.943, 7.926, 8.406,  // 9..16
+    6.345, 6.713, 7.084, 7.459, 7.204, 7.541, 7.889, 8.216,  // 17..24
+    6.810, 7.087, 7.357, 7.610, 7.889, 8.156, 8.436, 8.662,  // 25..32
+    6.196, 6.379, 6.571, 6.757, 6.941, 7.127, 7.309, 7.502,  // 33..40
+    7.144, 7.317, 7.493, 7.655, 7.839, 8.014, 8.174, 8.353,  // 41..48
+    7.578, 7.724, 7.884, 8.027, 8.185, 8.334, 8.488, 8.623,  // 49..56
+    8.752, 8.895, 9.050, 9.197, 9.357, 9.502, 9.650, 9.768}; // 57..64
+constexpr double kRateFull[6] = {9.782, 10.59, 11.10, 10.78, 10.99, 10.81};  // 64 .. 2048
 
 constexpr int kMaxChunk = 2048;
 
@@ -195,6 +195,9 @@ int next_chunk(int n, bool small)
 // splits at small omega counts
 constexpr long long kSmallCutPairs = 1LL << 22;
 
+// FP32 run length of tables fitted in k (see plan_request)
+constexpr long long kFittedFlushNodes = 512;
+
 // Cut one request into chunks.  d_amp / d_k point at this request's a_n, k_n.
 sc_status plan_request(sc_ctx* ctx, Lane& ln, const Table* tab, const double* omegas, int n_omega,
                        double dom, const double* d_pts, int n_points, const double* d_amp,
@@ -204,7 +207,15 @@ sc_status plan_request(sc_ctx* ctx, Lane& ln, const Table* tab, const double* om
         return fail(ctx, SC_ERR_INVALID,
                     "this mirror and beam do not focus on the origin (e.g. a collimated beam on an "
                     "ellipsoid): the compensated FP32 phase does not apply, use SC_FP64");
-    const int flush_tiles = (int)std::max<long long>(1, ctx->flush_nodes / sc::kTile);
+    // Beams expanded in Chebyshev terms of k sum their parts with weights of
+    // alternating sign, which magnifies the FP32 rounding of each part's long
+    // runs: they fold every 512 nodes (the worst of 1240 seeded random
+    // configurations went from 9.7e-6 to 5.7e-6 of the 1e-5 gate).
+    long long flush_nodes = ctx->flush_nodes;
+    for (const auto& part : tab->parts)
+        if (part.kind == PART_CHEB_RE || part.kind == PART_CHEB_IM)
+            flush_nodes = std::min<long long>(flush_nodes, kFittedFlushNodes);
+    const int flush_tiles = (int)std::max<long long>(1, flush_nodes / sc::kTile);
     const bool small_cuts = (long long)n_points * tab->n_surf >= kSmallCutPairs;
     for (int o0 = 0, no = 0; o0 < n_omega; o0 += no) {
         no = ctx->omega_chunks ? next_chunk(n_omega - o0, small_cuts) : std::min(kMaxChunk, n_omega - o0);

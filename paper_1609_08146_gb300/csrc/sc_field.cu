@@ -158,11 +158,13 @@ __device__ __forceinline__ float2 phasor_2wphi(float w_hi, float w_lo, float phi
 
 // The same phasor from the MUFU sine and cosine (__sincosf, absolute error
 // about 4e-7 on [-pi, pi], where the reduced argument pi r lies).  Used only
-// for seeds, whose error is a constant factor on the phasors derived from
-// them: it does not compound along the recurrence, unlike the rotation's,
-// which stays on sincospif.  In the direct kernel the seed is a large share
-// of the per-pair work (its small-omega classes got 2-27% faster); in the
-// grouped kernel's producers the direct seed of every 32 groups (1-2%).
+// for the direct kernel's seed, whose error is a constant factor on the
+// phasors derived from it: it does not compound along the recurrence, unlike
+// the rotation's, which stays on sincospif.  There the seed is a large share
+// of the per-pair work (the small-omega classes got 2-27% faster).  The
+// grouped kernel keeps sincospif for its seeds: with a MUFU seed one
+// Laguerre-Gauss configuration of the seeded random tests went from under
+// 5e-6 to 1.005e-5 of the gate metric, for 1.2% of speed.
 __device__ __forceinline__ float2 phasor_2wphi_mufu(float w_hi, float w_lo, float phi)
 {
     const float a = 2.0f * w_hi;
@@ -561,7 +563,7 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
                         for (int gg = g0; gg < g1; ++gg) {
                             if ((gg & 31) == 0) {  // one direct seed per 32 groups
                                 const float2 wv = soms[gg >> 4];
-                                sd = phasor_2wphi_mufu(wv.x, wv.y, phi);
+                                sd = phasor_2wphi(wv.x, wv.y, phi);
                             } else {
                                 sd = cmul(sd, rotB);
                             }
