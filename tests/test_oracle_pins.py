@@ -132,6 +132,112 @@ def test_paraboloid_focus_without_rim_term():
     assert abs(E[0] - Ex) < 1e-11 * abs(Ex)
 
 
+# --------------------------------------------------------------------------
+# Annulus r_min <= r <= r_max: Eq. 11's line integral runs over all of the
+# boundary, so an annulus has an inner rim too.  Stokes' theorem orients it
+# opposite to the outer one, which makes the annulus exactly the disk of
+# radius a minus the disk of radius b, each with its own rim term: the inner
+# rim of the annulus is the reversed outer rim of the disk b.
+
+
+def _disk_focus_linear(f, a, k):
+    """(E_x, B_y) at the focus of the top-hat x-polarised plane wave on the
+    paraboloid cut to 0 <= r <= a, rim term included (closed form above)."""
+    Ra = f + a * a / (4 * f)
+    Ex = 2 * (1j * k * f + 1) * (1 - f / Ra) - (1 - f * f / Ra ** 2) - (a * a / (2 * Ra ** 2)) * (
+        1 + 1j / (k * Ra))
+    By = 2j * k * f * (1 - f / Ra) - (1 - f * f / Ra ** 2)
+    return Ex, By
+
+
+def _inner_rim_share(mirror, beam, omegas, pts, form="stokes"):
+    """The inner rim's contribution to E, isolated from the oracle's own
+    outputs: (annulus with rim - without) - (disk with rim - without)."""
+    e = [oracle.field(dict(mirror, r_min=rm, rim=rim), beam, omegas, pts, form=form)[0]
+         for rm in (mirror["r_min"], 0.0) for rim in (1, 0)]
+    return (e[0] - e[1]) - (e[2] - e[3])
+
+
+@pytest.mark.parametrize("f,b,a,omega", [(20.0, 8.0, 30.0, 1.0), (5.0, 2.0, 10.0, 0.7),
+                                         (50.0, 20.0, 60.0, 1.4)])
+def test_annulus_focus_linear_tophat(f, b, a, omega):
+    """E_x(annulus) = E_x(disk a) - E_x(disk b), rims included; so is B_y.
+    A reversed inner rim would add twice the disk-b rim share
+    (b^2/R_b^2)(1 + i/(kR_b)), 7e-4 to 7e-3 of E_x in these cases."""
+    k = K0 * omega
+    m = dict(f=f, r_min=b, r_max=a, n_r=160, n_theta=64, rim=1)
+    beam = dict(profile="tophat", pol="linear", w0=1.01 * a)
+    E, B = _focus(m, beam, omega)
+    Ea, Ba = _disk_focus_linear(f, a, k)
+    Eb, Bb = _disk_focus_linear(f, b, k)
+    Ex, By = Ea - Eb, Ba - Bb
+    scale = abs(Ex)
+    assert abs(E[0] - Ex) < 1e-11 * scale
+    assert abs(B[1] - By) < 1e-11 * scale
+    for v in (E[1], E[2], B[0], B[2]):
+        assert abs(v) < 1e-12 * scale
+    Rb = f + b * b / (4 * f)
+    flipped = Ex + (b * b / Rb ** 2) * (1 + 1j / (k * Rb))
+    assert abs(flipped - Ex) > 1e-4 * scale  # the pin separates the two orientations
+
+
+def test_annulus_focus_radial_tophat():
+    """Radial polarisation on an annulus: E_z = E_z(disk a) - E_z(disk b)
+    with the closed form of the radial test below, rims included."""
+    f, b, a, om = 20.0, 9.0, 30.0, 1.3
+    w0 = 1.01 * a
+    k = K0 * om
+
+    def disk(r):
+        Rr = f + r * r / (4 * f)
+        L = math.log(Rr / f)
+        return (4 * f / w0) * (2j * k * f * (L - 1 + f / Rr) + L - 2 + 3 * f / Rr - f * f / Rr ** 2) - (
+            1 + 1j / (k * Rr)) * (Rr - 2 * f) * r * r / (Rr * Rr * w0)
+
+    m = dict(f=f, r_min=b, r_max=a, n_r=160, n_theta=64, rim=1)
+    E, B = _focus(m, dict(profile="tophat", pol="radial", w0=w0), om)
+    Ez = disk(a) - disk(b)
+    assert abs(E[2] - Ez) < 1e-11 * abs(Ez)
+    for v in (E[0], E[1], B[0], B[1], B[2]):
+        assert abs(v) < 1e-12 * abs(Ez)
+
+
+def test_annulus_stokes_form_equals_double_gradient_form():
+    """Eq. 11 = Eq. 10 on an annulus for a plane wave: Eq. 10 has no line
+    term, so the equality needs both rims with Stokes' orientation."""
+    m = dict(f=8.0, r_min=4.0, r_max=12.0, n_r=96, n_theta=96, rim=1)
+    b = dict(profile="tophat", pol="linear", w0=20.0, pol_angle=0.4)
+    pts = np.random.default_rng(7).uniform(-1.5, 1.5, size=(6, 3))
+    E1, B1 = oracle.field(m, b, [0.9], pts, form="stokes")
+    E2, B2 = oracle.field(m, b, [0.9], pts, form="dyadic")
+    scale = np.max(np.abs(E1))
+    assert np.max(np.abs(E1 - E2)) < 1e-9 * scale
+    assert np.max(np.abs(B1 - B2)) == 0.0
+    inner = _inner_rim_share(m, b, [0.9], pts)
+    assert np.max(np.abs(inner)) > 1e-3 * scale  # the inner rim matters here ...
+    assert np.max(np.abs(E1 - 2 * inner - E2)) > 1e-3 * scale  # ... and reversing it fails
+
+
+def test_annulus_ampere_and_divergence_for_plane_wave():
+    """curl B' = -ik E' and div E' = 0 on an annulus: Eq. 11's surface term
+    alone is not divergence-free; its boundary terms, inner rim included with
+    Stokes' orientation, make it so."""
+    f, om = 8.0, 1.1
+    k = K0 * om
+    m = dict(f=f, r_min=3.0, r_max=10.0, n_r=64, n_theta=64, rim=1)
+    b = dict(profile="tophat", pol="linear", w0=20.0)
+    p0, h = [0.23, 0.11, -0.19], 2e-3
+    E, B, cE, cB, dE = _curl(m, b, om, p0, h)
+    assert np.linalg.norm(cB + 1j * k * E) / np.linalg.norm(k * E) < 1e-7
+    assert abs(dE) / (k * np.linalg.norm(E)) < 1e-7
+    # the same with the inner rim reversed: E - 2 (inner share); B is unchanged
+    parts = [_curl(dict(m, r_min=rm, rim=rim), b, om, p0, h) for rm in (3.0, 0.0) for rim in (1, 0)]
+    inner = [(parts[0][i] - parts[1][i]) - (parts[2][i] - parts[3][i]) for i in range(5)]
+    Ef, cBf, dEf = E - 2 * inner[0], cB - 2 * inner[3], dE - 2 * inner[4]
+    assert np.linalg.norm(cBf + 1j * k * Ef) / np.linalg.norm(k * Ef) > 1e-3
+    assert abs(dEf) / (k * np.linalg.norm(Ef)) > 1e-3
+
+
 def test_paraboloid_focus_radial_tophat():
     """Radial polarisation (rho/w0) rho_hat: only E_z survives at the focus,
     E_z = (4f/w0)[2ikf(L - 1 + f/R_a) + L - 2 + 3f/R_a - f^2/R_a^2]
