@@ -88,11 +88,22 @@ const char* sc_last_error(const sc_ctx* ctx);
 /* ---------------------------------------------------------------------- */
 /* Mirror (Sec. III.A; Sec. III.C.1, Eq. 21 and the quadrature it names)    */
 
-enum { SC_QUAD_GAUSS_LEGENDRE = 0 };
+/*
+ * Radial rule on [r_min, r_max] (Sec. III.C.1 names "Simpson or
+ * Gauss-Legendre"; the angular rule is always the periodic trapezoid):
+ *   SC_QUAD_GAUSS_LEGENDRE  n_r >= 1 Gauss-Legendre nodes (exact for
+ *                           polynomials of degree 2 n_r - 1);
+ *   SC_QUAD_SIMPSON         composite Simpson, n_r odd >= 3 equally spaced
+ *                           nodes r_i = r_min + i h, h = (r_max - r_min) /
+ *                           (n_r - 1), both ends included, weights h/3 (1, 4,
+ *                           2, 4, ..., 2, 4, 1) (exact for cubics, error
+ *                           O(h^4)).  A node at r = 0 carries zero weight.
+ */
+enum { SC_QUAD_GAUSS_LEGENDRE = 0, SC_QUAD_SIMPSON = 1 };
 
 typedef struct {
-    int radial_kind; /* SC_QUAD_GAUSS_LEGENDRE: n_r nodes in r on [r_min, r_max]      */
-    int n_r;         /* >= 1                                                          */
+    int radial_kind; /* SC_QUAD_GAUSS_LEGENDRE or SC_QUAD_SIMPSON (above)             */
+    int n_r;         /* >= 1 (Gauss-Legendre), odd >= 3 (Simpson)                     */
     int n_theta;     /* >= 1, periodic trapezoid theta_l = 2 pi l / n_theta           */
     int rim_term;    /* 1: include the boundary line integral of Eq. 11 (outer rim,   */
                      /*    and the inner rim when r_min > 0)                          */
@@ -102,7 +113,8 @@ typedef struct {
  * Describe the paraboloid z = r^2/(4f) - f (focus at the origin) cut to
  * r_min <= r <= r_max, and the quadrature used on it.
  * Errors: SC_ERR_INVALID when f <= 0, r_min < 0, r_min >= r_max, n_r < 1,
- * n_theta < 1 or an unknown radial_kind.  The handle is host-side only;
+ * n_theta < 1, an unknown radial_kind, or SC_QUAD_SIMPSON with an even n_r
+ * or n_r < 3.  The handle is host-side only;
  * device tables are built lazily per (mirror, incident) pair by sc_eval.
  */
 /*

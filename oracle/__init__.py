@@ -53,6 +53,7 @@ class _Mirror(ctypes.Structure):
         ("r_max", ctypes.c_double),
         ("c_ell", ctypes.c_double),
         ("e_ell", ctypes.c_double),
+        ("radial", ctypes.c_int),
     ]
 
 
@@ -106,6 +107,7 @@ def _load():
         build()
         lib = ctypes.CDLL(_LIB)
         lib.or_gauss_legendre.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _DP, _DP]
+        lib.or_simpson.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _DP, _DP]
         lib.or_zernike.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
         lib.or_zernike.restype = ctypes.c_double
         lib.or_beam_power.argtypes = [ctypes.POINTER(_Beam)]
@@ -140,6 +142,7 @@ def _mirror(m: dict) -> _Mirror:
         f=float(m.get("f", 1.0)), z0=float(m.get("z0", 0.0)),
         r_min=float(m.get("r_min", 0.0)), r_max=float(m["r_max"]),
         c_ell=float(m.get("c", 0.0)), e_ell=float(m.get("e", 0.0)),
+        radial={"gauss_legendre": 0, "simpson": 1}[m.get("radial", "gauss_legendre")],
     )
 
 
@@ -173,6 +176,15 @@ def gauss_legendre(n: int, a: float = -1.0, b: float = 1.0):
     w = np.zeros(n)
     if _load().or_gauss_legendre(n, a, b, _ptr(x), _ptr(w)) != 0:
         raise ValueError("n must be >= 1")
+    return x, w
+
+
+def simpson(n: int, a: float = -1.0, b: float = 1.0):
+    """Composite Simpson nodes and weights on [a, b] (n odd >= 3)."""
+    x = np.zeros(n)
+    w = np.zeros(n)
+    if _load().or_simpson(n, a, b, _ptr(x), _ptr(w)) != 0:
+        raise ValueError("n must be odd and >= 3")
     return x, w
 
 

@@ -23,7 +23,8 @@
  *     inverse transform, per-component amplitude from a power spectrum
  *     (Eq. 16) and a spectral phase map (Eq. 18).
  *   - Sec. III.C.1, Eq. 21: the paraboloid z = r^2/(4f) - f with its focus at
- *     the origin; Sec. III.C.1: tensor-product Gauss-Legendre quadrature.
+ *     the origin; Sec. III.C.1: tensor-product quadrature, Gauss-Legendre or
+ *     composite Simpson in r (the two rules it names), trapezoid in theta.
  *   - Sec. IV.B, Eq. 27: super-Gaussian power spectrum in wavelength.
  *
  * Readings of passages the paper leaves open (its Supplementary Material,
@@ -109,7 +110,7 @@ typedef double complex cplx;
 
 typedef struct {
     int surface;      /* 0: paraboloid z = r^2/(4f) - f; 1: flat disk z = z0 */
-    int n_r;          /* Gauss-Legendre nodes in r on [r_min, r_max]          */
+    int n_r;          /* nodes in r on [r_min, r_max] (rule: `radial` below)  */
     int n_theta;      /* trapezoid nodes in theta, theta_l = 2 pi l / n_theta  */
     int rim;          /* 1: include the boundary line integral of Eq. 11      */
     double f;         /* focal length                                          */
@@ -117,6 +118,7 @@ typedef struct {
     double r_min;
     double r_max;
     double c_ell, e_ell; /* ellipsoid (surface 2): semi-axis along z, focal half-distance */
+    int radial;       /* radial rule: 0 Gauss-Legendre, 1 composite Simpson (n_r odd)   */
 } or_mirror;
 
 typedef struct {
@@ -180,6 +182,28 @@ int or_gauss_legendre(int n, double a, double b, double* x, double* w)
         int k = n - 1 - i;
         x[k] = 0.5 * (a + b) + 0.5 * (b - a) * t;
         w[k] = 0.5 * (b - a) * wi;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Composite Simpson rule on [a, b] (the other rule Sec. III.C.1 names): the */
+/* n = 2m + 1 equally spaced nodes form m panels of two intervals, and each  */
+/* panel [x_2p, x_2p+2] adds Simpson's (h/3)(f_2p + 4 f_2p+1 + f_2p+2).      */
+
+int or_simpson(int n, double a, double b, double* x, double* w)
+{
+    if (n < 3 || n % 2 == 0) return 1;
+    const int intervals = n - 1;
+    const double h = (b - a) / intervals;
+    for (int i = 0; i < n; ++i) {
+        x[i] = a + (b - a) * ((double)i / intervals);
+        w[i] = 0.0;
+    }
+    for (int panel = 0; 2 * panel + 2 < n; ++panel) {
+        w[2 * panel] += h / 3.0;
+        w[2 * panel + 1] += 4.0 * h / 3.0;
+        w[2 * panel + 2] += h / 3.0;
     }
     return 0;
 }
@@ -657,9 +681,11 @@ int or_field(const or_mirror* m, const or_beam* bm, int form, int n_omega, const
         return 1;
     if (bm->order >= 1 && bm->profile >= 2) return 1; /* needs a smooth real profile (R14) */
     if (bm->profile == 4 && !bm->env_fn) return 1;
+    if (m->radial != 0 && (m->radial != 1 || m->n_r < 3 || m->n_r % 2 == 0)) return 1;
     double* gl_r = (double*)malloc(sizeof(double) * m->n_r);
     double* gl_w = (double*)malloc(sizeof(double) * m->n_r);
-    or_gauss_legendre(m->n_r, m->r_min, m->r_max, gl_r, gl_w);
+    if (m->radial == 1) or_simpson(m->n_r, m->r_min, m->r_max, gl_r, gl_w);
+    else or_gauss_legendre(m->n_r, m->r_min, m->r_max, gl_r, gl_w);
     /* profiles 3 and 4: the envelope at every (omega, node), sampled up front
      * on this thread (a caller's function is not called from worker threads) */
     const long n_s = (long)m->n_r * m->n_theta, n_rim = 2L * m->n_theta, n_nd = n_s + n_rim;

@@ -178,12 +178,16 @@ def _addr(x):
     return x.data_ptr()
 
 
+RADIAL_RULES = {"gauss_legendre": 0, "simpson": 1}
+
+
 class Mirror:
-    def __init__(self, ctx, f, r_min, r_max, n_r, n_theta, rim=True, ellipsoid=None):
+    def __init__(self, ctx, f, r_min, r_max, n_r, n_theta, rim=True, ellipsoid=None, radial="gauss_legendre"):
         """Paraboloid of focal length f, or with ellipsoid=(c, e) the ellipsoidal
-        cap of semi-axis c and focal half-distance e (f is then c - e)."""
+        cap of semi-axis c and focal half-distance e (f is then c - e).
+        radial: "gauss_legendre" (n_r >= 1) or "simpson" (odd n_r >= 3)."""
         self._lib = ctx._lib
-        q = sc_quadrature(0, int(n_r), int(n_theta), 1 if rim else 0)
+        q = sc_quadrature(RADIAL_RULES[radial], int(n_r), int(n_theta), 1 if rim else 0)
         h = _VP()
         if ellipsoid is None:
             ctx._check(self._lib.sc_mirror(ctx._h, float(f), float(r_min), float(r_max), ctypes.byref(q),
@@ -194,6 +198,7 @@ class Mirror:
                                                      ctypes.byref(q), ctypes.byref(h)))
         self._h = h
         self.f, self.r_min, self.r_max, self.n_r, self.n_theta, self.rim = f, r_min, r_max, n_r, n_theta, rim
+        self.radial = radial
 
     @property
     def n_nodes(self):
@@ -285,11 +290,11 @@ class Context:
     def __del__(self):
         self.close()
 
-    def mirror(self, f, r_min, r_max, n_r, n_theta, rim=True) -> Mirror:
-        return Mirror(self, f, r_min, r_max, n_r, n_theta, rim)
+    def mirror(self, f, r_min, r_max, n_r, n_theta, rim=True, radial="gauss_legendre") -> Mirror:
+        return Mirror(self, f, r_min, r_max, n_r, n_theta, rim, radial=radial)
 
-    def ellipsoid(self, c, e, r_min, r_max, n_r, n_theta, rim=True) -> Mirror:
-        return Mirror(self, c - e, r_min, r_max, n_r, n_theta, rim, ellipsoid=(c, e))
+    def ellipsoid(self, c, e, r_min, r_max, n_r, n_theta, rim=True, radial="gauss_legendre") -> Mirror:
+        return Mirror(self, c - e, r_min, r_max, n_r, n_theta, rim, ellipsoid=(c, e), radial=radial)
 
     def incident(self, **kw) -> Incident:
         return Incident(self, **kw)

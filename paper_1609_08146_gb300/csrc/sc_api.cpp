@@ -148,13 +148,24 @@ const char* sc_last_error(const sc_ctx* ctx)
     return ctx ? ctx->err.c_str() : "null context";
 }
 
+namespace {
+
+// n_r >= 1 Gauss-Legendre nodes, or an odd n_r >= 3 for composite Simpson
+bool quadrature_ok(const sc_quadrature* q)
+{
+    if (q->n_r < 1 || q->n_theta < 1) return false;
+    if (q->radial_kind == SC_QUAD_GAUSS_LEGENDRE) return true;
+    return q->radial_kind == SC_QUAD_SIMPSON && q->n_r >= 3 && (q->n_r & 1) == 1;
+}
+
+}  // namespace
+
 sc_status sc_mirror(sc_ctx* ctx, double f, double r_min, double r_max, const sc_quadrature* q,
                     sc_mirror_t** out)
 {
     if (!out || !q) return fail(ctx, SC_ERR_INVALID, "null argument");
     *out = nullptr;
-    if (!(f > 0.0) || !(r_min >= 0.0) || !(r_max > r_min) || q->n_r < 1 || q->n_theta < 1 ||
-        q->radial_kind != SC_QUAD_GAUSS_LEGENDRE)
+    if (!(f > 0.0) || !(r_min >= 0.0) || !(r_max > r_min) || !quadrature_ok(q))
         return fail(ctx, SC_ERR_INVALID,
                     "invalid mirror (f=%g r_min=%g r_max=%g n_r=%d n_theta=%d kind=%d)", f, r_min,
                     r_max, q->n_r, q->n_theta, q->radial_kind);
@@ -174,7 +185,7 @@ sc_status sc_mirror_ellipsoid(sc_ctx* ctx, double c, double e, double r_min, dou
     if (!out || !q) return fail(ctx, SC_ERR_INVALID, "null argument");
     *out = nullptr;
     if (!(e > 0.0) || !(c > e) || !(r_min >= 0.0) || !(r_max > r_min) || !(r_max * r_max < c * c - e * e) ||
-        q->n_r < 1 || q->n_theta < 1 || q->radial_kind != SC_QUAD_GAUSS_LEGENDRE)
+        !quadrature_ok(q))
         return fail(ctx, SC_ERR_INVALID, "invalid ellipsoidal mirror (c=%g e=%g r_min=%g r_max=%g)", c, e, r_min,
                     r_max);
     sc_mirror_t* m = new sc_mirror_t();

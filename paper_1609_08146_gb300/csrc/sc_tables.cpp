@@ -1,5 +1,5 @@
 // sc_tables.cpp -- the FP64 host side of the node tables (A1) and spectra (A2):
-// Gauss-Legendre quadrature, the incident field on the mirror (Sec. III.A),
+// radial quadrature, the incident field on the mirror (Sec. III.A),
 // the spectrum (Sec. III.B, Eqs. 14-18; Sec. IV.B, Eq. 27), mirror surfaces,
 // the node-table builder and cache, and context helpers (errors, events).
 #include <math.h>
@@ -51,6 +51,27 @@ void gauss_legendre(int n, double a, double b, std::vector<double>& x, std::vect
         x[j] = 0.5 * (b + a) + 0.5 * (b - a) * t;
         w[j] = (b - a) / ((1.0 - t * t) * d * d);
     }
+}
+
+// Composite Simpson on [a, b] with n = 2m + 1 equally spaced nodes: weight
+// h/3 at the ends, 4h/3 at odd and 2h/3 at interior even nodes.
+void simpson(int n, double a, double b, std::vector<double>& x, std::vector<double>& w)
+{
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    const double h = (b - a) / (n - 1);
+    for (int i = 0; i < n; ++i) {
+        x[i] = i == n - 1 ? b : a + i * h;
+        const double c = (i == 0 || i == n - 1) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+        w[i] = c * h / 3.0;
+    }
+}
+
+// The mirror's radial rule on [r_min, r_max] (Sec. III.C.1).
+void radial_rule(const sc_mirror_t* m, std::vector<double>& x, std::vector<double>& w)
+{
+    if (m->q.radial_kind == SC_QUAD_SIMPSON) simpson(m->q.n_r, m->r_min, m->r_max, x, w);
+    else gauss_legendre(m->q.n_r, m->r_min, m->r_max, x, w);
 }
 
 // Zernike Z_j (Noll ordering and normalisation): radial order n and
@@ -354,7 +375,7 @@ void build_nodes(const sc_mirror_t* m, const sc_incident_t* in, std::vector<Host
     const int nr = m->q.n_r, nt = m->q.n_theta;
     const bool first = in->order >= 1;
     std::vector<double> gr, gw;
-    gauss_legendre(nr, m->r_min, m->r_max, gr, gw);
+    radial_rule(m, gr, gw);
     const double dth = 2.0 * kPi / nt;
     // E~, B~ of the first table at (r, th), z components included
     auto fields = [&](double r, double th, double e[3], double bv[3]) {
@@ -457,7 +478,7 @@ sc_status build_cheb_parts(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_
     const double f = m->f;
     const int nr = m->q.n_r, nt = m->q.n_theta;
     std::vector<double> gr, gw;
-    gauss_legendre(nr, m->r_min, m->r_max, gr, gw);
+    radial_rule(m, gr, gw);
     const double dth = 2.0 * kPi / nt;
     // node positions: surface (r_i, theta_l), then the rim edges
     struct Pos { double r, th; int edge; };
@@ -639,7 +660,7 @@ sc_status build_dipole_parts(sc_ctx* ctx, const sc_mirror_t* m, const sc_inciden
         return fail(ctx, SC_ERR_INVALID, "a dipole source needs an ellipsoidal mirror (it sits at its focus F1)");
     const int nr = m->q.n_r, nt = m->q.n_theta;
     std::vector<double> gr, gw;
-    gauss_legendre(nr, m->r_min, m->r_max, gr, gw);
+    radial_rule(m, gr, gw);
     const double dth = 2.0 * kPi / nt;
     const double* p = in->dip;
     parts.assign(3, HostPart());

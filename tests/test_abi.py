@@ -41,6 +41,15 @@ def test_host_validation_without_gpu():
     assert lib.sc_mirror(None, 1.0, 0.0, 1.0, ctypes.byref(bad), ctypes.byref(h)) == sc.SC_ERR_INVALID
     assert lib.sc_mirror(None, 1.0, 0.0, 2.0, ctypes.byref(q), ctypes.byref(h)) == sc.SC_OK
     lib.sc_mirror_free(h)
+    # composite Simpson (Sec. III.C.1) needs an odd node count >= 3
+    for n_r, want in ((3, sc.SC_OK), (9, sc.SC_OK), (1, sc.SC_ERR_INVALID), (8, sc.SC_ERR_INVALID)):
+        qs = sc.sc_quadrature(sc.RADIAL_RULES["simpson"], n_r, 8, 1)
+        assert lib.sc_mirror(None, 1.0, 0.0, 2.0, ctypes.byref(qs), ctypes.byref(h)) == want, n_r
+        assert lib.sc_mirror_ellipsoid(None, 14.0, 6.0, 0.0, 2.0, ctypes.byref(qs), ctypes.byref(h)) == want
+        if want == sc.SC_OK:
+            lib.sc_mirror_free(h)
+    unknown = sc.sc_quadrature(2, 9, 8, 1)
+    assert lib.sc_mirror(None, 1.0, 0.0, 2.0, ctypes.byref(unknown), ctypes.byref(h)) == sc.SC_ERR_INVALID
     prof = sc.sc_profile(0, -1.0, 4, 0, None)
     pol = sc.sc_polarization(0, 0.0)
     spec = sc.sc_spectrum(0, 1.0, 1.0, 0.1, 3, 1.0, 0, None, None, 0, None)

@@ -47,6 +47,58 @@ def test_gauss_legendre_exact_degree():
     assert abs(np.dot(w, x ** d) - exact) > 1e-10  # and not degree 2n
 
 
+def test_simpson_exact_for_cubics():
+    # composite Simpson integrates x^d exactly for d <= 3, and not x^4
+    a, b = 0.3, 2.9
+    for n in (3, 5, 11):
+        x, w = oracle.simpson(n, a, b)
+        assert abs(x[0] - a) < 1e-15 and abs(x[-1] - b) < 1e-15
+        assert np.max(np.abs(np.diff(x, 2))) < 1e-14  # equally spaced
+        for d in range(4):
+            exact = (b ** (d + 1) - a ** (d + 1)) / (d + 1)
+            assert abs(np.dot(w, x ** d) - exact) < 1e-13 * max(1.0, abs(exact))
+        exact = (b ** 5 - a ** 5) / 5
+        assert abs(np.dot(w, x ** 4) - exact) > 1e-8
+
+
+def test_simpson_is_richardson_of_trapezoid():
+    """Simpson on 2m intervals = (4 T_h - T_2h) / 3, T the composite trapezoid
+    (the textbook identity, independent of the panel weights)."""
+    a, b, n = -0.4, 1.7, 13
+    x, w = oracle.simpson(n, a, b)
+    rng = np.random.default_rng(3)
+    for _ in range(3):
+        fx = rng.standard_normal(n)
+        h = (b - a) / (n - 1)
+        t_h = h * (fx.sum() - 0.5 * (fx[0] + fx[-1]))
+        f2 = fx[::2]
+        t_2h = 2 * h * (f2.sum() - 0.5 * (f2[0] + f2[-1]))
+        assert abs(np.dot(w, fx) - (4 * t_h - t_2h) / 3) < 1e-13
+    with pytest.raises(ValueError):
+        oracle.simpson(4)
+
+
+def test_simpson_mirror_converges_at_fourth_order():
+    """Eq. 11 with Simpson in r (Sec. III.C.1 names Simpson or Gauss-Legendre)
+    tends to the focal closed form with error ~ h^4: halving h divides it by
+    16 (measured 16.0-16.3), on a disk and on an annulus."""
+    f, a, om = 20.0, 30.0, 1.0
+    k = K0 * om
+    beam = dict(profile="tophat", pol="linear", w0=1.01 * a)
+    for b in (0.0, 8.0):
+        Ea, _ = _disk_focus_linear(f, a, k)
+        Eb, _ = _disk_focus_linear(f, b, k) if b > 0 else (0.0, 0.0)
+        want = Ea - Eb
+        errs = []
+        for n in (9, 17, 33, 65):
+            m = dict(f=f, r_min=b, r_max=a, n_r=n, n_theta=16, rim=1, radial="simpson")
+            E, _ = _focus(m, beam, om)
+            errs.append(abs(E[0] - want) / abs(want))
+        ratios = [errs[i] / errs[i + 1] for i in range(3)]
+        assert all(14.0 < r < 18.5 for r in ratios), ratios
+        assert errs[-1] < 2e-8
+
+
 def test_zernike_noll_table():
     # Noll (1976), Table 1: explicit low orders
     r, t = 0.63, 0.41

@@ -54,10 +54,11 @@ def unit_spectrum(omegas):
 
 def run_gpu(ctx, mirror, beam, omegas, pts, precision="fp32", spectrum=None):
     m = ctx.mirror(mirror["f"], mirror.get("r_min", 0.0), mirror["r_max"], mirror["n_r"],
-                   mirror["n_theta"], rim=bool(mirror.get("rim", True)))
+                   mirror["n_theta"], rim=bool(mirror.get("rim", True)),
+                   radial=mirror.get("radial", "gauss_legendre"))
     inc = ctx.incident(profile=beam["profile"], w0=beam["w0"], sg_order=beam.get("sg_order", 4),
                        zernike=beam.get("zernike", []), pol=beam.get("pol", "linear"),
-                       pol_angle=beam.get("pol_angle", 0.0),
+                       pol_angle=beam.get("pol_angle", 0.0), order=beam.get("order", 0),
                        spectrum=spectrum or unit_spectrum(omegas))
     P = torch.tensor(np.asarray(pts, float), device="cuda")
     E, B = ctx.eval(m, inc, omegas, P, precision=precision)
@@ -178,6 +179,50 @@ def test_inner_rim_and_no_rim(ctx):
     pts = wl.random_cube(20, 1.5, seed=3)
     check(ctx, dict(f=500.0, r_min=150.0, r_max=900.0, n_r=32, n_theta=48, rim=True), beam, om, pts)
     check(ctx, dict(f=500.0, r_min=150.0, r_max=900.0, n_r=32, n_theta=48, rim=False), beam, om, pts)
+
+
+@pytest.mark.parametrize(
+    "mirror,beam",
+    [
+        # disk: the node row at r = 0 has zero weight
+        (dict(f=500.0, r_max=900.0, n_r=41, n_theta=48, rim=True, radial="simpson"),
+         dict(profile="gauss", w0=400.0, pol="linear", pol_angle=0.2)),
+        # annulus, both rims, aberrated radial beam
+        (dict(f=500.0, r_min=150.0, r_max=900.0, n_r=33, n_theta=48, rim=True, radial="simpson"),
+         dict(profile="supergauss", sg_order=4, w0=500.0, pol="radial", zernike=[0.1, -0.2, 0.05, 0.1])),
+        # first-order beam (second node table) through r = 0
+        (dict(f=40.0, r_max=60.0, n_r=45, n_theta=40, rim=True, radial="simpson"),
+         dict(profile="gauss", w0=12.0, pol="azimuthal", order=1)),
+    ],
+)
+def test_simpson_radial_rule(ctx, mirror, beam):
+    """Composite Simpson in r (Sec. III.C.1 names Simpson or Gauss-Legendre):
+    the same sum on both sides, FP32 and FP64 against the oracle, over
+    ragged tiles and omega groups (13 omegas)."""
+    om = wl.uniform_omegas(13)
+    pts = np.vstack([np.zeros((1, 3)), wl.random_cube(20, 1.5, seed=41)])
+    check(ctx, mirror, beam, om, pts, fp64=False)
+    E0, B0 = run_oracle(mirror, beam, om, pts)
+    E, B = run_gpu(ctx, mirror, beam, om, pts, "fp64")
+    # the first-order oracle takes its divergences by finite differences (1e-11)
+    tol = 1e-11 if beam.get("order", 0) else tol64(mirror, om)
+    assert max(rel_err(E, E0), rel_err(B, B0)) <= tol
+
+
+def test_simpson_focus_closed_form_on_gpu(ctx):
+    """Simpson in r on the GPU tends to the hand-derived focal value of Eq. 11
+    at fourth order: the FP64 path's error falls 16x per halving of h."""
+    f, a, om = 20.0, 30.0, np.array([1.0])
+    k = 2 * math.pi
+    Ra = f + a * a / (4 * f)
+    Ex = 2 * (1j * k * f + 1) * (1 - f / Ra) - (1 - f * f / Ra ** 2) - (a * a / (2 * Ra ** 2)) * (
+        1 + 1j / (k * Ra))
+    errs = []
+    for n in (9, 17, 33):
+        E, _ = run_gpu(ctx, dict(f=f, r_max=a, n_r=n, n_theta=16, rim=True, radial="simpson"),
+                       dict(profile="tophat", w0=1.01 * a, pol="linear"), om, np.zeros((1, 3)), "fp64")
+        errs.append(abs(E[0, 0, 0] - Ex) / abs(Ex))
+    assert 14.0 < errs[0] / errs[1] < 18.5 and 14.0 < errs[1] / errs[2] < 18.5, errs
 
 
 def test_point_chunking_small_workspace(ctx):
