@@ -398,11 +398,13 @@ sc_status sc_eval_time_domain(sc_ctx* ctx, const sc_mirror_t* mirror, const sc_i
 /*
  * Allocation-free variant of sc_eval for the SC_FP32_COMP path.  The paper
  * has no counterpart: this entry point exists for callers that cannot call
- * cudaMalloc while they evaluate -- code running inside a global-mode stream
- * capture, services that hand all device memory to their own pools up front,
- * or real-time loops that forbid allocation.  It allocates nothing: no
- * cudaMalloc, no cudaFree, no allocating library routine.  Its split
- * partials live in a fixed 64 MiB static device array of the library
+ * cudaMalloc while they evaluate -- services that hand all device memory to
+ * their own pools at start-up (an allocation would fail or escape their
+ * accounting), and real-time or latency-bound loops that forbid cudaMalloc
+ * and cudaFree because those calls can block on the whole device.  It
+ * allocates nothing: no cudaMalloc, no cudaFree, no allocating library
+ * routine, and it copies nothing from the host.  The wavenumbers k_n and the
+ * split partials live in a fixed 64 MiB static device array of the library
  * (SC_STATIC_SCRATCH_BYTES), which every GPU that loads the library holds
  * until the process exits.
  *   Preconditions: the node table of (mirror, inc) is already resident in
@@ -411,17 +413,23 @@ sc_status sc_eval_time_domain(sc_ctx* ctx, const sc_mirror_t* mirror, const sc_i
  *   gives 1 table and fp32_ok 1: a collimated beam of order 0 on the
  *   paraboloid).  Other pairs are rejected with SC_ERR_INVALID: use sc_eval.
  *   omega_n = omega0 + n * domega, n < n_omega (<= 2048), omega0 > 0.
- *   amp_re_im   host, [n_omega][2], e.g. from sc_spectrum_eval.
+ *   amp_re_im   device, [n_omega][2] doubles, caller-owned (e.g. filled from
+ *               sc_spectrum_eval); read by the call's kernels.
  *   points_xyz  device, [n_points][3] doubles.
  *   E_out,B_out device, [n_omega][n_points][3] float2 pairs; B_out may be NULL.
- * The scratch needed is 2 x 96 x n_points x n_omega bytes plus 24 x n_omega;
- * larger requests are rejected with SC_ERR_INVALID and a message giving the
- * limit.  The first call on a device looks up the array's device address
- * (which may load the module): make that first call before any stream
- * capture.  Every call shares the array and leaves its contents behind; each
- * call writes every partial before reading it, so nothing needs clearing,
- * but calls whose GPU work overlaps (other streams, other contexts on the
- * same device) race on it.  Asynchronous on the context stream.
+ * A host pointer in any of these is rejected with SC_ERR_INVALID.  The
+ * scratch needed is 2 x 96 x n_points x n_omega bytes plus 8 x n_omega
+ * (rounded up to 256); larger requests are rejected with SC_ERR_INVALID and
+ * a message giving the limit.  The first call on a device looks up the
+ * array's device address (which may load the library's module) and leaves
+ * the caller's current device as it was.  Every call shares the array and
+ * leaves its contents behind; each call writes every value it later reads,
+ * so nothing needs clearing, but calls whose GPU work overlaps (other
+ * streams, other contexts on the same device) race on it.  Asynchronous on
+ * the context stream: as for sc_eval with device buffers and no stats, a
+ * bounded device wait that runs out is reported as SC_ERR_TIMEOUT by the
+ * context's next call that synchronizes (sc_get_counters, or an sc_eval
+ * with stats).
  * Errors: SC_ERR_INVALID, SC_ERR_CUDA.
  */
 #define SC_STATIC_SCRATCH_BYTES ((size_t)64 << 20)

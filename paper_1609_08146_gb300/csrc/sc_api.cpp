@@ -669,18 +669,23 @@ sc_status sc_eval_fp32_static(sc_ctx* ctx, const sc_mirror_t* m, const sc_incide
                               double omega0, double domega, int n_omega, const double* amp_re_im,
                               const double* points_xyz, int n_points, void* E_out, void* B_out)
 {
-    // No device allocation on this path: the table must already be resident,
-    // a_n and k_n travel through the static scratch, and so do the partials.
+    // No device allocation and no host-to-device copy on this path: the table
+    // must already be resident, a_n is the caller's device array, and k_n and
+    // the split partials live in the static scratch.
     constexpr int kMaxOmega = 2048;
     if (!ctx) return SC_ERR_INVALID;
     if (!m || !in || !amp_re_im || !points_xyz || !E_out || n_points < 1 || n_omega < 1)
         return fail(ctx, SC_ERR_INVALID, "invalid argument");
+    if (!is_device_ptr(amp_re_im) || !is_device_ptr(points_xyz) || !is_device_ptr(E_out) ||
+        (B_out && !is_device_ptr(B_out)))
+        return fail(ctx, SC_ERR_INVALID,
+                    "amp_re_im, points_xyz, E_out and B_out must be device memory on this path");
     if (n_omega > kMaxOmega)
         return fail(ctx, SC_ERR_INVALID, "n_omega %d exceeds %d for the static-scratch path", n_omega,
                     kMaxOmega);
     if (!(omega0 > 0.0) || !(domega >= 0.0) || (n_omega > 1 && !(domega > 0.0)))
         return fail(ctx, SC_ERR_INVALID, "omega grid must be positive and increasing");
-    const size_t header = (size_t)n_omega * 3 * sizeof(double);   // a_n (2) and k_n (1)
+    const size_t header = (size_t)n_omega * sizeof(double);   // k_n
     const size_t header_al = (header + 255) / 256 * 256;
     const size_t ws_bytes = (size_t)2 * n_points * n_omega * sc::kAcc * sizeof(float2);
     if (header_al + ws_bytes > sc::kStaticScratchBytes)
@@ -704,17 +709,10 @@ sc_status sc_eval_fp32_static(sc_ctx* ctx, const sc_mirror_t* m, const sc_incide
     cudaError_t e = sc::static_scratch(ctx->device, &scratch);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "static scratch address");
     SC_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
-    double hdr[3 * kMaxOmega];
-    for (int i = 0; i < n_omega; ++i) {
-        hdr[2 * i] = amp_re_im[2 * i];
-        hdr[2 * i + 1] = amp_re_im[2 * i + 1];
-        hdr[2 * n_omega + i] = 2.0 * kPi * (omega0 + i * domega);
-    }
-    double* d_amp = (double*)scratch;
-    double* d_k = d_amp + 2 * (size_t)n_omega;
-    // pageable source: the call returns once the bytes are staged
-    SC_CUDA(cudaMemcpyAsync(d_amp, hdr, header, cudaMemcpyHostToDevice, ctx->stream),
-            "upload a_n, k_n");
+    double* d_k = (double*)scratch;
+    int r = sc::launch_kgrid(d_k, omega0, domega, n_omega, ctx->stream);
+    if (r < 0) return cuda_fail(ctx, (cudaError_t)(-r), "k grid kernel launch");
+    ctx->ctr.launches += r;
     float2* ws = (float2*)((unsigned char*)scratch + header_al);
     sc::FieldLaunch f;
     f.nodes = tab->d32;
@@ -732,7 +730,7 @@ sc_status sc_eval_fp32_static(sc_ctx* ctx, const sc_mirror_t* m, const sc_incide
     f.dom_lo = (float)(domega - (double)f.dom_hi);
     f.ws = ws;
     f.err = ctx->d_err;
-    int r = sc::launch_field_f32(f, ctx->stream);
+    r = sc::launch_field_f32(f, ctx->stream);
     if (r < 0) return cuda_fail(ctx, (cudaError_t)(-r), "field kernel launch");
     ctx->ctr.launches += r;
     ctx->ctr.field_launches += 1;
@@ -741,7 +739,7 @@ sc_status sc_eval_fp32_static(sc_ctx* ctx, const sc_mirror_t* m, const sc_incide
     rl.n_splits = 1;
     rl.n_pts = n_points;
     rl.n_omega = n_omega;
-    rl.amp = d_amp;
+    rl.amp = amp_re_im;
     rl.kval = d_k;
     rl.out_pt_stride_omega = (long long)n_points * 3;
     rl.E = (float2*)E_out;

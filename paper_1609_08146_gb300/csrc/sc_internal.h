@@ -155,5 +155,7 @@ int alu_probe_grid(int kind, int device);  // resident 512-thread blocks on all 
 // `device` (looked up once per device with that device current).
 constexpr size_t kStaticScratchBytes = size_t(64) << 20;
 cudaError_t static_scratch(int device, void** ptr);
+// writes k_n = 2 pi (omega0 + n domega), n < count, into device memory k
+int launch_kgrid(double* k, double omega0, double domega, int count, cudaStream_t s);
 
 }  // namespace sc

@@ -6,6 +6,8 @@ mistake in it cannot hide under the tolerance of the whole field: it is
 O(eps) of the field, eps = lambda / (pi w0), and the cases use eps of a few
 per cent.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -106,7 +108,9 @@ def test_static_path_rejects_first_order(ctx):
     pts = torch.zeros((4, 3), dtype=torch.float64, device="cuda")
     ctx.eval(m, inc, [1.0], pts)  # makes the tables resident
     E = torch.empty((1, 4, 3), dtype=torch.complex64, device="cuda")
-    amp = np.array([1.0, 0.0])
-    st = ctx._lib.sc_eval_fp32_static(ctx._h, m._h, inc._h, 1.0, 0.0, 1, amp.ctypes.data_as(sc._DP),
+    amp = torch.tensor([1.0, 0.0], dtype=torch.float64, device="cuda")
+    st = ctx._lib.sc_eval_fp32_static(ctx._h, m._h, inc._h, 1.0, 0.0, 1,
+                                      ctypes.cast(amp.data_ptr(), sc._DP),
                                       sc._VP(pts.data_ptr()), 4, sc._VP(E.data_ptr()), None)
     assert st == sc.SC_ERR_INVALID
+    assert b"node tables" in ctx._lib.sc_last_error(ctx._h)
