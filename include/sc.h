@@ -560,9 +560,15 @@ enum {
     SC_OPT_GRAPHS = 5,          /* 1 (default): capture/replay field launches       */
     SC_OPT_AUTOTUNE = 6,        /* 1 (default): time split-count candidates on the  */
                                 /* first request of each shape and cache the best   */
-    SC_OPT_OMEGA_CHUNKS = 7     /* 1 (default): cut a request's omegas into chunks  */
+    SC_OPT_OMEGA_CHUNKS = 7,    /* 1 (default): cut a request's omegas into chunks  */
                                 /* that keep the field kernels' threads busy;      */
                                 /* 0: one chunk per 2048 omegas                     */
+    SC_OPT_FAIL_COPY = 8        /* failure-path test, -1 (default) off: in every   */
+                                /* batched FP32 field launch, the work item 0 skips */
+                                /* the bulk copy of its node tile `value`, so the   */
+                                /* wait for that tile runs out (no fault, no copy   */
+                                /* in flight); the launch then stops and the call   */
+                                /* reports SC_ERR_TIMEOUT                           */
 };
 sc_status sc_set_option(sc_ctx* ctx, int option, long long value);
 

@@ -31,7 +31,7 @@ PROFILES = {"gauss": 0, "supergauss": 1, "tophat": 2, "laguerre_gauss": 3, "enve
 POLS = {"linear": 0, "radial": 1, "azimuthal": 2}
 SPECTRA = {"mono": 0, "gauss_time": 1, "supergauss_lambda": 2, "sampled": 3}
 SC_OPT_TIME_FIELD, SC_OPT_NODES_PER_SPLIT, SC_OPT_WORKSPACE_CAP, SC_OPT_FLUSH_NODES = 1, 2, 3, 4
-SC_OPT_GRAPHS, SC_OPT_AUTOTUNE, SC_OPT_OMEGA_CHUNKS = 5, 6, 7
+SC_OPT_GRAPHS, SC_OPT_AUTOTUNE, SC_OPT_OMEGA_CHUNKS, SC_OPT_FAIL_COPY = 5, 6, 7, 8
 
 _DP = ctypes.POINTER(ctypes.c_double)
 _VP = ctypes.c_void_p

@@ -1110,6 +1110,10 @@ sc_status sc_set_option(sc_ctx* ctx, int option, long long value)
         if (value < (1 << 20)) return fail(ctx, SC_ERR_INVALID, "workspace cap below 1 MiB");
         ctx->ws_cap = (size_t)value;
         return SC_OK;
+    case SC_OPT_FAIL_COPY:
+        if (value < -1 || value > (1 << 30)) return fail(ctx, SC_ERR_INVALID, "tile index out of range");
+        ctx->fail_tile = (int)value;
+        return SC_OK;
     default: return fail(ctx, SC_ERR_INVALID, "unknown option %d", option);
     }
 }

@@ -310,7 +310,7 @@ sc_status launch_chunks(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch, float2* w
         }
     std::vector<sc::ReduceLaunch> rls;
     for (auto& c : ch) rls.push_back(c.rl);
-    // arena: queues (64 B each) | WorkReq arrays | ReduceLaunch array
+    // arena: queues and abort words (64 B per class) | WorkReq arrays | ReduceLaunch array
     size_t bytes = kClasses * 64;
     size_t req_off[kClasses];
     for (int k = 0; k < kClasses; ++k) {
@@ -340,7 +340,9 @@ sc_status launch_chunks(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch, float2* w
         b.n_req = (int)reqs[k].size();
         b.n_items = items[k];
         b.queue = (int*)(arena + 64 * k);
+        b.abort = b.queue + 1;  // the launch's abort word, reset with its queue
         b.err = ctx->d_err;
+        b.fail_tile = ctx->fail_tile;
         launches.push_back({k, b, (int)std::min<long long>(slots, items[k])});
     }
     auto issue = [&](cudaStream_t s) -> sc_status {

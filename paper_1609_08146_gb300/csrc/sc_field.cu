@@ -110,12 +110,17 @@ __device__ __forceinline__ uint64_t global_ns()
 }
 
 // Bounded wait on phase `parity`: gives up after about one second of wall
-// time (or kSpinLimit polls) and returns false, so a copy or a hand-over that
-// never lands turns into an error flag instead of a hung kernel.  Each poll
-// may suspend the warp for up to kSuspendNs until the phase completes, and
-// the clock is read only every 64 polls, so waiting warps take few issue
-// slots from working ones.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity)
+// time (or kSpinLimit polls) and returns WAIT_EXPIRED, so a copy or a
+// hand-over that never lands turns into an error flag instead of a hung
+// kernel.  With an abort flag (the CTA's shared word, set by the first of its
+// waits that expires) the wait also returns WAIT_ABORTED as soon as the flag
+// is set, so one expired wait ends every later one at once.  Each poll may
+// suspend the warp for up to kSuspendNs until the phase completes, and the
+// clock is read only every 64 polls, so waiting warps take few issue slots
+// from working ones.
+enum : int { WAIT_ABORTED = -1, WAIT_EXPIRED = 0, WAIT_DONE = 1 };
+
+__device__ __forceinline__ int mbar_wait(uint64_t* bar, unsigned parity, const volatile int* abort = nullptr)
 {
     const uint32_t addr = smem_u32(bar);
     uint64_t t0 = 0;
@@ -128,14 +133,35 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity)
             : "=r"(done)
             : "r"(addr), "r"(parity), "n"(kSuspendNs)
             : "memory");
-        if (done) return true;
+        if (done) return WAIT_DONE;
+        if (abort && *abort) return WAIT_ABORTED;
         if ((it & 63) == 0) {
             const uint64_t now = global_ns();
             if (it == 0) t0 = now;
-            else if (now - t0 > kWaitNs) return false;
+            else if (now - t0 > kWaitNs) return WAIT_EXPIRED;
         }
     }
-    return false;
+    return WAIT_EXPIRED;
+}
+
+// A main-loop wait of a field kernel: on expiry latch the CTA's abort flag
+// and the launch's, and note the timeout for the error word.
+__device__ __forceinline__ int field_wait(uint64_t* bar, unsigned parity, volatile int* s_abort, int* launch_abort,
+                                          bool& timed_out)
+{
+    const int w = mbar_wait(bar, parity, s_abort);
+    if (w == WAIT_EXPIRED) {
+        *s_abort = 1;
+        timed_out = true;
+        if (launch_abort) atomicExch(launch_abort, 1);
+    }
+    return w;
+}
+
+// Failure-path test hook: leave this copy unissued (see BatchLaunch).
+__device__ __forceinline__ bool skip_copy(const BatchLaunch& b, long long item, int tile)
+{
+    return b.fail_tile >= 0 && item == 0 && tile == b.fail_tile;
 }
 
 // ------------------------------------------------------------------------
@@ -323,12 +349,17 @@ __device__ __forceinline__ const WorkReq* find_req(const BatchLaunch& b, long lo
     return &b.reqs[lo];
 }
 
-// next item for the whole CTA (thread 0 takes it, everyone reads it)
-__device__ __forceinline__ long long next_item(const BatchLaunch& b, long long* slot, long long prev)
+// next item for the whole CTA (thread 0 takes it, everyone reads it); none
+// once this CTA or another of the launch has aborted on an expired wait
+__device__ __forceinline__ long long next_item(const BatchLaunch& b, long long* slot, long long prev,
+                                               const volatile int* s_abort)
 {
     __syncthreads();  // everyone is done with the previous item (and its slot value)
-    if (threadIdx.x == 0)
-        *slot = b.queue ? (long long)atomicAdd(b.queue, 1) : (prev < 0 ? (long long)blockIdx.x : b.n_items);
+    if (threadIdx.x == 0) {
+        const bool stop = *s_abort || (b.abort && *(const volatile int*)b.abort);
+        *slot = stop ? b.n_items
+                     : (b.queue ? (long long)atomicAdd(b.queue, 1) : (prev < 0 ? (long long)blockIdx.x : b.n_items));
+    }
     __syncthreads();
     return *slot;
 }
@@ -387,7 +418,7 @@ struct Grouped {
     static constexpr size_t OFF_OMS = OFF_PTS + PPC * 16;
     static constexpr size_t NOMS = (TPP + 15) / 16;  // omegas of every 16th group (every 32nd used)
     static constexpr size_t OFF_BAR = (OFF_OMS + NOMS * 8 + 15) / 16 * 16;
-    static constexpr size_t SMEM = OFF_BAR + 7 * 8;  // node[2], full[2], empty[2], item slot
+    static constexpr size_t SMEM = OFF_BAR + 8 * 8;  // node[2], full[2], empty[2], item slot, abort
     static_assert(SMEM <= 227 * 1024, "shared memory");
     static_assert(NC % TPP == 0 && kTile % TC == 0, "shape");
 };
@@ -406,6 +437,7 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
     uint64_t* full = nbar + 2;
     uint64_t* empty = nbar + 4;
     long long* slot = reinterpret_cast<long long*>(nbar + 6);
+    volatile int* s_abort = reinterpret_cast<volatile int*>(nbar + 7);
 
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -415,12 +447,14 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
         mbar_init(&full[1], L::NPROD);
         mbar_init(&empty[0], L::NC / 32);
         mbar_init(&empty[1], L::NC / 32);
+        *s_abort = 0;
         mbar_fence_init();
     }
     bool timed_out = false;
     long long cbase = 0, tbase = 0;  // compute tiles and node tiles done by this CTA
 
-    for (long long item = next_item(b, slot, -1); item < b.n_items; item = next_item(b, slot, item)) {
+    for (long long item = next_item(b, slot, -1, s_abort); item < b.n_items;
+         item = next_item(b, slot, item, s_abort)) {
         const Item w = decode(b, item);
         const FieldLaunch& p = w.r->f;
         const int p0 = w.pbi * L::PPC;
@@ -465,7 +499,9 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
             for (int c = 0; c < nct; ++c) {
                 const long long cg = cbase + c;
                 const int pb = (int)(cg & 1);
-                if (!mbar_wait(&full[pb], (unsigned)((cg >> 1) & 1))) timed_out = true;
+                // after an abort this wait returns at once and the rest of the
+                // item (microseconds of work on stale tables) is discarded
+                field_wait(&full[pb], (unsigned)((cg >> 1) & 1), s_abort, b.abort, timed_out);
                 const float* cb = coefbuf + (size_t)pb * L::NPAIR * L::COEF + (size_t)pl * L::TC * L::COEF;
                 const float2* sb = seedbuf + (size_t)pb * L::NPAIR * L::SROW + (size_t)pl * L::TC * L::SROW + g;
 #pragma unroll 1
@@ -513,6 +549,7 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
             unsigned issued[2] = {0, 0}, waited[2] = {0, 0};
             if (ptid == 0) {
                 for (int s = 0; s < 2 && s < nt; ++s) {
+                    if (skip_copy(b, item, s)) continue;
                     const int nbi = (int)((tbase + s) & 1);
                     mbar_expect_tx(&nbar[nbi], kTileBytes);
                     bulk_g2s(nodebuf + nbi * kTileFloats, p.nodes + (size_t)(t0 + s) * kTileFloats,
@@ -527,11 +564,13 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
                 const long long tg = tbase + it;
                 const int nbi = (int)(tg & 1);
                 if (sub == 0) {
-                    if (!mbar_wait(&nbar[nbi], (unsigned)((tg >> 1) & 1))) timed_out = true;
-                    if (ptid == 0) waited[nbi]++;
+                    // only a wait that saw the copy land counts it as drained
+                    if (field_wait(&nbar[nbi], (unsigned)((tg >> 1) & 1), s_abort, b.abort, timed_out) == WAIT_DONE &&
+                        ptid == 0)
+                        waited[nbi]++;
                 }
                 // the table pb was last used for compute tile cg - 2
-                if (cg >= 2 && !mbar_wait(&empty[pb], (unsigned)(((cg >> 1) - 1) & 1))) timed_out = true;
+                if (cg >= 2) field_wait(&empty[pb], (unsigned)(((cg >> 1) - 1) & 1), s_abort, b.abort, timed_out);
                 const float* nb = nodebuf + nbi * kTileFloats;
                 float* cb = coefbuf + (size_t)pb * L::NPAIR * L::COEF;
                 float2* sb = seedbuf + (size_t)pb * L::NPAIR * L::SROW;
@@ -575,7 +614,7 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
                 // node tile it fully read by all producers: refill its buffer with tile it + 2
                 if (sub == L::CPT - 1) {
                     asm volatile("bar.sync 1, %0;" ::"n"(L::NPROD) : "memory");
-                    if (ptid == 0 && it + 2 < nt) {
+                    if (ptid == 0 && it + 2 < nt && !*s_abort && !skip_copy(b, item, it + 2)) {
                         fence_proxy_async();
                         mbar_expect_tx(&nbar[nbi], kTileBytes);
                         bulk_g2s(nodebuf + nbi * kTileFloats, p.nodes + (size_t)(t0 + it + 2) * kTileFloats,
@@ -584,13 +623,15 @@ __global__ void __launch_bounds__(Grouped<TPP>::NT, 1) field_grouped_kernel(Batc
                     }
                 }
             }
-            // drain: never leave a bulk copy in flight into shared memory that is reused
+            // drain: never leave a bulk copy in flight into shared memory that is
+            // reused or released; these waits ignore the abort flag (each is
+            // bounded), and at most one issued copy per buffer is still pending
             if (ptid == 0) {
                 for (int s = 0; s < 2; ++s)
                     while (waited[s] < issued[s]) {
                         // the k-th tile of this item in buffer s has global index first + 2k
                         const long long first = tbase + ((s - (int)(tbase & 1)) & 1);
-                        if (!mbar_wait(&nbar[s], (unsigned)(((first >> 1) + waited[s]) & 1))) {
+                        if (mbar_wait(&nbar[s], (unsigned)(((first >> 1) + waited[s]) & 1)) != WAIT_DONE) {
                             timed_out = true;
                             break;
                         }
@@ -625,15 +666,19 @@ __global__ void __launch_bounds__(256, (NB == 2 || NB == 3) ? 3 : 2) field_direc
     __shared__ __align__(128) float nodebuf[2 * kTileFloats];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ long long slot;
+    __shared__ int abort_word;
+    volatile int* s_abort = &abort_word;
     const int tid = threadIdx.x;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
+        *s_abort = 0;
         mbar_fence_init();
     }
     bool timed_out = false;
     long long tbase = 0;
-    for (long long item = next_item(b, &slot, -1); item < b.n_items; item = next_item(b, &slot, item)) {
+    for (long long item = next_item(b, &slot, -1, s_abort); item < b.n_items;
+         item = next_item(b, &slot, item, s_abort)) {
         const Item w = decode(b, item);
         const FieldLaunch& p = w.r->f;
         const int pt = w.pbi * PPI + tid / GP;
@@ -655,6 +700,7 @@ __global__ void __launch_bounds__(256, (NB == 2 || NB == 3) ? 3 : 2) field_direc
         unsigned issued[2] = {0, 0}, waited[2] = {0, 0};
         if (tid == 0) {
             for (int s = 0; s < 2 && s < nt; ++s) {
+                if (skip_copy(b, item, s)) continue;
                 const int nbi = (int)((tbase + s) & 1);
                 mbar_expect_tx(&bar[nbi], kTileBytes);
                 bulk_g2s(nodebuf + nbi * kTileFloats, p.nodes + (size_t)(t0 + s) * kTileFloats,
@@ -678,8 +724,11 @@ __global__ void __launch_bounds__(256, (NB == 2 || NB == 3) ? 3 : 2) field_direc
         for (int it = 0; it < nt; ++it) {
             const long long tg = tbase + it;
             const int nbi = (int)(tg & 1);
-            if (!mbar_wait(&bar[nbi], (unsigned)((tg >> 1) & 1))) timed_out = true;
-            if (tid == 0) waited[nbi]++;
+            // only a wait that saw the copy land counts it as drained; after an
+            // abort the waits return at once and the item's rest is discarded
+            if (field_wait(&bar[nbi], (unsigned)((tg >> 1) & 1), s_abort, b.abort, timed_out) == WAIT_DONE &&
+                tid == 0)
+                waited[nbi]++;
             const float* nb = nodebuf + nbi * kTileFloats;
 #pragma unroll 1
             for (int j = 0; j < kTile; ++j) {
@@ -712,7 +761,7 @@ __global__ void __launch_bounds__(256, (NB == 2 || NB == 3) ? 3 : 2) field_direc
             }
             if ((it + 1) % p.flush_tiles == 0 || it + 1 == nt) fold_now(it + 1 <= p.flush_tiles);
             __syncthreads();
-            if (tid == 0 && it + 2 < nt) {
+            if (tid == 0 && it + 2 < nt && !*s_abort && !skip_copy(b, item, it + 2)) {
                 fence_proxy_async();
                 mbar_expect_tx(&bar[nbi], kTileBytes);
                 bulk_g2s(nodebuf + nbi * kTileFloats, p.nodes + (size_t)(t0 + it + 2) * kTileFloats,
@@ -721,10 +770,11 @@ __global__ void __launch_bounds__(256, (NB == 2 || NB == 3) ? 3 : 2) field_direc
             }
         }
         if (tid == 0) {
+            // drain (waits that ignore the abort flag, each bounded)
             for (int s = 0; s < 2; ++s)
                 while (waited[s] < issued[s]) {
                     const long long first = tbase + ((s - (int)(tbase & 1)) & 1);
-                    if (!mbar_wait(&bar[s], (unsigned)(((first >> 1) + waited[s]) & 1))) {
+                    if (mbar_wait(&bar[s], (unsigned)(((first >> 1) + waited[s]) & 1)) != WAIT_DONE) {
                         timed_out = true;
                         break;
                     }
@@ -893,6 +943,8 @@ int launch_field_f32(const FieldLaunch& p, cudaStream_t s)
     b.n_items = (long long)b.one.pb * (p.n_splits + 1);
     b.queue = nullptr;
     b.err = p.err;
+    b.abort = nullptr;  // grid mode: one item per CTA, nothing to stop early
+    b.fail_tile = -1;
     return launch_field_batch(cls, b, (int)b.n_items, s);
 }
 
@@ -908,7 +960,7 @@ __global__ void wait_selftest_kernel(int* err)
         mbar_fence_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0 && !mbar_wait(&bar, 0)) atomicOr(err, ERR_TIMEOUT);
+    if (threadIdx.x == 0 && mbar_wait(&bar, 0) != WAIT_DONE) atomicOr(err, ERR_TIMEOUT);
 }
 
 }  // namespace

@@ -140,6 +140,7 @@ struct sc_ctx {
     bool use_graphs = true;
     bool autotune = true;
     bool omega_chunks = true;       // plan omega chunk sizes (else 2048 per chunk)
+    int fail_tile = -1;             // failure-path test: a node-tile copy left unissued
     uint64_t graph_tick = 0;
     uint64_t graph_captures = 0, graph_replays = 0;
     std::map<std::tuple<int, int, int, int, int, int>, int> tuned;  // shape -> split count

@@ -66,6 +66,13 @@ struct WorkReq {
 // device array sorted by item0 and CTAs take items from *queue (reset to 0
 // before the launch).  Grid mode (reqs == nullptr): the single request `one`,
 // item = blockIdx.x, grid = n_items.
+//   abort      per-launch flag (reset to 0 before the launch, or null): a
+//              CTA whose bounded wait runs out sets it, and every CTA stops
+//              taking items once it is set, so a lost copy ends the launch
+//              after one wait limit instead of one per item;
+//   fail_tile  failure-path test (-1 off): the CTA that runs item 0 leaves
+//              the bulk copy of that item's node tile fail_tile unissued, so
+//              the wait for it runs out (no fault, no copy in flight).
 struct BatchLaunch {
     const WorkReq* reqs;
     WorkReq one;
@@ -73,6 +80,8 @@ struct BatchLaunch {
     long long n_items;
     int* queue;
     int* err;
+    int* abort;
+    int fail_tile;
 };
 
 // Kernel class for a chunk of n_omega (<= 2048) omegas: 0..16 the direct

@@ -38,3 +38,39 @@ def test_bounded_wait_times_out_and_context_survives():
         assert torch.equal(E1, E2) and torch.equal(B1, B2)
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("n_omega,tile", [(256, 0), (256, 7), (8, 1), (8, 9)])
+def test_lost_copy_ends_the_launch_after_one_wait(n_omega, tile):
+    """A node-tile copy that never lands (SC_OPT_FAIL_COPY leaves it
+    unissued: no fault, no copy in flight) makes its wait run out once; the
+    CTA and then the whole launch stop instead of spending a wait limit on
+    every later tile of the item (hundreds here).  The call reports
+    SC_ERR_TIMEOUT within a few seconds, and the next call on the context is
+    bitwise equal to one made before.  Grouped (256 omegas) and direct (8)
+    kernels; the lost copy is one of the first two or a refill."""
+    ctx = sc.Context(0)
+    try:
+        w = wl.sweep(1e4, 256, n_points=2048)
+        mc = w["mirror"]
+        m = ctx.mirror(mc["f"], 0.0, mc["r_max"], mc["n_r"], mc["n_theta"])
+        om = wl.uniform_omegas(n_omega)
+        inc = ctx.incident(profile="gauss", w0=w["beam"]["w0"],
+                           spectrum=dict(kind="sampled", omega=om, amp=np.ones(om.size)))
+        P = torch.tensor(w["points"], device="cuda")
+        E1, B1 = ctx.eval(m, inc, om, P, stats=True)[:2]  # tunes and caches this shape
+        ctx.set_option(sc.SC_OPT_FAIL_COPY, tile)
+        try:
+            t0 = time.time()
+            with pytest.raises(sc.ScError) as e:
+                ctx.eval(m, inc, om, P, stats=True)
+            dt = time.time() - t0
+        finally:
+            ctx.set_option(sc.SC_OPT_FAIL_COPY, -1)
+        assert e.value.status == sc.SC_ERR_TIMEOUT
+        assert 0.5 < dt < 5.0, dt
+        E2, B2 = ctx.eval(m, inc, om, P, stats=True)[:2]
+        torch.cuda.synchronize()
+        assert torch.equal(E1, E2) and torch.equal(B1, B2)
+    finally:
+        ctx.close()
