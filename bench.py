@@ -60,13 +60,16 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched and serving legs")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="broadband", choices=["broadband", "profile", "small_omega", "c5"],
+    ap.add_argument("--workload", default="broadband",
+                    choices=["broadband", "profile", "small_omega", "c5", "c4", "sweep"],
                     help="broadband: the benchmark workload; profile: the same kernel "
                          "configuration at 128 x 128 nodes, for ncu captures; small_omega: the "
                          "broadband mirror, pulse and points at 256 x 256 nodes and 8 omegas (the "
                          "direct kernel of small requests); c5: the largest "
                          "serving request (1024^2 nodes, GRID^3 points over +-3, 512 omegas, "
-                         "512 times) through the fused time-domain path, timed once")
+                         "512 times) through the fused time-domain path, timed once; c4: the "
+                         "batched leg at its full size (64 requests); sweep: the precision "
+                         "sweep over f and node counts (per-component errors)")
     ap.add_argument("--grid", type=int, default=128, help="points per axis of the c5 workload")
     return ap.parse_args()
 
@@ -260,46 +263,84 @@ def make_config_handles(ctx, configs):
     return out
 
 
-def batch_leg(sc, torch, dev, n_req=64):
-    """The uneven batch: one sc_eval_batch against the same requests one by one."""
+def sampled_oracle_error(configs, reqs, outs, n_points=4, n_omega=16):
+    """Max over requests of the R11 error (relative L2 over the sampled points,
+    normalised by their largest |F|, max over omega) of the GPU outputs against
+    the FP64 oracle at the first n_points points and up to n_omega omegas."""
+    import oracle
     from paper_1609_08146_gb300 import workloads as wl
 
-    configs, reqs = wl.uneven_requests(n_req, seed=1609)
+    worst = 0.0
+    for r, (E, B) in zip(reqs, outs):
+        m, b = wl.oracle_args(configs[r["config"]])
+        om = r["omegas"]
+        so = np.unique(np.round(np.linspace(0, len(om) - 1, min(n_omega, len(om)))).astype(int))
+        a = oracle.spectrum(configs[r["config"]]["spectrum"], om[so], b)
+        E0, B0 = oracle.field(m, b, om[so], r["points"][:n_points], amp=a)
+        import torch
+
+        ti = torch.as_tensor(so, device=E.device)
+        Eg = E.index_select(0, ti)[:, :n_points].cpu().numpy()
+        Bg = B.index_select(0, ti)[:, :n_points].cpu().numpy()
+        worst = max(worst, rel_l2(Eg, E0), rel_l2(Bg, B0))
+    return worst
+
+
+def c4_workload_name(n, seed):
+    return ("%d seeded uneven requests (seed %d), each its own mirror and beam: f 1e3-1e5 lambda0 "
+            "log-uniform, 128^2-1024^2 nodes, 1k-262k points, 1-512 omegas, Gaussian/super-Gaussian, "
+            "linear/radial/azimuthal, Zernike j=2..15 N(0, 0.1) waves" % (n, seed))
+
+
+def batch_leg(sc, torch, dev, n_req=16, seed=1609, check=True):
+    """The uneven batch at the batched workload's full ranges: one
+    sc_eval_batch against the same requests one by one (both timed after a
+    warm-up pass that builds the tables and tunes the shapes); the batch
+    must equal the one-by-one results bitwise."""
+    from paper_1609_08146_gb300 import workloads as wl
+
+    configs, reqs = wl.config4_requests(n_req, seed=seed)
     stream = torch.cuda.Stream(device=dev)
     ctx = sc.Context(dev.index or 0, stream=stream)
     hs = make_config_handles(ctx, configs)
     batch = [(hs[r["config"]][0], hs[r["config"]][1], r["omegas"],
               torch.tensor(r["points"], device=dev)) for r in reqs]
     evals = sum(len(r["points"]) * hs[r["config"]][2] * len(r["omegas"]) for r in reqs)
-    for (m, inc, om, P) in batch:  # tables resident, shapes tuned
-        ctx.eval(m, inc, om, P)
-    ctx.eval_batch(batch)
-    stream.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    ev[0].record(stream)
-    ctx.eval_batch(batch)
-    ev[1].record(stream)
-    for (m, inc, om, P) in batch:
-        ctx.eval(m, inc, om, P)
-    ev[2].record(stream)
-    stream.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for (m, inc, om, P) in batch:  # tables resident, shapes tuned
+            ctx.eval(m, inc, om, P)
+        stream.synchronize()
+        warm_s = time.perf_counter() - t0
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        outs_b = ctx.eval_batch(batch)
+        ev[1].record(stream)
+        outs_s = [ctx.eval(m, inc, om, P) for (m, inc, om, P) in batch]
+        ev[2].record(stream)
+        stream.synchronize()
     t_batch = ev[0].elapsed_time(ev[1]) / 1000.0
     t_seq = ev[1].elapsed_time(ev[2]) / 1000.0
+    same = all(torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) for a, b in zip(outs_b, outs_s))
+    err = sampled_oracle_error(configs, reqs, outs_b) if check else None
     ctx.close()
     return {"requests": n_req, "evals": evals, "value": evals / t_batch, "unit": "evals/s",
             "sequential_value": evals / t_seq, "batch_ms": 1000 * t_batch, "sequential_ms": 1000 * t_seq,
-            "workload": "64 seeded uneven requests: 8 mirror/beam configs (f 1e3-1e5, 64^2-256^2 nodes, "
-                        "Gaussian/super-Gaussian, linear/radial/azimuthal, Zernike), 256-8192 points, "
-                        "1-256 omegas"}
+            "bitwise_equal_alone": bool(same), "oracle_rel_l2_err": err,
+            "oracle_sample": "first 4 points x up to 16 omegas of every request, FP64 oracle",
+            "warmup_s": warm_s, "workload": c4_workload_name(n_req, seed)}
 
 
-def serving_leg(sc, torch, dev, n_per_rate=48, loads=(0.5, 0.8, 0.95)):
-    """Poisson arrivals of uneven requests at fractions of the saturated rate;
-    latency = observed completion - submission (library clock)."""
+def serving_leg(sc, torch, dev, n_req=16, seed=2016, loads=(0.5, 0.8, 0.95), budget=150 << 30):
+    """Poisson arrivals of the batched workload's requests (full ranges) at
+    fractions of the saturated rate, HBM admission budget 150 GB, node tables
+    resident; the same requests serve saturation and every load.  Latency =
+    observed completion - submission (library clock), host points copied in
+    by the server."""
     from paper_1609_08146_gb300 import workloads as wl
 
-    configs, reqs = wl.uneven_requests(n_per_rate * (len(loads) + 1), seed=2016)
-    ctx = sc.Context(dev.index or 0)
+    configs, reqs = wl.config4_requests(n_req, seed=seed)
+    ctx = sc.Context(dev.index or 0, budget_bytes=budget)
     ctx.set_option(sc.SC_OPT_AUTOTUNE, 0)  # no timing runs on the serving path
     hs = make_config_handles(ctx, configs)
     for (m, inc, _) in hs:  # node tables resident before the first arrival
@@ -308,50 +349,55 @@ def serving_leg(sc, torch, dev, n_per_rate=48, loads=(0.5, 0.8, 0.95)):
     def evals(r):
         return len(r["points"]) * hs[r["config"]][2] * len(r["omegas"])
 
-    def run(chunk, arrivals):
+    total = sum(evals(r) for r in reqs)
+
+    def run(arrivals, keep=()):
         t0 = time.perf_counter()
-        pending, lat, tick = [], [], []
+        pending, lat, kept = [], [], {}
         i = 0
-        while i < len(chunk) or pending:
+        while i < len(reqs) or pending:
             now = time.perf_counter() - t0
-            while i < len(chunk) and arrivals[i] <= now:
-                r = chunk[i]
+            while i < len(reqs) and arrivals[i] <= now:
+                r = reqs[i]
                 m, inc, _ = hs[r["config"]]
-                pending.append(ctx.submit(m, inc, r["omegas"], r["points"]))
+                pending.append((i, ctx.submit(m, inc, r["omegas"], r["points"])))
                 i += 1
             still = []
-            for t in pending:
+            for k, t in pending:
                 if ctx.poll(t):
                     s0, s1, s2 = ctx.ticket_times(t)
                     lat.append(s2 - s0)
-                    tick.append(s2)
+                    if k in keep:
+                        kept[k] = ctx.fetch(t)
                     ctx.release(t)
                 else:
-                    still.append(t)
+                    still.append((k, t))
             pending = still
             time.sleep(0.0002)
-        wall = time.perf_counter() - t0
-        return lat, wall
+        return lat, time.perf_counter() - t0, kept
 
-    # saturated: everything submitted at once
-    sat_chunk = reqs[:n_per_rate]
-    lat, wall = run(sat_chunk, [0.0] * len(sat_chunk))
-    sat_rate = len(sat_chunk) / wall
-    out = {"saturated_req_per_s": sat_rate,
-           "saturated_evals_per_s": sum(evals(r) for r in sat_chunk) / wall,
-           "workload": "seeded uneven requests (8 resident mirror/beam configs, 64^2-256^2 nodes, "
-                       "256-8192 points, 1-256 omegas), Poisson arrivals", "rates": []}
+    # saturated: everything submitted at once; two small requests kept for the error check
+    order = sorted(range(len(reqs)), key=lambda k: evals(reqs[k]))
+    keep = tuple(order[:2])
+    lat, wall, kept = run([0.0] * len(reqs), keep=keep)
+    sat_rate = len(reqs) / wall
+    err = sampled_oracle_error(configs, [reqs[k] for k in keep], [kept[k] for k in keep])
+    out = {"saturated_req_per_s": sat_rate, "saturated_evals_per_s": total / wall,
+           "requests": n_req, "evals": total, "budget_bytes": budget,
+           "oracle_rel_l2_err": err,
+           "oracle_sample": "the two smallest requests as served: first 4 points x up to 16 omegas",
+           "workload": c4_workload_name(n_req, seed) + ", Poisson arrivals, same requests at every load",
+           "rates": []}
     rng = np.random.Generator(np.random.PCG64(5))
-    for k, load in enumerate(loads):
-        chunk = reqs[(k + 1) * n_per_rate:(k + 2) * n_per_rate]
+    for load in loads:
         rate = load * sat_rate
-        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(chunk)))
-        lat, wall = run(chunk, arrivals)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
+        lat, wall, _ = run(arrivals)
         lat_ms = 1000.0 * np.array(lat)
-        out["rates"].append({"load": load, "rate_req_per_s": rate, "requests": len(chunk),
+        out["rates"].append({"load": load, "rate_req_per_s": rate, "requests": len(reqs),
                              "p50_ms": float(np.percentile(lat_ms, 50)),
                              "p99_ms": float(np.percentile(lat_ms, 99)),
-                             "throughput_evals_per_s": sum(evals(r) for r in chunk) / wall})
+                             "throughput_evals_per_s": total / wall})
     ctx.close()
     return out
 
@@ -382,6 +428,77 @@ def run_reference(args, rank, world, pg):
                          "sample": sample, "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+    print(json.dumps(line), flush=True)
+
+
+def component_errors(F, R):
+    """Per component c: max over omega of sqrt(mean_points |F_c - R_c|^2) /
+    max_points |R| (the R11 metric split by component)."""
+    F = np.asarray(F, dtype=np.complex128)
+    den = np.max(np.sqrt(np.sum(np.abs(R) ** 2, axis=2)), axis=1)
+    num = np.sqrt(np.mean(np.abs(F - R) ** 2, axis=1))  # [omega, c]
+    return [float(np.max(num[:, c] / np.maximum(den, 1e-300))) for c in range(3)]
+
+
+def run_sweep(args, ctx, sc, torch, dev, stream, wl):
+    """Precision sweep: the broadband pulse's 256 omegas (unit amplitudes: the
+    errors are those of the spatial sums) at f in {1e2, 1e3, 1e4, 1e5} lambda0
+    and 256^2, 512^2, 1024^2 nodes, 4096 seeded points in the +-2 cube.
+    FP32-compensated on every point, the FP64 GPU form on every 16th point,
+    the FP64 oracle on every 512th; per-component error of E and B for each
+    pair, and the field time of each form."""
+    import oracle
+
+    rows = []
+    clk = ClockSampler(dev.index if dev.index is not None else 0)
+    clk.start()
+    for n_nodes in (256, 512, 1024):
+        for f in (1e2, 1e3, 1e4, 1e5):
+            w = wl.sweep(f, n_nodes, n_points=4096)
+            mc, b = w["mirror"], w["beam"]
+            om = w["omegas"]
+            m = ctx.mirror(mc["f"], mc["r_min"], mc["r_max"], mc["n_r"], mc["n_theta"], rim=mc["rim"])
+            inc = ctx.incident(profile=b["profile"], w0=b["w0"], pol=b["pol"],
+                               spectrum=dict(kind="sampled", omega=om, amp=np.ones(om.size)))
+            with torch.cuda.stream(stream):
+                P = torch.tensor(w["points"], device=dev)
+                ctx.eval(m, inc, om, P[:8])  # table resident
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                e[0].record(stream)
+                E32, B32 = ctx.eval(m, inc, om, P)
+                e[1].record(stream)
+                E64, B64 = ctx.eval(m, inc, om, P[::16], precision="fp64")
+                e[2].record(stream)
+                stream.synchronize()
+            sel = np.arange(0, 4096, 512)
+            mo, bo = wl.oracle_args(w)
+            t0 = time.perf_counter()
+            E0, B0 = oracle.field(mo, bo, om, w["points"][sel])
+            t_or = time.perf_counter() - t0
+            e32 = E32.cpu().numpy()
+            b32 = B32.cpu().numpy()
+            e64 = E64.cpu().numpy()
+            b64 = B64.cpu().numpy()
+            rows.append({
+                "f_lambda0": f, "nodes": n_nodes * n_nodes,
+                "fp32_vs_oracle": {"E": component_errors(e32[:, sel], E0), "B": component_errors(b32[:, sel], B0)},
+                "fp64_vs_oracle": {"E": component_errors(e64[:, sel // 16], E0),
+                                   "B": component_errors(b64[:, sel // 16], B0)},
+                "fp32_vs_fp64_gpu": {"E": component_errors(e32[:, ::16], e64),
+                                     "B": component_errors(b32[:, ::16], b64)},
+                "fp32_vs_fp64_gpu_at_oracle_points": {"E": component_errors(e32[:, sel], e64[:, sel // 16]),
+                                                      "B": component_errors(b32[:, sel], b64[:, sel // 16])},
+                "fp32_ms": e[0].elapsed_time(e[1]), "fp64_ms_256_points": e[1].elapsed_time(e[2]),
+                "oracle_s_8_points": t_or})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    clocks = clk.stop()
+    line = {"metric": "precision sweep: per-component relative L2 error (R11 metric by component)",
+            "config": {"workload": "broadband pulse, 256 omegas, f 1e2-1e5 lambda0, 256^2-1024^2 nodes, "
+                                   "4096 seeded points in +-2 lambda0",
+                       "samples": "FP32 all 4096 points; FP64 GPU every 16th (256); oracle every 512th (8); "
+                                  "each error is normalised by the largest |F| over its own point set, so "
+                                  "the 8-point errors read higher than the 256-point ones"},
+            "rows": rows, "clocks": clocks}
     print(json.dumps(line), flush=True)
 
 
@@ -445,6 +562,17 @@ def main():
     ctx = sc.Context(local, stream=stream)
     if args.workload == "c5":
         run_c5(args, ctx, sc, torch, dev, stream, wl)
+        return
+    if args.workload == "sweep":
+        run_sweep(args, ctx, sc, torch, dev, stream, wl)
+        return
+    if args.workload == "c4":
+        clk = ClockSampler(local)
+        clk.start()
+        res = batch_leg(sc, torch, dev, n_req=64, seed=1609)
+        res["clocks"] = clk.stop()
+        res["metric"] = "Stratton-Chu obs*node*omega evals/s (batched)"
+        print(json.dumps(res), flush=True)
         return
     if args.workload == "broadband":
         w = wl.broadband()

@@ -560,6 +560,8 @@ enum {
     SC_OPT_GRAPHS = 5,          /* 1 (default): capture/replay field launches       */
     SC_OPT_AUTOTUNE = 6,        /* 1 (default): time split-count candidates on the  */
                                 /* first request of each shape and cache the best   */
+                                /* (chunks above 1.2e12 evaluations are not timed:  */
+                                /* they take the most splits whose workspace fits)  */
     SC_OPT_OMEGA_CHUNKS = 7,    /* 1 (default): cut a request's omegas into chunks  */
                                 /* that keep the field kernels' threads busy;      */
                                 /* 0: one chunk per 2048 omegas                     */

@@ -58,6 +58,8 @@ float time_chunk(sc_ctx* ctx, Lane& ln, Chunk c, int S, const Table* tab, float2
     return ms;
 }
 
+constexpr double kTuneMaxEvals = 1.2e12;
+
 // Split count for a chunk shape: explicit option, tuned value, or heuristic
 // (tuned on first sight when the autotuner is on).
 sc_status choose_splits(sc_ctx* ctx, Lane& ln, Chunk& c, const Table* tab, int slots, int* S_out)
@@ -95,7 +97,14 @@ sc_status choose_splits(sc_ctx* ctx, Lane& ln, Chunk& c, const Table* tab, int s
                 need = std::max(need, n);
             }
         }
-        if (fit.size() > 1) {
+        // Timing costs one run of the chunk per candidate.  A chunk of more
+        // than kTuneMaxEvals evaluations (about a second) takes the most
+        // splits that fit instead: at that size more, shorter items balance
+        // the CTAs' tails better, and the extra partials cost little.
+        const double chunk_evals = (double)c.f.n_pts * tiles * sc::kTile * c.f.n_omega * c.n_parts;
+        if (chunk_evals > kTuneMaxEvals && !fit.empty()) {
+            best = *std::max_element(fit.begin(), fit.end());
+        } else if (fit.size() > 1) {
             sc_status st = ensure(ctx, ln.ws, need * sizeof(float2), ln.stream);
             if (st != SC_OK) return st;
             float best_ms = 1e30f;

@@ -6,10 +6,30 @@
 #include <string.h>
 
 #include <algorithm>
+#include <thread>
 
 #include "sc_host.h"
 
 namespace sch {
+
+// f(i) for i in [0, n) on up to 32 host threads (contiguous blocks of i);
+// f must only write state of its own i.
+template <typename F>
+void parallel_for(int n, F f)
+{
+    const int hw = (int)std::thread::hardware_concurrency();
+    const int nth = std::max(1, std::min({hw, 32, n / 8}));
+    if (nth <= 1) {
+        for (int i = 0; i < n; ++i) f(i);
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nth; ++t)
+        pool.emplace_back([&, t] {
+            for (int i = (int)((long long)n * t / nth); i < (int)((long long)n * (t + 1) / nth); ++i) f(i);
+        });
+    for (auto& th : pool) th.join();
+}
 
 // ------------------------------------------------------------------------
 // Quadrature: Gauss-Legendre on [a, b].  Roots of P_n by Newton iteration
@@ -390,11 +410,10 @@ void build_nodes(const sc_mirror_t* m, const sc_incident_t* in, std::vector<Host
             bv[2] = bv[0] * gx + bv[1] * gy;
         }
     };
-    surf.clear();
-    surf1.clear();
-    surf.reserve((size_t)nr * nt);
-    if (first) surf1.reserve((size_t)nr * nt);
-    for (int i = 0; i < nr; ++i) {
+    surf.assign((size_t)nr * nt, HostNode{});
+    surf1.assign(first ? (size_t)nr * nt : 0, HostNode{});
+    // rings in parallel: every node is a pure function of (r_i, theta_l)
+    parallel_for(nr, [&](int i) {
         const double r = gr[i];
         const SurfPt sp = surf_at(m, r);
         for (int l = 0; l < nt; ++l) {
@@ -413,7 +432,7 @@ void build_nodes(const sc_mirror_t* m, const sc_incident_t* in, std::vector<Host
             nd.jy = (Nz * bv[0] - Nx * bv[2]) * wq;
             nd.jz = (Nx * bv[1] - Ny * bv[0]) * wq;
             nd.rho = (Nx * e[0] + Ny * e[1] + Nz * e[2]) * wq;
-            surf.push_back(nd);
+            surf[(size_t)i * nt + l] = nd;
             if (first) {
                 double de, db;
                 incident_div(in, r, th, de, db);
@@ -422,10 +441,10 @@ void build_nodes(const sc_mirror_t* m, const sc_incident_t* in, std::vector<Host
                 n1.jy = -Nx * db * wq;
                 n1.jz = 0.0;
                 n1.rho = Nz * de * wq;  // N . (0, 0, de)
-                surf1.push_back(n1);
+                surf1[(size_t)i * nt + l] = n1;
             }
         }
-    }
+    });
     rim.clear();
     if (!m->q.rim_term) return;
     for (int edge = 0; edge < 2; ++edge) {

@@ -14,6 +14,8 @@ lambda0, omega in units of omega0, time in lambda0/c (2.6685 fs at 800 nm).
             points on the axis over +-5, 512 time samples t = (m - 256)/8.
   sweep     the broadband pulse with f in {1e2, 1e3, 1e4, 1e5}, r_max = 2f,
             w0 = 0.6 f, N x N nodes, 4096 uniform random points in [-2, 2]^3.
+  config4_requests  uneven requests, each its own mirror and beam, 128^2 to
+            1024^2 nodes, 1k to 262k points, 1 to 512 omegas.
 """
 from __future__ import annotations
 
@@ -108,6 +110,34 @@ def uneven_requests(n: int, seed: int, max_nodes: int = 256, max_points: int = 8
         npts = int(round(10 ** rng.uniform(np.log10(256), np.log10(max_points))))
         nom = int(round(10 ** rng.uniform(0, np.log10(max_omega))))
         reqs.append(dict(config=c, omegas=uniform_omegas(nom),
+                         points=rng.uniform(-2.0, 2.0, size=(npts, 3))))
+    return configs, reqs
+
+
+def config4_requests(n: int, seed: int):
+    """Seeded uneven requests at the batched workload's full ranges, each with
+    its own mirror and beam: f log-uniform in [1e3, 1e5], r_max = 2f,
+    w0 = 0.6 f, N x N nodes with N = 2^U{7..10} (128^2 to 1024^2), Gaussian
+    or super-Gaussian N=4 beam, x-linear / radial / azimuthal polarisation,
+    Zernike j = 2..15 with N(0, 0.1) waves, the broadband 10 fs pulse; a
+    log-uniform point count in [1024, 262144] uniform in the +-2 cube and a
+    log-uniform omega count in [1, 512] on [0.5, 1.5] (omega0 alone if 1).
+    Returns (configs, reqs) with request i using configs[i]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    configs, reqs = [], []
+    for i in range(n):
+        f = float(10 ** rng.uniform(3, 5))
+        N = int(2 ** rng.integers(7, 11))
+        profile = str(rng.choice(["gauss", "supergauss"]))
+        pol = str(rng.choice(["linear", "radial", "azimuthal"]))
+        zern = list(rng.normal(0.0, 0.1, size=14))
+        npts = int(round(10 ** rng.uniform(np.log10(1024), np.log10(262144))))
+        nom = int(round(10 ** rng.uniform(0, np.log10(512))))
+        configs.append(dict(
+            mirror=dict(f=f, r_min=0.0, r_max=2 * f, n_r=N, n_theta=N, rim=True),
+            beam=dict(profile=profile, sg_order=4, w0=0.6 * f, pol=pol, pol_angle=0.0, zernike=zern),
+            spectrum=dict(kind="gauss_time", fwhm_t=10.0 / FS_PER_UNIT_800NM, lambda_c=1.0, energy=1.0)))
+        reqs.append(dict(config=i, omegas=uniform_omegas(nom),
                          points=rng.uniform(-2.0, 2.0, size=(npts, 3))))
     return configs, reqs
 

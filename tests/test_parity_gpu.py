@@ -333,6 +333,25 @@ def test_precision_sweep_sampled(ctx, f):
     check(ctx, w["mirror"], w["beam"], w["omegas"], pts, fp64=False)
 
 
+def test_precision_sweep_1024_nodes_at_f_1e5(ctx):
+    """The largest precision-sweep case: f = 1e5 lambda0, 1024 x 1024 nodes,
+    256 omegas, the 4096-point focal cube on the GPU in one call; the oracle
+    checks 64 sampled points at 16 omegas spread over the band (both ends)."""
+    w = wl.sweep(1e5, 1024, n_points=4096)
+    mirror, beam = w["mirror"], w["beam"]
+    om = w["omegas"]
+    m = ctx.mirror(mirror["f"], 0.0, mirror["r_max"], mirror["n_r"], mirror["n_theta"])
+    inc = ctx.incident(profile="gauss", w0=beam["w0"], spectrum=unit_spectrum(om))
+    E, B = ctx.eval(m, inc, om, torch.tensor(w["points"], device="cuda"))
+    torch.cuda.synchronize()
+    sel = np.arange(0, 4096, 64)
+    so = np.round(np.linspace(0, 255, 16)).astype(int)
+    E0, B0 = run_oracle(mirror, beam, om[so], w["points"][sel])
+    Es = E.cpu().numpy()[so][:, sel]
+    Bs = B.cpu().numpy()[so][:, sel]
+    assert max(rel_err(Es, E0), rel_err(Bs, B0)) <= TOL32
+
+
 def test_broadband_full_size_sampled(ctx):
     """The benchmark's workload (512 x 512 nodes, 256 omegas, 4160 points) in
     the benchmark's launch configuration; the oracle checks 10 sampled points
