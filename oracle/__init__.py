@@ -117,6 +117,12 @@ def _load():
             ctypes.c_int, _DP, _DP, _DP, ctypes.c_int,
         ]
         lib.or_envelope.argtypes = [ctypes.POINTER(_Beam), ctypes.c_double, ctypes.c_int, _DP, _DP]
+        lib.or_mfie_current.argtypes = [ctypes.POINTER(_Mirror), ctypes.POINTER(_Beam), ctypes.c_double,
+                                        ctypes.c_int, _DP, ctypes.c_int, ctypes.c_int, _DP]
+        lib.or_field_mfie.argtypes = [ctypes.POINTER(_Mirror), ctypes.POINTER(_Beam), ctypes.c_int, _DP, _DP,
+                                      ctypes.c_int, _DP, ctypes.c_int, ctypes.c_int, _DP, _DP, ctypes.c_int]
+        lib.or_mfie_sphere_te1.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, _DP, ctypes.c_int,
+                                           ctypes.c_int, _DP]
         lib.or_incident.argtypes = [
             ctypes.POINTER(_Beam), ctypes.c_double, ctypes.c_int, _DP, ctypes.c_int, _DP, _DP, _DP,
         ]
@@ -284,4 +290,50 @@ def time_domain(F, omegas, times, threads: int = 0):
     out = np.zeros((t.size,) + F.shape[1:], dtype=np.float64)
     _load().or_time_domain(om.size, _ptr(om), nv, _ptr(F.view(np.float64)), t.size, _ptr(t),
                            _ptr(out), int(threads))
+    return out
+
+
+def mfie_current(mirror: dict, beam: dict, omega: float, targets_xy, n_rho: int, n_phi: int):
+    """First MFIE correction dJ [n, 3] complex (Sec. II's Liouville-Neumann
+    series: dJ = 2 n x PV SS J0 x grad g dS, J0 = 2 J_inc) at mirror points
+    above targets_xy [n, 2], polar rule n_rho x n_phi about each target."""
+    xy = np.ascontiguousarray(np.asarray(targets_xy, dtype=np.float64).reshape(-1, 2))
+    out = np.zeros((xy.shape[0], 3), dtype=np.complex128)
+    keep: list = []
+    m = _mirror(mirror)
+    b = _beam(beam, keep)
+    if _load().or_mfie_current(ctypes.byref(m), ctypes.byref(b), 2.0 * np.pi * float(omega), xy.shape[0],
+                               _ptr(xy), int(n_rho), int(n_phi), _ptr(out.view(np.float64))):
+        raise ValueError("the MFIE correction needs a disk (r_min = 0) and a collimated beam of order 0")
+    return out
+
+
+def field_mfie(mirror: dict, beam: dict, omegas, pts, n_rho: int, n_phi: int, amp=None, threads: int = 0):
+    """Physical-optics field (Eq. 11) plus the field of the first MFIE
+    correction, E, B [n_omega, n_pts, 3] complex."""
+    om = np.ascontiguousarray(np.atleast_1d(omegas), dtype=np.float64)
+    p = np.ascontiguousarray(np.asarray(pts, dtype=np.float64).reshape(-1, 3))
+    a = None
+    if amp is not None:
+        a = np.ascontiguousarray(np.asarray(amp, dtype=np.complex128).view(np.float64))
+    E = np.zeros((om.size, p.shape[0], 3), dtype=np.complex128)
+    B = np.zeros_like(E)
+    keep: list = []
+    m = _mirror(mirror)
+    b = _beam(beam, keep)
+    rc = _load().or_field_mfie(ctypes.byref(m), ctypes.byref(b), om.size, _ptr(om), _ptr(a), p.shape[0], _ptr(p),
+                               int(n_rho), int(n_phi), _ptr(E.view(np.float64)), _ptr(B.view(np.float64)),
+                               int(threads))
+    if rc != 0:
+        raise ValueError("invalid mirror or beam for the MFIE correction")
+    return E, B
+
+
+def mfie_sphere_te1(a: float, k: float, targets, n_psi: int, n_phi: int):
+    """The MFIE operator K[J] = n x PV SS J x grad g dS on a sphere of radius
+    a for J = z x r^, at unit-vector targets [n, 3] (test of the operator)."""
+    t = np.ascontiguousarray(np.asarray(targets, dtype=np.float64).reshape(-1, 3))
+    out = np.zeros((t.shape[0], 3), dtype=np.complex128)
+    _load().or_mfie_sphere_te1(float(a), float(k), t.shape[0], _ptr(t), int(n_psi), int(n_phi),
+                               _ptr(out.view(np.float64)))
     return out

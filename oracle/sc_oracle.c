@@ -22,6 +22,9 @@
  *   - Sec. III.B, Eqs. 12-18: Fourier convention exp(-ikt), semi-discrete
  *     inverse transform, per-component amplitude from a power spectrum
  *     (Eq. 16) and a spectral phase map (Eq. 18).
+ *   - Sec. II, eq:theory.mfie with its Liouville-Neumann series: the first
+ *     correction beyond physical optics (eq:theory.poa), and Appendix A's
+ *     singular limits (the principal value of the on-surface integral).
  *   - Sec. III.C.1, Eq. 21: the paraboloid z = r^2/(4f) - f with its focus at
  *     the origin; Sec. III.C.1: tensor-product quadrature, Gauss-Legendre or
  *     composite Simpson in r (the two rules it names), trapezoid in theta.
@@ -88,6 +91,15 @@
  *       b_perp = (-z) x e_perp; B_perp stays (-z) x E_perp.  Here the
  *       transverse divergences are taken by fourth-order central
  *       differences of step 1e-3 w0 (the library uses closed forms).
+ *   R17 the first correction beyond physical optics (NEXT-4): the
+ *       Liouville-Neumann series of the MFIE (Sec. II) starts at J0 = 2 J_inc
+ *       and its next term adds dJ = 2 n_t x PV SS J0 x grad g dS.  The
+ *       integrand is O(1/R) at the target on a smooth surface, so the
+ *       principal value is the improper integral, taken in polar coordinates
+ *       about the target (Gauss-Legendre in rho to the rim, trapezoid in phi).
+ *       The corrected field adds the field of dJ from Sancer's representation
+ *       with n x E = 0 (Eq. 10's form for a general current) on the mirror's
+ *       nodes.  Disks (r_min = 0) and collimated beams of order 0 only.
  *
  * Output layout: E[n_omega][n_pts][3] complex, stored as interleaved doubles
  * (re, im); same for B.
@@ -847,5 +859,260 @@ int or_time_domain(int n_omega, const double* omega, long n_vals, const double* 
         }
         out[idx] = 2.0 * creal(s) * dk;
     }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* First correction of the Liouville-Neumann series of the MFIE (Sec. II,   */
+/* eq:theory.mfie; reading R17).                                             */
+/*                                                                           */
+/*   (1/2) J = J_inc + n x PV SS J x grad g dS,   J_inc = n x B_inc.         */
+/*                                                                           */
+/* The first term of the series is physical optics, J0 = 2 J_inc            */
+/* (eq:theory.poa).  The next iterate is J1 = J0 + dJ with                   */
+/*   dJ(r_t) = 2 n_t x PV SS J0(r) x grad g(r, r_t) dS(r),                   */
+/* grad acting on the surface variable r (reading R1), n_t the unit normal   */
+/* at the target r_t on the mirror.  Near r_t the integrand is O(1/R): both  */
+/* n_t . (r - r_t) and n_t . J0(r) vanish like R on a smooth surface (J0 is  */
+/* tangent at r), so the principal value is the ordinary improper integral.  */
+/* It is taken in polar coordinates (rho, phi) about the target's projection */
+/* (x_t, y_t) on the plane of the mirror's parametrisation z = F(x, y):      */
+/* dS = |N| dx dy = |N| rho drho dphi, and the factor rho cancels the 1/R.   */
+/* Each ray phi runs from the target to the rim r = r_max (a disk,           */
+/* r_min = 0): Gauss-Legendre in rho on [0, rho_max(phi)], periodic          */
+/* trapezoid in phi.  The field of the corrected current adds the field of   */
+/* dJ to the physical-optics field; dJ does not come from a Maxwell          */
+/* incident field, so its field is the general representation behind        */
+/* Eq. 10 (Sancer's form with n x E = 0 and n x B = J),                       */
+/*   E' += SS { ik dJ g + (i/k) grad grad g . dJ } dS,  B' += SS dJ x grad g dS, */
+/* on the mirror's own quadrature nodes, with the Appendix-A dyadic.         */
+
+/* SS J x grad g(r, r_t) dS for one source point: adds J x grad g * dS to acc.
+ * The incident phase of J (phi_in) joins the phase of g in one exponential. */
+static void mfie_term(double k, const double r[3], const double rt[3], const cplx Jt[3], double phi_in,
+                      double dS, cplx acc[3])
+{
+    const double d[3] = {r[0] - rt[0], r[1] - rt[1], r[2] - rt[2]};
+    const double R = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    if (!(R > 0.0)) return; /* the target itself carries weight rho = 0 */
+    const cplx dg = (I * k - 1.0 / R) * cexp(I * (k * R + phi_in)) / (4.0 * OR_PI * R);
+    const cplx G[3] = {dg * d[0] / R, dg * d[1] / R, dg * d[2] / R};
+    cplx c[3];
+    ccross(Jt, G, c);
+    for (int q = 0; q < 3; ++q) acc[q] += c[q] * dS;
+}
+
+/* PO current J0 = 2 n x B_inc at the mirror point above (x, y), without its
+ * phase, which goes to phi_in: B_inc = (-z) x E_inc of reading R4. */
+static void mfie_po_current(const or_mirror* m, const or_beam* bm, double k, double x, double y, cplx J[3],
+                            double* phi_in, double* area)
+{
+    double nv[3];
+    surf_normal(m, x, y, nv);
+    const double nlen = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+    double es[3];
+    beam_field(bm, x, y, es);
+    const cplx nh[3] = {nv[0] / nlen, nv[1] / nlen, nv[2] / nlen};
+    const cplx Bt[3] = {es[1], -es[0], 0.0};
+    cplx c[3];
+    ccross(nh, Bt, c);
+    for (int q = 0; q < 3; ++q) J[q] = 2.0 * c[q];
+    const double z = surf_z(m, sqrt(x * x + y * y));
+    *phi_in = k * (beam_opd(bm, x, y) - (z + surf_zref(m)));
+    *area = nlen;
+}
+
+/* dJ at the mirror point above (xt, yt), polar rule of n_rho x n_phi points;
+ * gx, gw: Gauss-Legendre nodes and weights on [0, 1]. */
+static void mfie_dj(const or_mirror* m, const or_beam* bm, double k, double xt, double yt, int n_rho,
+                    const double* gx, const double* gw, int n_phi, cplx dJ[3])
+{
+    const double rt[3] = {xt, yt, surf_z(m, sqrt(xt * xt + yt * yt))};
+    double nv[3];
+    surf_normal(m, xt, yt, nv);
+    const double nlen = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+    const cplx nt[3] = {nv[0] / nlen, nv[1] / nlen, nv[2] / nlen};
+    cplx acc[3] = {0.0, 0.0, 0.0};
+    const double dphi = 2.0 * OR_PI / n_phi;
+    for (int j = 0; j < n_phi; ++j) {
+        const double ux = cos(j * dphi), uy = sin(j * dphi);
+        /* rho_max: |(xt, yt) + rho u| = r_max */
+        const double b = xt * ux + yt * uy, c = xt * xt + yt * yt - m->r_max * m->r_max;
+        const double rho_max = -b + sqrt(b * b - c);
+        for (int i = 0; i < n_rho; ++i) {
+            const double rho = rho_max * gx[i];
+            const double x = xt + rho * ux, y = yt + rho * uy;
+            cplx J[3];
+            double phi_in, area;
+            mfie_po_current(m, bm, k, x, y, J, &phi_in, &area);
+            const double r[3] = {x, y, surf_z(m, sqrt(x * x + y * y))};
+            mfie_term(k, r, rt, J, phi_in, area * rho * gw[i] * rho_max * dphi, acc);
+        }
+    }
+    cplx c[3];
+    ccross(nt, acc, c);
+    for (int q = 0; q < 3; ++q) dJ[q] = 2.0 * c[q];
+}
+
+static int mfie_supported(const or_mirror* m, const or_beam* bm)
+{
+    if (m->r_min != 0.0 || m->n_r < 1 || m->n_theta < 1 || !(m->r_max > 0.0)) return 0;
+    if (m->surface == 0 && !(m->f > 0.0)) return 0;
+    return bm->profile <= 2 && bm->order == 0;
+}
+
+/* dJ at n_t targets (x, y) on the mirror for one wavenumber, out[n_t][3]
+ * complex.  Returns 0, or 1 if the mirror or beam is not supported (an
+ * annulus, a beam of order 1, profiles 3-5). */
+int or_mfie_current(const or_mirror* m, const or_beam* bm, double k, int n_t, const double* xy, int n_rho,
+                    int n_phi, double* out)
+{
+    if (!mfie_supported(m, bm) || n_rho < 1 || n_phi < 1) return 1;
+    double* gx = (double*)malloc(sizeof(double) * n_rho);
+    double* gw = (double*)malloc(sizeof(double) * n_rho);
+    or_gauss_legendre(n_rho, 0.0, 1.0, gx, gw);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int t = 0; t < n_t; ++t) {
+        cplx dJ[3];
+        mfie_dj(m, bm, k, xy[2 * t], xy[2 * t + 1], n_rho, gx, gw, n_phi, dJ);
+        for (int q = 0; q < 3; ++q) {
+            out[6 * t + 2 * q] = creal(dJ[q]);
+            out[6 * t + 2 * q + 1] = cimag(dJ[q]);
+        }
+    }
+    free(gx);
+    free(gw);
+    return 0;
+}
+
+/* The physical-optics field (Eq. 11, or_field form 0) plus the field of the
+ * first MFIE correction dJ, evaluated at the mirror's surface nodes (its
+ * Gauss-Legendre x trapezoid rule) with the polar rule n_rho x n_phi.
+ * Layouts and amp as or_field.  Returns 0, or nonzero on invalid input. */
+int or_field_mfie(const or_mirror* m, const or_beam* bm, int n_omega, const double* omega, const double* amp,
+                  int n_pts, const double* pts, int n_rho, int n_phi, double* E_out, double* B_out, int nthreads)
+{
+    if (!mfie_supported(m, bm) || n_rho < 1 || n_phi < 1) return 1;
+    int rc = or_field(m, bm, 0, n_omega, omega, amp, n_pts, pts, E_out, B_out, nthreads);
+    if (rc) return rc;
+    const int nr = m->n_r, nt = m->n_theta;
+    double* rr = (double*)malloc(sizeof(double) * nr);
+    double* rw = (double*)malloc(sizeof(double) * nr);
+    if (m->radial == 1) or_simpson(nr, m->r_min, m->r_max, rr, rw);
+    else or_gauss_legendre(nr, m->r_min, m->r_max, rr, rw);
+    double* gx = (double*)malloc(sizeof(double) * n_rho);
+    double* gw = (double*)malloc(sizeof(double) * n_rho);
+    or_gauss_legendre(n_rho, 0.0, 1.0, gx, gw);
+    const long ns = (long)nr * nt;
+    const double dth = 2.0 * OR_PI / nt;
+    cplx* dJ = (cplx*)malloc(sizeof(cplx) * 3 * ns * n_omega);
+    /* dJ at every surface node and frequency */
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (long idx = 0; idx < ns * n_omega; ++idx) {
+        const int n = (int)(idx / ns);
+        const long s = idx % ns;
+        const double r = rr[s / nt], th = (s % nt) * dth;
+        mfie_dj(m, bm, 2.0 * OR_PI * omega[n], r * cos(th), r * sin(th), n_rho, gx, gw, n_phi, dJ + 3 * idx);
+    }
+    /* the field of dJ at the observation points */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (long idx = 0; idx < (long)n_omega * n_pts; ++idx) {
+        const int n = (int)(idx / n_pts), p = (int)(idx % n_pts);
+        const double k = 2.0 * OR_PI * omega[n];
+        const double* rp = pts + 3 * p;
+        cplx E[3] = {0.0, 0.0, 0.0}, B[3] = {0.0, 0.0, 0.0};
+        for (long s = 0; s < ns; ++s) {
+            const double r = rr[s / nt], th = (s % nt) * dth;
+            const double x = r * cos(th), y = r * sin(th), z = surf_z(m, r);
+            double nv[3];
+            surf_normal(m, x, y, nv);
+            const double dS = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]) * r * rw[s / nt] * dth;
+            const cplx* J = dJ + 3 * ((long)n * ns + s);
+            const double d[3] = {x - rp[0], y - rp[1], z - rp[2]};
+            const double R = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            const double Rh[3] = {d[0] / R, d[1] / R, d[2] / R};
+            const cplx g = cexp(I * k * R) / (4.0 * OR_PI * R);
+            const cplx a_iso = -(-I * k / R + 1.0 / (R * R)) * g;
+            const cplx a_rr = (3.0 / (R * R) - 3.0 * I * k / R - k * k) * g;
+            const cplx RJ = Rh[0] * J[0] + Rh[1] * J[1] + Rh[2] * J[2];
+            const cplx dg = (I * k - 1.0 / R) * g;
+            const cplx G[3] = {dg * Rh[0], dg * Rh[1], dg * Rh[2]};
+            cplx JxG[3];
+            ccross(J, G, JxG);
+            for (int c = 0; c < 3; ++c) {
+                E[c] += (I * k * J[c] * g + (I / k) * (a_iso * J[c] + a_rr * Rh[c] * RJ)) * dS;
+                B[c] += JxG[c] * dS;
+            }
+        }
+        const cplx a = amp ? amp[2 * n] + I * amp[2 * n + 1] : 1.0;
+        for (int c = 0; c < 3; ++c) {
+            const long o = 2 * (idx * 3 + c);
+            E_out[o] += creal(a * E[c]);
+            E_out[o + 1] += cimag(a * E[c]);
+            B_out[o] += creal(a * B[c]);
+            B_out[o + 1] += cimag(a * B[c]);
+        }
+    }
+    free(dJ);
+    free(gx);
+    free(gw);
+    free(rr);
+    free(rw);
+    return 0;
+}
+
+/* Pin of the MFIE operator itself on a sphere of radius a (a closed surface,
+ * used only by the tests): K[J](r_t) = n_t x PV SS J(r) x grad g(r, r_t) dS
+ * for the current J = (z x r^) (K0 = 1), evaluated at n_t targets (unit
+ * vectors) in geodesic polar coordinates about each target: the angle psi
+ * from the target (Gauss-Legendre on [0, pi], n_psi) and the azimuth around
+ * it (trapezoid, n_phi); dS = a^2 sin psi dpsi dphi, whose sin psi cancels
+ * the 1/R of the integrand.  out[n_t][3] complex.  Returns 0. */
+int or_mfie_sphere_te1(double a, double k, int n_t, const double* tgt, int n_psi, int n_phi, double* out)
+{
+    double* gx = (double*)malloc(sizeof(double) * n_psi);
+    double* gw = (double*)malloc(sizeof(double) * n_psi);
+    or_gauss_legendre(n_psi, 0.0, OR_PI, gx, gw);
+    const double dphi = 2.0 * OR_PI / n_phi;
+    for (int t = 0; t < n_t; ++t) {
+        const double* e3 = tgt + 3 * t;
+        /* an orthonormal frame (e1, e2, e3) about the target direction */
+        double h[3] = {1.0, 0.0, 0.0};
+        if (fabs(e3[0]) > 0.9) { h[0] = 0.0; h[1] = 1.0; }
+        double e1[3] = {h[1] * e3[2] - h[2] * e3[1], h[2] * e3[0] - h[0] * e3[2], h[0] * e3[1] - h[1] * e3[0]};
+        const double l1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+        for (int q = 0; q < 3; ++q) e1[q] /= l1;
+        const double e2[3] = {e3[1] * e1[2] - e3[2] * e1[1], e3[2] * e1[0] - e3[0] * e1[2],
+                              e3[0] * e1[1] - e3[1] * e1[0]};
+        const double rt[3] = {a * e3[0], a * e3[1], a * e3[2]};
+        cplx acc[3] = {0.0, 0.0, 0.0};
+        for (int j = 0; j < n_phi; ++j) {
+            const double cp = cos(j * dphi), sp = sin(j * dphi);
+            for (int i = 0; i < n_psi; ++i) {
+                const double ps = gx[i];
+                double u[3];
+                for (int q = 0; q < 3; ++q) u[q] = sin(ps) * (cp * e1[q] + sp * e2[q]) + cos(ps) * e3[q];
+                const double r[3] = {a * u[0], a * u[1], a * u[2]};
+                const cplx J[3] = {-u[1], u[0], 0.0}; /* z x r^ */
+                mfie_term(k, r, rt, J, 0.0, a * a * sin(ps) * gw[i] * dphi, acc);
+            }
+        }
+        const cplx nt[3] = {e3[0], e3[1], e3[2]};
+        cplx c[3];
+        ccross(nt, acc, c);
+        for (int q = 0; q < 3; ++q) {
+            out[6 * t + 2 * q] = creal(c[q]);
+            out[6 * t + 2 * q + 1] = cimag(c[q]);
+        }
+    }
+    free(gx);
+    free(gw);
     return 0;
 }

@@ -892,3 +892,132 @@ def test_ellipsoid_tends_to_the_paraboloid():
         E, _ = oracle.field(m, beam, [1.0], pts)
         d.append(np.max(np.abs(E - E0)) / np.max(np.abs(E0)))
     assert d[0] < 1e-2 and 8.0 < d[0] / d[1] < 12.0 and 8.0 < d[1] / d[2] < 12.0
+
+
+# --------------------------------------------------------------------------
+# The first correction of the MFIE's Liouville-Neumann series (Sec. II,
+# eq:theory.mfie): dJ = 2 n x PV SS J0 x grad g dS with J0 = 2 J_inc, and
+# the field of the corrected current
+
+
+def _mfie_sphere_eigenvalue(x):
+    """n x PV SS J x grad g dS = lam J on a sphere (radius a, x = ka) for
+    J = z x r^, from g = ik sum_l j_l(k r<) h_l(k r>) Y Y*: the current has
+    only l = 1, its vector potential is ik a^2 j_1 h_1 (z x r^), and the
+    principal value is the mean of the inner and outer limits of n x curl A:
+    lam = -(ika/2) [h_1 (x j_1)' + j_1 (x h_1)'] (-1/6 in the static limit)."""
+    from scipy.special import spherical_jn, spherical_yn
+
+    j, jp = spherical_jn(1, x), spherical_jn(1, x, derivative=True)
+    h = j + 1j * spherical_yn(1, x)
+    hp = jp + 1j * spherical_yn(1, x, derivative=True)
+    return -(1j * x / 2) * (h * (j + x * jp) + j * (h + x * hp))
+
+
+@pytest.mark.parametrize("ka", [1e-3, 0.5, 2.0, 5.0])
+def test_mfie_operator_on_a_sphere(ka):
+    """The MFIE operator of the oracle (its integrand and the polar handling of
+    the principal value) on a closed sphere, where J = z x r^ is an
+    eigenfunction with the closed-form eigenvalue above; at ka -> 0 it is the
+    magnetostatic -1/6 of a uniformly magnetised sphere (mean of the inner
+    2/3 M and outer -1/3 M tangential fields).  A flipped grad g, a swapped
+    cross product, the source normal in place of the target's or a dropped
+    ik term each change the result."""
+    pytest.importorskip("scipy")
+    t = np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0], [0.6, 0.0, 0.8], [0.3, -0.5, math.sqrt(0.66)]])
+    K = oracle.mfie_sphere_te1(1.0, ka, t, 32, 64)
+    lam = _mfie_sphere_eigenvalue(ka)
+    J = np.cross(np.array([0.0, 0.0, 1.0]), t)
+    assert np.max(np.abs(K - lam * J)) < 1e-12
+    if ka < 0.01:
+        assert abs(lam + 1.0 / 6.0) < 1e-6
+
+
+def test_mfie_correction_vanishes_on_a_flat_mirror():
+    """Sec. II: on a plane mirror physical optics is exact, and indeed
+    n x (J0 x grad g) = 0 when J0 and R^ both lie in the plane."""
+    m = dict(surface="flat", z0=0.0, r_max=6.0, n_r=12, n_theta=16, rim=1)
+    b = dict(profile="gauss", pol="linear", w0=3.0, pol_angle=0.3)
+    dJ = oracle.mfie_current(m, b, 1.0, [[0.3, -0.7], [2.0, 1.0], [-4.0, 0.5]], 32, 64)
+    assert np.max(np.abs(dJ)) == 0.0
+    pts = np.array([[0.2, 0.1, 2.0], [-0.4, 0.3, 3.5]])
+    E0, B0 = oracle.field(m, b, [1.0, 1.2], pts)
+    E1, B1 = oracle.field_mfie(m, b, [1.0, 1.2], pts, 16, 32)
+    assert np.array_equal(E0, E1) and np.array_equal(B0, B1)
+
+
+def test_mfie_polar_rule_converges_spectrally():
+    """The polar rule about each target is smooth in (rho, phi) (the factor
+    rho cancels the 1/R of the integrand): on the paraboloid the correction
+    converges to 1e-9 by 48 x 96 points, and vanishes at the vertex of an
+    x-polarised beam (its angular dependence there is cos 2theta, sin 2theta)."""
+    m = dict(f=5.0, r_max=10.0, n_r=8, n_theta=8, rim=1)
+    b = dict(profile="gauss", pol="linear", w0=5.0)
+    tx = np.array([[1.0, 0.5], [4.0, -3.0], [0.0, 0.0]])
+    ref = oracle.mfie_current(m, b, 1.0, tx, 160, 320)
+    scale = np.max(np.abs(ref))
+    errs = [np.max(np.abs(oracle.mfie_current(m, b, 1.0, tx, n, 2 * n) - ref)) / scale for n in (24, 48, 96)]
+    assert errs[0] > 1e-6 and errs[1] < 1e-9 and errs[2] < 1e-9
+    assert np.max(np.abs(ref[2])) < 1e-9 * scale
+
+
+def test_mfie_correction_is_a_curvature_effect():
+    """Sec. II: the terms of the series get smaller when the radius of
+    curvature exceeds the wavelength.  At NA = 1 with w0 = f, the correction
+    relative to J0 = 2 J_inc is below 1% and falls from f = 5 to f = 40."""
+    rel = []
+    for f in (5.0, 10.0, 20.0, 40.0):
+        m = dict(f=f, r_max=2 * f, n_r=8, n_theta=8, rim=1)
+        b = dict(profile="gauss", pol="linear", w0=f)
+        x, y = 0.5 * f, 0.3 * f
+        dJ = oracle.mfie_current(m, b, 1.0, [[x, y]], int(12 * f) + 32, int(24 * f) + 64)
+        n = np.array([-x / (2 * f), -y / (2 * f), 1.0])
+        n /= np.linalg.norm(n)
+        J0 = 2 * math.exp(-(x * x + y * y) / f ** 2) * np.linalg.norm(np.cross(n, [0.0, -1.0, 0.0]))
+        rel.append(np.linalg.norm(dJ[0]) / J0)
+    assert max(rel) < 1e-2
+    assert rel[-1] < rel[0] and rel[-1] < rel[1]
+
+
+def test_mfie_correction_field_obeys_maxwell():
+    """The field of the correction current alone (Sancer's representation with
+    the Appendix-A dyadic) satisfies Faraday, Ampere and div E = 0 in free
+    space for any current: a slip in the isotropic or R^R^ part of the dyadic
+    breaks Ampere or div E."""
+    f, om = 4.0, 1.0
+    k = K0 * om
+    m = dict(f=f, r_max=8.0, n_r=24, n_theta=24, rim=1)
+    b = dict(profile="gauss", pol="linear", w0=4.0, pol_angle=0.2)
+    p0, h = np.array([0.21, -0.13, 0.17]), 2e-3
+    offs = [p0]
+    for ax in range(3):
+        for s in (-2, -1, 1, 2):
+            q = p0.copy()
+            q[ax] += s * h
+            offs.append(q)
+    pts = np.array(offs)
+    E0, B0 = oracle.field(m, b, [om], pts)
+    E1, B1 = oracle.field_mfie(m, b, [om], pts, 48, 96)
+    dE, dB = (E1 - E0)[0], (B1 - B0)[0]
+
+    def d(F, ax, c):
+        i = 1 + 4 * ax
+        return (-F[i + 3, c] + 8 * F[i + 2, c] - 8 * F[i + 1, c] + F[i, c]) / (12 * h)
+
+    def curl(F):
+        return np.array([d(F, 1, 2) - d(F, 2, 1), d(F, 2, 0) - d(F, 0, 2), d(F, 0, 1) - d(F, 1, 0)])
+
+    scale = k * np.linalg.norm(dE[0])
+    assert np.linalg.norm(dE[0]) > 1e-4 * np.linalg.norm(E0[0, 0])  # the correction is visible
+    assert np.linalg.norm(curl(dE) - 1j * k * dB[0]) < 1e-6 * scale
+    assert np.linalg.norm(curl(dB) + 1j * k * dE[0]) < 1e-6 * scale
+    assert abs(d(dE, 0, 0) + d(dE, 1, 1) + d(dE, 2, 2)) < 1e-6 * scale
+
+
+def test_mfie_rejects_annulus_and_fitted_beams():
+    with pytest.raises(ValueError):
+        oracle.mfie_current(dict(f=5.0, r_min=1.0, r_max=10.0, n_r=8, n_theta=8), dict(profile="gauss", w0=5.0),
+                            1.0, [[2.0, 0.0]], 16, 32)
+    with pytest.raises(ValueError):
+        oracle.mfie_current(dict(f=5.0, r_max=10.0, n_r=8, n_theta=8), dict(profile="gauss", w0=5.0, order=1),
+                            1.0, [[2.0, 0.0]], 16, 32)
