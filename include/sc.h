@@ -565,6 +565,12 @@ enum {
     SC_OPT_OMEGA_CHUNKS = 7,    /* 1 (default): cut a request's omegas into chunks  */
                                 /* that keep the field kernels' threads busy;      */
                                 /* 0: one chunk per 2048 omegas                     */
+    SC_OPT_MFIE_ORDER = 9,      /* 0 (default): physical optics; 1: add the first  */
+                                /* correction of the MFIE's Liouville-Neumann      */
+                                /* series (see below; sc_eval, sc_eval_time_domain) */
+    SC_OPT_MFIE_RHO = 10,       /* its polar rule: Gauss-Legendre points per ray    */
+                                /* (default 64)                                     */
+    SC_OPT_MFIE_PHI = 11,       /* ... and rays about each node (default 128)       */
     SC_OPT_FAIL_COPY = 8        /* failure-path test, -1 (default) off: in every   */
                                 /* batched FP32 field launch, the work item 0 skips */
                                 /* the bulk copy of its node tile `value`, so the   */
@@ -573,6 +579,31 @@ enum {
                                 /* reports SC_ERR_TIMEOUT                           */
 };
 sc_status sc_set_option(sc_ctx* ctx, int option, long long value);
+
+/*
+ * The first correction beyond physical optics (SC_OPT_MFIE_ORDER = 1).  Sec. II
+ * writes the mirror current as the solution of the magnetic-field integral
+ * equation (1/2) J = J_inc + n x PV SS J x grad g dS and solves it by its
+ * Liouville-Neumann series, whose first term is physical optics, J0 =
+ * 2 J_inc (all of the field above).  With the option set, sc_eval (and
+ * sc_eval_time_domain, which calls it per chunk) adds the next term:
+ *   dJ(r_t) = 2 n_t x PV SS J0(r) x grad g(r, r_t) dS(r)
+ * at every surface node r_t, and the field of dJ at the points, from
+ * Sancer's representation with n x E = 0 (Eq. 10's form for a general
+ * current): E += SS {ik dJ g + (i/k) grad grad g . dJ} dS, B += SS dJ x
+ * grad g dS, on the mirror's own nodes.  The principal value is taken in
+ * polar coordinates about each node (Gauss-Legendre in rho from the node to
+ * the rim, SC_OPT_MFIE_RHO points; SC_OPT_MFIE_PHI rays), whose Jacobian
+ * cancels the O(1/R) integrand.  The polar rule must resolve the phase of
+ * g between mirror points (tens of points per wavelength of path along a
+ * ray), and the node grid must resolve dJ: the correction is meant for
+ * mirrors of tens to hundreds of wavelengths, where it is of order
+ * lambda / (curvature radius).  Both correction sums run in FP64 and cost
+ * n_nodes x n_rho x n_phi and n_points x n_nodes evaluations per omega.
+ * Needs a disk (r_min = 0), a paraboloid or ellipsoid, and a collimated beam
+ * (kinds 0-2) of order 0; other pairs, sc_eval_batch, sc_submit and
+ * sc_eval_fp32_static are refused with SC_ERR_INVALID while the option is set.
+ */
 
 #ifdef __cplusplus
 }

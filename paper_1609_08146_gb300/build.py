@@ -25,7 +25,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I" + INCLUDE, "-I" + CSRC]
 SOURCES = ["sc_api.cpp", "sc_tables.cpp", "sc_batch.cpp", "sc_serve.cpp", "sc_field.cu", "sc_reduce.cu",
-           "sc_f64_idft.cu", "sc_static_scratch.cu", "sc_peaks.cu"]
+           "sc_f64_idft.cu", "sc_static_scratch.cu", "sc_peaks.cu", "sc_mfie.cu", "sc_mfie_host.cpp"]
 
 
 def _nvcc() -> str:

@@ -133,7 +133,8 @@ sc_status sc_destroy(sc_ctx* ctx)
     for (auto& t : ctx->tables) free_table(ctx, t);
     for (DevBuf* b : {&ctx->pts, &ctx->outE, &ctx->outB, &ctx->tkval, &ctx->tvals, &ctx->phasor,
                       &ctx->specE, &ctx->specB, &ctx->tE, &ctx->tB, &ctx->fpts, &ctx->fspecE,
-                      &ctx->fspecB, &ctx->ftE, &ctx->ftB})
+                      &ctx->fspecB, &ctx->ftE, &ctx->ftB, &ctx->mfie_geo, &ctx->mfie_zern, &ctx->mfie_gl,
+                      &ctx->mfie_dJ})
         if (b->p) cudaFree(b->p);
     free_lane(ctx->main);
     for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
@@ -322,6 +323,8 @@ static sc_status eval_unlocked(sc_ctx* ctx, const sc_mirror_t* m, const sc_incid
     const bool timing_before = ctx->time_field;
     if (stats) ctx->time_field = true;
 
+    if (ctx->mfie_order > 0)
+        if (const char* why = mfie_unsupported(m, in)) return fail(ctx, SC_ERR_INVALID, "%s", why);
     Table* tab = nullptr;
     sc_status st = get_table(ctx, m, in, &tab, ctx->stream);
     if (st != SC_OK) return st;
@@ -407,6 +410,11 @@ static sc_status eval_unlocked(sc_ctx* ctx, const sc_mirror_t* m, const sc_incid
         if (st != SC_OK) return st;
     }
     ctx->ctr.evals += evals;
+    // the first MFIE correction beyond physical optics (Sec. II), added to the outputs
+    if (ctx->mfie_order > 0) {
+        st = mfie_correction(ctx, m, in, n_omega, d_pts, n_points, d_amp, d_k, dE, dB, prec == SC_FP64);
+        if (st != SC_OK) return st;
+    }
 
     if (!e_dev) {
         SC_CUDA(cudaMemcpyAsync(E_out, dE, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "download E");
@@ -572,6 +580,8 @@ sc_status sc_eval_batch(sc_ctx* ctx, const sc_request* reqs, int n_req, sc_eval_
 {
     if (!ctx) return SC_ERR_INVALID;
     if (!reqs || n_req < 1) return fail(ctx, SC_ERR_INVALID, "invalid argument");
+    if (ctx->mfie_order > 0)
+        return fail(ctx, SC_ERR_INVALID, "the MFIE correction runs through sc_eval and sc_eval_time_domain only");
     std::vector<double> dom(n_req);
     size_t n_om_total = 0;
     for (int r = 0; r < n_req; ++r) {
@@ -680,6 +690,8 @@ sc_status sc_eval_fp32_static(sc_ctx* ctx, const sc_mirror_t* m, const sc_incide
         (B_out && !is_device_ptr(B_out)))
         return fail(ctx, SC_ERR_INVALID,
                     "amp_re_im, points_xyz, E_out and B_out must be device memory on this path");
+    if (ctx->mfie_order > 0)
+        return fail(ctx, SC_ERR_INVALID, "the MFIE correction runs through sc_eval and sc_eval_time_domain only");
     if (n_omega > kMaxOmega)
         return fail(ctx, SC_ERR_INVALID, "n_omega %d exceeds %d for the static-scratch path", n_omega,
                     kMaxOmega);
@@ -842,6 +854,8 @@ sc_status sc_submit(sc_ctx* ctx, const sc_request* req, uint64_t* ticket)
     if (!req || !ticket || !req->mirror || !req->incident || !req->omegas || !req->points_xyz ||
         req->n_omega < 1 || req->n_points < 1 || req->n_omega > 2048 * 64)
         return fail(ctx, SC_ERR_INVALID, "invalid request");
+    if (ctx->mfie_order > 0)
+        return fail(ctx, SC_ERR_INVALID, "the MFIE correction runs through sc_eval and sc_eval_time_domain only");
     double dom = 0.0;
     for (int i = 0; i < req->n_omega; ++i)
         if (!(req->omegas[i] > 0.0) || !std::isfinite(req->omegas[i]))
@@ -1109,6 +1123,15 @@ sc_status sc_set_option(sc_ctx* ctx, int option, long long value)
     case SC_OPT_WORKSPACE_CAP:
         if (value < (1 << 20)) return fail(ctx, SC_ERR_INVALID, "workspace cap below 1 MiB");
         ctx->ws_cap = (size_t)value;
+        return SC_OK;
+    case SC_OPT_MFIE_ORDER:
+        if (value < 0 || value > 1) return fail(ctx, SC_ERR_INVALID, "MFIE order must be 0 or 1");
+        ctx->mfie_order = (int)value;
+        return SC_OK;
+    case SC_OPT_MFIE_RHO:
+    case SC_OPT_MFIE_PHI:
+        if (value < 1 || value > 65536) return fail(ctx, SC_ERR_INVALID, "polar rule size out of range");
+        (option == SC_OPT_MFIE_RHO ? ctx->mfie_rho : ctx->mfie_phi) = (int)value;
         return SC_OK;
     case SC_OPT_FAIL_COPY:
         if (value < -1 || value > (1 << 30)) return fail(ctx, SC_ERR_INVALID, "tile index out of range");

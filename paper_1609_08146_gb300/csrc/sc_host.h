@@ -141,6 +141,9 @@ struct sc_ctx {
     bool autotune = true;
     bool omega_chunks = true;       // plan omega chunk sizes (else 2048 per chunk)
     int fail_tile = -1;             // failure-path test: a node-tile copy left unissued
+    int mfie_order = 0;             // 1: add the first MFIE correction (sc_eval)
+    int mfie_rho = 64, mfie_phi = 128;  // its polar rule about each node
+    sch::DevBuf mfie_geo, mfie_zern, mfie_gl, mfie_dJ;
     uint64_t graph_tick = 0;
     uint64_t graph_captures = 0, graph_replays = 0;
     std::map<std::tuple<int, int, int, int, int, int>, int> tuned;  // shape -> split count
@@ -189,6 +192,23 @@ cudaEvent_t take_event(sc_ctx* ctx);
 void settle_events(sc_ctx* ctx);
 sc_status check_points_host(sc_ctx* ctx, const sc_mirror_t* m, const double* pts, int n_pts);
 bool uniform_grid(const double* om, int n, double& d);
+void radial_rule(const sc_mirror_t* m, std::vector<double>& x, std::vector<double>& w);
+void gauss_legendre(int n, double a, double b, std::vector<double>& x, std::vector<double>& w);
+void noll_nm(int j, int& n, int& m);
+struct SurfPt {
+    double z, dzdr, pn, extra;
+};
+SurfPt surf_at(const sc_mirror_t* m, double r);
+
+// ---- the first MFIE correction (sc_mfie_host.cpp)
+// Why the pair cannot take it, or nullptr.
+const char* mfie_unsupported(const sc_mirror_t* m, const sc_incident_t* in);
+// Adds the field of the first MFIE correction of (m, in) to the outputs dE,
+// dB (device, [n_omega][n_points][3], double2 if f64 else float2) on
+// ctx->stream; d_amp, d_k: a_n and k_n on the device.
+sc_status mfie_correction(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in, int n_omega,
+                          const double* d_pts, int n_points, const double* d_amp, const double* d_k, void* dE,
+                          void* dB, bool f64);
 
 // ---- batched FP32 execution (sc_batch.cpp)
 struct Chunk {

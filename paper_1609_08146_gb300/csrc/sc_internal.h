@@ -149,6 +149,51 @@ struct IdftLaunch {
 };
 int launch_idft(const IdftLaunch& p, cudaStream_t s);
 
+// First correction beyond physical optics (sc_mfie.cu): the current dJ of the
+// MFIE's Liouville-Neumann series at every surface node, by a polar rule about
+// each node, and the field of dJ at the observation points.  FP64.
+struct MfieZern {           // c_j Z_j = P(u^2 + v^2) {1, Re, Im}((u + iv)^m)
+    int m;                  // |m|
+    int kind;               // 0: m = 0, 1: cos (Re), 2: sin (Im)
+    int deg;                // degree of P in u^2 + v^2
+    double p[6];            // coefficients of P, constant first (times c_j N_j)
+};
+struct MfieLaunch {
+    int surface;            // 0 paraboloid (f), 2 ellipsoid (c_ell, e_ell)
+    double f, c_ell, e_ell;
+    double zref;            // incident phase reference e^{-ik(z + zref)}
+    double r_max;           // rim of the disk
+    int profile, sg_order, pol;
+    double w0, cos_a, sin_a;
+    const MfieZern* zern;   // [n_zern], optical path in units of lambda0
+    int n_zern;
+    double r_norm;          // radius of the Zernike unit disk
+    const double* gx;       // Gauss-Legendre nodes and weights on [0, 1] [n_rho]
+    const double* gw;
+    int n_rho, n_phi;
+    const double4* geo;     // surface nodes (x, y, z, dS) [n_surf]
+    int n_surf;
+    const double* kval;     // [n_omega]
+    int n_omega;
+    double2* dJ;            // out [n_omega][n_surf][3]
+};
+struct MfieFieldLaunch {
+    const double4* geo;     // (x, y, z, dS) [n_surf]
+    int n_surf;
+    const double2* dJ;      // [n_omega][n_surf][3]
+    const double* pts;      // [n_pts][3]
+    int n_pts;
+    const double* kval;     // [n_omega]
+    int n_omega;
+    const double* amp;      // a_n [n_omega][2]
+    void* E;                // added to: [n_omega][n_pts][3] float2 or double2
+    void* B;                // nullable
+    int f64;
+    long long out_stride_omega;  // n_pts * 3
+};
+int launch_mfie_current(const MfieLaunch& p, cudaStream_t s);
+int launch_mfie_field(const MfieFieldLaunch& p, cudaStream_t s);
+
 // Failure-path self-test: one bounded mbarrier wait that nothing completes.
 int launch_wait_selftest(int* err, cudaStream_t s);
 

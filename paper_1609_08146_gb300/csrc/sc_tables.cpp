@@ -352,13 +352,9 @@ sc_status spectrum_amps(sc_ctx* ctx, const sc_incident_t* in, const double* om, 
 // ------------------------------------------------------------------------
 // Mirror surfaces of revolution z = F(r), focus (F2) at the origin.
 
-struct SurfPt {
-    double z, dzdr;  // F(r), F'(r): n dS = (-F' cos, -F' sin, 1) r dr dtheta
-    double pn;       // |P|, the distance to the focus
-    double extra;    // optical path added to W so that the kernel's phase
-                     // R - |P| + W equals R - (z + z_ref) + W (collimated beams)
-};
-
+// SurfPt (sc_host.h): F(r), F'(r) (n dS = (-F' cos, -F' sin, 1) r dr dtheta),
+// |P| (the distance to the focus) and the optical path added to W so that
+// the kernel's phase R - |P| + W equals R - (z + z_ref) + W (collimated beams).
 SurfPt surf_at(const sc_mirror_t* m, double r)
 {
     SurfPt p;
