@@ -45,9 +45,10 @@ sys.path.insert(0, ROOT)
 
 OPS_PER_EVAL = 28     # algorithmic FP32 instructions per (point, node, omega) of the factorised summand
 KERNEL_OPS_PER_EVAL = 24  # what the kernel issues: three-term phasor recurrence, packed FMAs
-FIELD_KERNEL = "field_grouped_kernel<32>"
-PROFILE_JSON = os.path.join(ROOT, "profiles", "field_grouped_broadband.json")
-FIELD_SRC = os.path.join(ROOT, "paper_1609_08146_gb300", "csrc", "sc_field.cu")
+FIELD_KERNEL = "field_direct_kernel<8, 32>"  # 256 omegas: 32 threads of 8 omegas per point
+PROFILE_JSON = os.path.join(ROOT, "profiles", "field_direct_broadband.json")
+CSRC = os.path.join(ROOT, "paper_1609_08146_gb300", "csrc")
+FIELD_SRCS = [os.path.join(CSRC, f) for f in ("sc_field_direct.cu", "sc_field_common.cuh")]
 
 
 def parse():
@@ -241,10 +242,10 @@ def rel_l2(F, R):
 
 def profile_traffic():
     """DRAM bytes per launch of the field kernel from the committed ncu
-    summary, only while the kernel source is unchanged since the capture."""
+    summary, only while the kernel's sources are unchanged since the capture."""
     try:
         prof = json.load(open(PROFILE_JSON))
-        sha = hashlib.sha256(open(FIELD_SRC, "rb").read()).hexdigest()
+        sha = hashlib.sha256(b"".join(open(f, "rb").read() for f in FIELD_SRCS)).hexdigest()
         if prof.get("source_sha256") == sha:
             return prof.get("dram_bytes_per_launch")
     except (OSError, ValueError):
@@ -660,7 +661,7 @@ def main():
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s",
             "frac": achieved / peak,
             "traffic": profile_traffic() if args.workload != "small_omega" else None,
-            "kernel": FIELD_KERNEL if args.workload != "small_omega" else "field_direct_kernel<8, 1>",
+            "kernel": FIELD_KERNEL if args.workload != "small_omega" else "field_direct_kernel<4, 2>",
             "ops_per_eval": OPS_PER_EVAL,
             "ops_basis": "algorithmic work per evaluation: complex rotation (4) + 12 real coefficients "
                          "x complex phasor (24)",

@@ -24,7 +24,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host symbols are hidden: the library exports only the extern "C" API of sc.h
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I" + INCLUDE, "-I" + CSRC]
-SOURCES = ["sc_api.cpp", "sc_tables.cpp", "sc_batch.cpp", "sc_serve.cpp", "sc_field.cu", "sc_reduce.cu",
+SOURCES = ["sc_api.cpp", "sc_tables.cpp", "sc_batch.cpp", "sc_serve.cpp", "sc_field.cu", "sc_field_direct.cu",
+           "sc_reduce.cu",
            "sc_f64_idft.cu", "sc_static_scratch.cu", "sc_peaks.cu", "sc_mfie.cu", "sc_mfie_host.cpp"]
 
 

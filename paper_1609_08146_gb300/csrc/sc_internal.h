@@ -84,11 +84,15 @@ struct BatchLaunch {
     int fail_tile;
 };
 
-// Kernel class for a chunk of n_omega (<= 2048) omegas: 0..16 the direct
-// kernel (1, 2, 4 or 8 threads per point, 1..8 omegas per thread, up to 48
-// omegas), 17..22 the grouped kernel with 8 ... 256 threads per point.
-constexpr int kNumClasses = 23;
+// Kernel class for a chunk of n_omega (<= 2048) omegas: 0..20 the direct
+// kernel (1 to 32 threads per point, 1..8 omegas per thread, up to 256
+// omegas), 21..23 the grouped kernel with 64, 128, 256 threads per point.
+constexpr int kNumClasses = 24;
+constexpr int kFirstGroupedClass = 21;
 int field_class(int n_omega);
+// the direct kernel's classes (0 .. kFirstGroupedClass - 1), in sc_field_direct.cu
+void direct_field_shape(int cls, int device, int* points_per_item, int* resident_ctas);
+int launch_direct_field(int cls, const BatchLaunch& b, int grid, cudaStream_t s);
 // Observation points per work item and resident CTAs on the device.
 void field_shape(int cls, int device, int* points_per_item, int* resident_ctas);
 // Launch one class; grid = CTAs (queue mode: resident slots; grid mode:
