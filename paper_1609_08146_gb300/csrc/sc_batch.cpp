@@ -128,15 +128,16 @@ sc_status choose_splits(sc_ctx* ctx, Lane& ln, Chunk& c, const Table* tab, int s
 // chunk of its capacity (the next power of two >= n).
 constexpr double kRateSmall[65] = {
     0.0,
-    3.493, 3.856, 4.961, 5.612, 6.351, 7.100, 7.120, 7.285,  // 1..8
-    6.465, 7.182, 7.520, 8.184, 7.379, 7.943, 7.926, 8.406,  // 9..16
-    6.345, 6.713, 7.084, 7.459, 7.204, 7.541, 7.889, 8.216,  // 17..24
-    6.810, 7.087, 7.357, 7.610, 7.889, 8.156, 8.436, 8.662,  // 25..32
-    6.196, 6.379, 6.571, 6.757, 6.941, 7.127, 7.309, 7.502,  // 33..40
-    7.144, 7.317, 7.493, 7.655, 7.839, 8.014, 8.174, 8.353,  // 41..48
-    7.578, 7.724, 7.884, 8.027, 8.185, 8.334, 8.488, 8.623,  // 49..56
-    8.752, 8.895, 9.050, 9.197, 9.357, 9.502, 9.650, 9.768}; // 57..64
-constexpr double kRateFull[6] = {9.782, 10.59, 11.10, 10.78, 10.99, 10.81};  // 64 .. 2048
+    3.399, 3.924, 4.911, 5.553, 6.252, 6.758, 7.148, 7.384,  // 1..8
+    7.259, 8.060, 7.890, 8.577, 8.207, 8.836, 8.390, 8.890,  // 9..16
+    8.120, 8.587, 9.056, 9.537, 8.841, 9.248, 9.678, 10.071,  // 17..24
+    8.142, 8.468, 8.793, 9.088, 9.424, 9.740, 10.071, 10.320,  // 25..32
+    8.250, 8.493, 8.752, 8.998, 9.241, 9.231, 9.463, 9.716,  // 33..40
+    9.098, 9.318, 9.542, 9.746, 9.983, 10.207, 10.404, 10.628,  // 41..48
+    9.658, 9.858, 10.037, 10.233, 10.433, 10.612, 10.804, 11.022,  // 49..56
+    9.914, 10.071, 10.248, 10.414, 10.607, 10.775, 10.941, 11.064,  // 57..64
+};
+constexpr double kRateFull[6] = {11.07, 11.42, 11.71, 10.82, 11.04, 10.88};  // 64 .. 2048
 
 constexpr int kMaxChunk = 2048;
 
