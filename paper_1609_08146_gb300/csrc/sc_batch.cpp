@@ -128,16 +128,16 @@ sc_status choose_splits(sc_ctx* ctx, Lane& ln, Chunk& c, const Table* tab, int s
 // chunk of its capacity (the next power of two >= n).
 constexpr double kRateSmall[65] = {
     0.0,
-    3.399, 3.924, 4.911, 5.553, 6.252, 6.758, 7.148, 7.384,  // 1..8
-    7.259, 8.060, 7.890, 8.577, 8.207, 8.836, 8.390, 8.890,  // 9..16
-    8.120, 8.587, 9.056, 9.537, 8.841, 9.248, 9.678, 10.071,  // 17..24
-    8.142, 8.468, 8.793, 9.088, 9.424, 9.740, 10.071, 10.320,  // 25..32
-    8.250, 8.493, 8.752, 8.998, 9.241, 9.231, 9.463, 9.716,  // 33..40
-    9.098, 9.318, 9.542, 9.746, 9.983, 10.207, 10.404, 10.628,  // 41..48
-    9.658, 9.858, 10.037, 10.233, 10.433, 10.612, 10.804, 11.022,  // 49..56
-    9.914, 10.071, 10.248, 10.414, 10.607, 10.775, 10.941, 11.064,  // 57..64
+    3.403, 3.934, 4.918, 5.565, 6.260, 6.763, 7.154, 7.456,  // 1..8
+    7.244, 8.041, 8.005, 8.710, 8.389, 9.031, 8.566, 9.086,  // 9..16
+    8.187, 8.659, 9.132, 9.619, 8.914, 9.325, 9.755, 10.153,  // 17..24
+    8.317, 8.653, 8.987, 9.288, 9.631, 9.957, 10.301, 10.564,  // 25..32
+    8.343, 8.591, 8.849, 9.100, 9.344, 9.593, 9.838, 10.100,  // 33..40
+    9.109, 9.327, 9.550, 9.756, 9.995, 10.215, 10.416, 10.639,  // 41..48
+    10.005, 10.209, 10.393, 10.596, 10.808, 10.989, 11.187, 11.413,  // 49..56
+    10.165, 10.331, 10.515, 10.682, 10.878, 11.047, 11.219, 11.345,  // 57..64
 };
-constexpr double kRateFull[6] = {11.07, 11.42, 11.71, 10.82, 11.04, 10.88};  // 64 .. 2048
+constexpr double kRateFull[6] = {11.35, 11.64, 12.01, 10.86, 11.06, 10.89};  // 64 .. 2048
 
 constexpr int kMaxChunk = 2048;
 

@@ -158,10 +158,11 @@ def test_chunk_planning_on_and_off(ctx):
     assert max(e_on, e_off) <= TOL32
 
 
-@pytest.mark.parametrize("n_omega", [17, 33, 41, 49])
+@pytest.mark.parametrize("n_omega", [25, 33, 41, 49])
 def test_small_count_cuts_on_a_large_request(ctx, n_omega):
     # 64 x 64 nodes and 1030 points: above 4M pairs per omega, so small counts
-    # are cut too (e.g. 33 as 1 + 32); a sample of the points against the oracle
+    # are cut too (e.g. 33 as 1 + 32, 41 as 10 + 31 under the measured tables);
+    # a sample of the points against the oracle
     mirror = dict(f=1000.0, r_max=2000.0, n_r=64, n_theta=64, rim=True)
     beam = dict(profile="supergauss", w0=1200.0, pol="azimuthal")
     om = wl.uniform_omegas(n_omega)
