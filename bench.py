@@ -24,7 +24,8 @@ Metric: obs x node x omega evaluations per second (surface nodes), whole job.
           the same workload.
 --impl reference times that oracle as the reference arm.
 Multi-GPU (torchrun): every rank evaluates its own copy of the workload
-(weak scaling, no data-path collective); timing is max over ranks.
+(weak scaling), or with --scaling strong its shard of the points; no data-path
+collective either way; timing is max over ranks.
 """
 from __future__ import annotations
 
@@ -72,6 +73,10 @@ def parse():
                          "batched leg at its full size (64 requests); sweep: the precision "
                          "sweep over f and node counts (per-component errors)")
     ap.add_argument("--grid", type=int, default=128, help="points per axis of the c5 workload")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="N > 1: weak = every rank evaluates the whole workload (replicas); strong = the "
+                         "points are sharded across ranks (sharding.py, no data-path collective) and the "
+                         "end-to-end leg gathers E(t) to rank 0 by host copy")
     return ap.parse_args()
 
 
@@ -587,6 +592,13 @@ def main():
                        spectrum=w["spectrum"])
     om, times = w["omegas"], w["times"]
     n_nodes = mc["n_r"] * mc["n_theta"]
+    strong = args.scaling == "strong" and world > 1
+    n_total = len(w["points"])
+    if strong:  # this rank's contiguous shard of the points
+        from paper_1609_08146_gb300.sharding import shard_range
+
+        lo, hi = shard_range(n_total, rank, world)
+        w = dict(w, points=w["points"][lo:hi])
     npts = len(w["points"])
     evals_per_step = float(npts) * n_nodes * len(om)
 
@@ -646,6 +658,10 @@ def main():
     for _ in range(args.steps):
         ctx.eval(m, inc, om, Ph, out=(E, B))          # points: pinned host -> device
         ctx.time_domain(E, B, om, times, out=(Eth, Bth))  # E(t), B(t): device -> pinned host
+        if strong:  # the whole E(t) on rank 0, by host copy over the process group
+            from paper_1609_08146_gb300.sharding import gather_points
+
+            gather_points(Eth, n_total, dim=1)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
     e2e_value = sum_over_ranks(pg, evals_per_step * args.steps) / e2e_s
@@ -726,13 +742,15 @@ def main():
         line = {
             "metric": "Stratton-Chu obs*node*omega evals/s", "value": value, "unit": "evals/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "strong" if strong else "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w["name"], "mirror_nodes": n_nodes, "points": npts,
                        "omegas": len(om), "time_samples": len(times), "f_lambda0": mc["f"],
                        "precision": "FP32 compensated phase, FP64 cross-split reduction",
                        "l2": "256 MB memset between steps, outside the timed events",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": ("points sharded over %d GPUs" % world if strong else
+                                       "replicas" if world > 1 else "single GPU")},
             "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(ctr["launches"]),
