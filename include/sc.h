@@ -571,6 +571,8 @@ enum {
     SC_OPT_MFIE_RHO = 10,       /* its polar rule: Gauss-Legendre points per ray    */
                                 /* (default 64)                                     */
     SC_OPT_MFIE_PHI = 11,       /* ... and rays about each node (default 128)       */
+    SC_OPT_CLASS_STREAMS = 12,  /* 1 (default): the field launches of a batch's     */
+                                /* kernel classes run as concurrent branches        */
     SC_OPT_FAIL_COPY = 8        /* failure-path test, -1 (default) off: in every   */
                                 /* batched FP32 field launch, the work item 0 skips */
                                 /* the bulk copy of its node tile `value`, so the   */

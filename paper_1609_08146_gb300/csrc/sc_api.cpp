@@ -1120,6 +1120,7 @@ sc_status sc_set_option(sc_ctx* ctx, int option, long long value)
     case SC_OPT_GRAPHS: ctx->use_graphs = value != 0; return SC_OK;
     case SC_OPT_AUTOTUNE: ctx->autotune = value != 0; return SC_OK;
     case SC_OPT_OMEGA_CHUNKS: ctx->omega_chunks = value != 0; return SC_OK;
+    case SC_OPT_CLASS_STREAMS: ctx->class_streams = value != 0; return SC_OK;
     case SC_OPT_WORKSPACE_CAP:
         if (value < (1 << 20)) return fail(ctx, SC_ERR_INVALID, "workspace cap below 1 MiB");
         ctx->ws_cap = (size_t)value;

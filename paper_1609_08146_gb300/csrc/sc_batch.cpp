@@ -355,11 +355,39 @@ sc_status launch_chunks(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch, float2* w
         b.fail_tile = ctx->fail_tile;
         launches.push_back({k, b, (int)std::min<long long>(slots, items[k])});
     }
+    // With several kernel classes, each persistent launch runs on a branch of
+    // its own (forked from the lane's stream and joined back into it), so the
+    // CTAs of one class fill the SMs that another class's tail leaves idle.
+    // Every item writes only its own workspace section and its arithmetic does
+    // not depend on scheduling, so results stay bitwise the same.
+    const bool branches = ctx->class_streams && launches.size() > 1;
+    if (branches) {
+        if (!ln.fork_ev) SC_CUDA(cudaEventCreateWithFlags(&ln.fork_ev, cudaEventDisableTiming), "fork event");
+        while (ln.side.size() < launches.size()) {
+            cudaStream_t b = nullptr;
+            cudaEvent_t e = nullptr;
+            SC_CUDA(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking), "class stream");
+            ln.side.push_back(b);
+            SC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "join event");
+            ln.join_ev.push_back(e);
+        }
+    }
     auto issue = [&](cudaStream_t s) -> sc_status {
         SC_CUDA(cudaMemsetAsync(arena, 0, kClasses * 64, s), "reset work queues");
-        for (auto& l : launches) {
-            const int r = sc::launch_field_batch(l.cls, l.b, l.grid, s);
+        if (!branches) {
+            for (auto& l : launches) {
+                const int r = sc::launch_field_batch(l.cls, l.b, l.grid, s);
+                if (r < 0) return cuda_fail(ctx, (cudaError_t)(-r), "field kernel launch");
+            }
+            return SC_OK;
+        }
+        SC_CUDA(cudaEventRecord(ln.fork_ev, s), "fork");
+        for (size_t i = 0; i < launches.size(); ++i) {
+            SC_CUDA(cudaStreamWaitEvent(ln.side[i], ln.fork_ev, 0), "fork wait");
+            const int r = sc::launch_field_batch(launches[i].cls, launches[i].b, launches[i].grid, ln.side[i]);
             if (r < 0) return cuda_fail(ctx, (cudaError_t)(-r), "field kernel launch");
+            SC_CUDA(cudaEventRecord(ln.join_ev[i], ln.side[i]), "join");
+            SC_CUDA(cudaStreamWaitEvent(s, ln.join_ev[i], 0), "join wait");
         }
         return SC_OK;
     };
@@ -377,6 +405,7 @@ sc_status launch_chunks(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch, float2* w
             sig.insert(sig.end(), q, q + n);
         };
         put(&arena, sizeof arena);
+        put(&branches, sizeof branches);
         for (auto& l : launches) {
             put(&l.cls, sizeof l.cls);
             put(&l.grid, sizeof l.grid);
@@ -473,6 +502,12 @@ void free_lane(Lane& ln)
     ln.graphs.clear();
     if (ln.cap_stream) cudaStreamDestroy(ln.cap_stream);
     ln.cap_stream = nullptr;
+    for (cudaStream_t b : ln.side) cudaStreamDestroy(b);
+    for (cudaEvent_t e : ln.join_ev) cudaEventDestroy(e);
+    if (ln.fork_ev) cudaEventDestroy(ln.fork_ev);
+    ln.side.clear();
+    ln.join_ev.clear();
+    ln.fork_ev = nullptr;
     if (ln.own_stream && ln.stream) cudaStreamDestroy(ln.stream);
     ln.stream = nullptr;
 }

@@ -110,6 +110,11 @@ struct Lane {
     DevBuf ws, desc, amp, kval;
     cudaStream_t cap_stream = nullptr;
     std::vector<GraphEntry> graphs;
+    // one branch per kernel class of a batch: side streams forked from and
+    // joined back into the lane's stream (graph branches when captured)
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> join_ev;
+    cudaEvent_t fork_ev = nullptr;
 };
 
 struct Server;
@@ -140,6 +145,7 @@ struct sc_ctx {
     bool use_graphs = true;
     bool autotune = true;
     bool omega_chunks = true;       // plan omega chunk sizes (else 2048 per chunk)
+    bool class_streams = true;      // a batch's kernel classes run as concurrent branches
     int fail_tile = -1;             // failure-path test: a node-tile copy left unissued
     int mfie_order = 0;             // 1: add the first MFIE correction (sc_eval)
     int mfie_rho = 64, mfie_phi = 128;  // its polar rule about each node
