@@ -128,16 +128,16 @@ sc_status choose_splits(sc_ctx* ctx, Lane& ln, Chunk& c, const Table* tab, int s
 // chunk of its capacity (the next power of two >= n).
 constexpr double kRateSmall[65] = {
     0.0,
-    3.403, 3.934, 4.918, 5.565, 6.260, 6.763, 7.154, 7.456,  // 1..8
-    7.244, 8.041, 8.005, 8.710, 8.389, 9.031, 8.566, 9.086,  // 9..16
-    8.187, 8.659, 9.132, 9.619, 8.914, 9.325, 9.755, 10.153,  // 17..24
-    8.317, 8.653, 8.987, 9.288, 9.631, 9.957, 10.301, 10.564,  // 25..32
-    8.343, 8.591, 8.849, 9.100, 9.344, 9.593, 9.838, 10.100,  // 33..40
-    9.109, 9.327, 9.550, 9.756, 9.995, 10.215, 10.416, 10.639,  // 41..48
-    10.005, 10.209, 10.393, 10.596, 10.808, 10.989, 11.187, 11.413,  // 49..56
-    10.165, 10.331, 10.515, 10.682, 10.878, 11.047, 11.219, 11.345,  // 57..64
+    3.402, 4.686, 5.362, 5.555, 6.254, 6.760, 7.155, 7.456,  // 1..8
+    7.242, 8.043, 8.002, 8.709, 8.388, 9.031, 8.566, 9.082,  // 9..16
+    8.182, 8.658, 9.129, 9.614, 8.912, 9.322, 9.754, 10.150,  // 17..24
+    8.306, 8.641, 8.976, 9.278, 9.620, 9.946, 10.291, 10.553,  // 25..32
+    8.339, 8.585, 8.846, 9.095, 9.340, 9.590, 9.832, 10.093,  // 33..40
+    9.107, 9.326, 9.548, 9.755, 9.991, 10.216, 10.415, 10.640,  // 41..48
+    10.000, 10.205, 10.390, 10.594, 10.805, 10.985, 11.186, 11.413,  // 49..56
+    10.163, 10.329, 10.512, 10.681, 10.875, 11.043, 11.217, 11.342,  // 57..64
 };
-constexpr double kRateFull[6] = {11.35, 11.64, 12.01, 10.86, 11.06, 10.89};  // 64 .. 2048
+constexpr double kRateFull[6] = {11.34, 11.64, 12, 10.84, 11.06, 10.89};  // 64 .. 2048
 
 constexpr int kMaxChunk = 2048;
 
