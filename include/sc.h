@@ -422,7 +422,8 @@ sc_status sc_eval_time_domain(sc_ctx* ctx, const sc_mirror_t* mirror, const sc_i
  * (rounded up to 256); larger requests are rejected with SC_ERR_INVALID and
  * a message giving the limit.  The first call on a device looks up the
  * array's device address (which may load the library's module) and leaves
- * the caller's current device as it was.  Every call shares the array and
+ * the caller's current device as it was; make that first call before any
+ * stream capture begins.  Every call shares the array and
  * leaves its contents behind; each call writes every value it later reads,
  * so nothing needs clearing, but calls whose GPU work overlaps (other
  * streams, other contexts on the same device) race on it.  Asynchronous on

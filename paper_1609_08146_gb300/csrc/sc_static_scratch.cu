@@ -15,7 +15,8 @@
 // device address, so the device address is looked up once per device, with
 // that device current, by cudaGetSymbolAddress and then passed to kernels as a
 // plain pointer.  The first call of the entry point on a device does that
-// lookup (which may load the module) and restores the caller's current device.
+// lookup (which may load the module) and restores the caller's current
+// device; that first call should come before any stream capture begins.
 #include <cuda_runtime.h>
 
 #include <mutex>
