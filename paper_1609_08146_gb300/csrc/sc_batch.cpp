@@ -137,7 +137,7 @@ constexpr double kRateSmall[65] = {
     10.000, 10.205, 10.390, 10.594, 10.805, 10.985, 11.186, 11.413,  // 49..56
     10.163, 10.329, 10.512, 10.681, 10.875, 11.043, 11.217, 11.342,  // 57..64
 };
-constexpr double kRateFull[6] = {11.34, 11.64, 12, 10.84, 11.06, 10.89};  // 64 .. 2048
+constexpr double kRateFull[6] = {11.340, 11.640, 12.000, 10.840, 11.060, 10.890};  // 64 .. 2048
 
 constexpr int kMaxChunk = 2048;
 

@@ -109,7 +109,7 @@ def main():
     for i in range(1, 65, 8):
         print("    " + ", ".join("%.3f" % v for v in small[i:i + 8]) + ",  // %d..%d" % (i, i + 7))
     print("};")
-    print("constexpr double kRateFull[6] = {" + ", ".join("%.4g" % v for v in full) + "};  // 64 .. 2048")
+    print("constexpr double kRateFull[6] = {" + ", ".join("%.3f" % v for v in full) + "};  // 64 .. 2048")
 
 
 if __name__ == "__main__":

@@ -40,16 +40,19 @@ def test_bounded_wait_times_out_and_context_survives():
         ctx.close()
 
 
-@pytest.mark.parametrize("n_omega,tile", [(256, 0), (256, 7), (8, 1), (8, 9)])
+@pytest.mark.parametrize("n_omega,tile", [(256, 0), (256, 7), (8, 1), (8, 9), (300, 0), (300, 7)])
 def test_lost_copy_ends_the_launch_after_one_wait(n_omega, tile):
     """A node-tile copy that never lands (SC_OPT_FAIL_COPY leaves it
     unissued: no fault, no copy in flight) makes its wait run out once; the
     CTA and then the whole launch stop instead of spending a wait limit on
     every later tile of the item (hundreds here).  The call reports
     SC_ERR_TIMEOUT within a few seconds, and the next call on the context is
-    bitwise equal to one made before.  Grouped (256 omegas) and direct (8)
-    kernels; the lost copy is one of the first two or a refill."""
+    bitwise equal to one made before.  The direct kernel (256 and 8 omegas)
+    and, with chunk planning off, the grouped kernel (300 omegas in one
+    chunk); the lost copy is one of the first two or a refill."""
     ctx = sc.Context(0)
+    if n_omega > 256:
+        ctx.set_option(sc.SC_OPT_OMEGA_CHUNKS, 0)
     try:
         w = wl.sweep(1e4, 256, n_points=2048)
         mc = w["mirror"]

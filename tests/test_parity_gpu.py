@@ -158,6 +158,27 @@ def test_chunk_planning_on_and_off(ctx):
     assert max(e_on, e_off) <= TOL32
 
 
+@pytest.mark.parametrize("n_omega", [300, 600, 1100])
+def test_grouped_kernel_classes(ctx, n_omega):
+    # chunk planning off: chunks above 256 omegas run on the grouped kernel
+    # (64, 128 and 256 threads per point), the classes planning never reaches;
+    # ragged splits and folds
+    mirror = dict(f=500.0, r_max=1000.0, n_r=40, n_theta=44, rim=True)
+    beam = dict(profile="gauss", w0=500.0, pol="radial", zernike=[0.05, -0.1, 0.03])
+    om = wl.uniform_omegas(n_omega)
+    pts = np.vstack([np.zeros((1, 3)), wl.random_cube(9, 1.5, seed=n_omega)])
+    ctx.set_option(sc.SC_OPT_OMEGA_CHUNKS, 0)
+    ctx.set_option(sc.SC_OPT_NODES_PER_SPLIT, 640)
+    ctx.set_option(sc.SC_OPT_FLUSH_NODES, 256)
+    try:
+        assert ctx.plan_omega_chunks(n_omega, 1000) == [n_omega]
+        check(ctx, mirror, beam, om, pts, fp64=False)
+    finally:
+        ctx.set_option(sc.SC_OPT_OMEGA_CHUNKS, 1)
+        ctx.set_option(sc.SC_OPT_NODES_PER_SPLIT, 0)
+        ctx.set_option(sc.SC_OPT_FLUSH_NODES, 2048)
+
+
 @pytest.mark.parametrize("n_omega", [25, 33, 41, 49])
 def test_small_count_cuts_on_a_large_request(ctx, n_omega):
     # 64 x 64 nodes and 1030 points: above 4M pairs per omega, so small counts
