@@ -335,6 +335,14 @@ typedef struct {
     int launches;       /* kernels launched by the call                           */
     int tables;         /* node tables summed per evaluation (field passes; for a */
                         /* batch the largest over its requests)                   */
+    /* the tile shape chosen for the (first request's) first omega chunk on the   */
+    /* FP32 path, or -1 on the FP64 path: kernel class, threads per point, omegas */
+    /* per thread (the measured default layout for its omega count, or the       */
+    /* autotuner's choice between it and an alternative) and node splits         */
+    int kernel_class;
+    int threads_per_point;
+    int omegas_per_thread;
+    int splits;
 } sc_eval_stats;
 
 /*
@@ -574,6 +582,15 @@ enum {
     SC_OPT_MFIE_PHI = 11,       /* ... and rays about each node (default 128)       */
     SC_OPT_CLASS_STREAMS = 12,  /* 1 (default): the field launches of a batch's     */
                                 /* kernel classes run as concurrent branches        */
+    SC_OPT_TILE_LAYOUT = 13,    /* tile shape of the FP32 field kernel (threads per */
+                                /* point x omegas per thread) for chunks of 8,      */
+                                /* 9..16, 33..64 and 65..128 omegas, which have two */
+                                /* near layouts: -1 (default) the autotuner times   */
+                                /* both on the first chunk of each shape when       */
+                                /* SC_OPT_AUTOTUNE is on (else the default); 0 the  */
+                                /* default layout; 1 the alternative.  Other omega  */
+                                /* counts have one layout.  sc_eval_stats reports   */
+                                /* the layout taken                                 */
     SC_OPT_FAIL_COPY = 8        /* failure-path test, -1 (default) off: in every   */
                                 /* batched FP32 field launch, the work item 0 skips */
                                 /* the bulk copy of its node tile `value`, so the   */

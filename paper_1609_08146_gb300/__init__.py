@@ -33,6 +33,7 @@ SPECTRA = {"mono": 0, "gauss_time": 1, "supergauss_lambda": 2, "sampled": 3}
 SC_OPT_TIME_FIELD, SC_OPT_NODES_PER_SPLIT, SC_OPT_WORKSPACE_CAP, SC_OPT_FLUSH_NODES = 1, 2, 3, 4
 SC_OPT_GRAPHS, SC_OPT_AUTOTUNE, SC_OPT_OMEGA_CHUNKS, SC_OPT_FAIL_COPY = 5, 6, 7, 8
 SC_OPT_MFIE_ORDER, SC_OPT_MFIE_RHO, SC_OPT_MFIE_PHI, SC_OPT_CLASS_STREAMS = 9, 10, 11, 12
+SC_OPT_TILE_LAYOUT = 13
 
 _DP = ctypes.POINTER(ctypes.c_double)
 _VP = ctypes.c_void_p
@@ -70,7 +71,16 @@ class sc_spectrum(ctypes.Structure):
 
 class sc_eval_stats(ctypes.Structure):
     _fields_ = [("evals", ctypes.c_double), ("field_ms", ctypes.c_double),
-                ("total_ms", ctypes.c_double), ("launches", ctypes.c_int), ("tables", ctypes.c_int)]
+                ("total_ms", ctypes.c_double), ("launches", ctypes.c_int), ("tables", ctypes.c_int),
+                ("kernel_class", ctypes.c_int), ("threads_per_point", ctypes.c_int),
+                ("omegas_per_thread", ctypes.c_int), ("splits", ctypes.c_int)]
+
+
+def _stats_dict(st):
+    return dict(evals=st.evals, field_ms=st.field_ms, total_ms=st.total_ms,
+                launches=st.launches, tables=st.tables, kernel_class=st.kernel_class,
+                threads_per_point=st.threads_per_point, omegas_per_thread=st.omegas_per_thread,
+                splits=st.splits)
 
 
 class sc_counters(ctypes.Structure):
@@ -345,8 +355,7 @@ class Context:
                                       npts, prec, _addr(E), _addr(B) if B is not None else None,
                                       ctypes.byref(st) if stats else None))
         if stats:
-            return E, B, dict(evals=st.evals, field_ms=st.field_ms, total_ms=st.total_ms,
-                              launches=st.launches, tables=st.tables)
+            return E, B, _stats_dict(st)
         return E, B
 
     def eval_time_domain(self, mirror: Mirror, inc: Incident, omegas, points, times, precision: str = "fp32",
@@ -373,8 +382,7 @@ class Context:
                                                   _addr(Et), _addr(Bt) if Bt is not None else None,
                                                   ctypes.byref(st) if stats else None))
         if stats:
-            return Et, Bt, dict(evals=st.evals, field_ms=st.field_ms, total_ms=st.total_ms,
-                                launches=st.launches, tables=st.tables)
+            return Et, Bt, _stats_dict(st)
         return Et, Bt
 
     def time_domain(self, E, B, omegas, times, precision: str = "fp32", out=None):
@@ -423,8 +431,7 @@ class Context:
         self._check(self._lib.sc_eval_batch(self._h, arr, len(requests),
                                             ctypes.byref(st) if stats else None))
         if stats:
-            return outs, dict(evals=st.evals, field_ms=st.field_ms, total_ms=st.total_ms,
-                              launches=st.launches, tables=st.tables)
+            return outs, _stats_dict(st)
         return outs
 
     # ---- serving

@@ -302,6 +302,19 @@ sc_status sc_spectrum_eval(sc_ctx* ctx, const sc_incident_t* inc, const double* 
 
 // sc_eval after validation, with ctx->mu held and the device set (dom: the
 // omega step of the uniform grid the FP32 path needs).
+// The tile shape a call chose (kernel class, its layout, node splits), or -1s.
+static void fill_shape(sc_eval_stats* st, int cls, int splits)
+{
+    st->kernel_class = cls;
+    st->splits = splits;
+    if (cls >= 0) {
+        sc::class_layout(cls, &st->threads_per_point, &st->omegas_per_thread);
+    } else {
+        st->threads_per_point = -1;
+        st->omegas_per_thread = -1;
+    }
+}
+
 static sc_status eval_unlocked(sc_ctx* ctx, const sc_mirror_t* m, const sc_incident_t* in,
                                const double* omegas, int n_omega, const double* points_xyz,
                                int n_points, sc_precision prec, double dom, void* E_out,
@@ -369,6 +382,7 @@ static sc_status eval_unlocked(sc_ctx* ctx, const sc_mirror_t* m, const sc_incid
     const double* d_k = (const double*)ctx->main.kval.p;
 
     const double evals = (double)n_points * (double)tab->n_surf * (double)n_omega;
+    int shape_cls = -1, shape_splits = -1;  // reported in stats (FP32 path)
 
     if (prec == SC_FP64) {
         cudaEvent_t f0 = nullptr, f1 = nullptr;
@@ -406,6 +420,10 @@ static sc_status eval_unlocked(sc_ctx* ctx, const sc_mirror_t* m, const sc_incid
         st = plan_request(ctx, ctx->main, tab, omegas, n_omega, dom, d_pts, n_points, d_amp, d_k,
                           (float2*)dE, (float2*)dB, ch);
         if (st != SC_OK) return st;
+        if (!ch.empty()) {
+            ctx->shape_cls = shape_cls = ch[0].cls;
+            ctx->shape_splits = shape_splits = ch[0].f.n_splits;
+        }
         st = run_chunks(ctx, ctx->main, ch);
         if (st != SC_OK) return st;
     }
@@ -437,6 +455,7 @@ static sc_status eval_unlocked(sc_ctx* ctx, const sc_mirror_t* m, const sc_incid
         stats->field_ms = ctx->ctr.field_ms - field_ms_before;
         stats->launches = (int)(ctx->ctr.launches - launches_before);
         stats->tables = (int)tab->parts.size();
+        fill_shape(stats, shape_cls, shape_splits);
         ctx->time_field = timing_before;
     }
     return SC_OK;
@@ -540,11 +559,17 @@ sc_status sc_eval_time_domain(sc_ctx* ctx, const sc_mirror_t* m, const sc_incide
     if (B_t && (st = ensure(ctx, ctx->fspecB, (size_t)chunk * per_omega)) != SC_OK) return st;
     const double dk = n_omega > 1 ? 2.0 * kPi * dom : 1.0;
     double evals = 0.0;
+    int first_cls = -1, first_splits = -1;
     for (int o0 = 0; o0 < n_omega; o0 += chunk) {
         const int c = std::min(chunk, n_omega - o0);
+        ctx->shape_cls = ctx->shape_splits = -1;
         st = eval_unlocked(ctx, m, in, omegas + o0, c, d_pts, n_points, prec, dom, ctx->fspecE.p,
                            B_t ? ctx->fspecB.p : nullptr, nullptr);
         if (st != SC_OK) return st;
+        if (o0 == 0) {
+            first_cls = ctx->shape_cls;
+            first_splits = ctx->shape_splits;
+        }
         st = time_domain_unlocked(ctx, prec, ctx->fspecE.p, B_t ? ctx->fspecB.p : nullptr, omegas + o0, c,
                                   n_points, times, n_t, dEt, dBt, dk, o0 > 0);
         if (st != SC_OK) return st;
@@ -572,6 +597,7 @@ sc_status sc_eval_time_domain(sc_ctx* ctx, const sc_mirror_t* m, const sc_incide
         stats->tables = 0;
         for (const auto& t : ctx->tables)
             if (t.mid == m->id && t.iid == in->id) stats->tables = (int)t.parts.size();
+        fill_shape(stats, first_cls, first_splits);
     }
     return st;
 }
@@ -645,12 +671,17 @@ sc_status sc_eval_batch(sc_ctx* ctx, const sc_request* reqs, int n_req, sc_eval_
     SC_CUDA(cudaMemcpyAsync(ln.kval.p, k_all.data(), k_all.size() * sizeof(double),
                             cudaMemcpyHostToDevice, ln.stream), "upload wavenumbers");
     std::vector<Chunk> ch;
+    int first_cls = -1, first_splits = -1;
     for (int r = 0; r < n_req; ++r) {
         const sc_request& q = reqs[r];
         st = plan_request(ctx, ln, tabs[r], q.omegas, q.n_omega, dom[r], q.points_xyz, q.n_points,
                           (const double*)ln.amp.p + amp_off[r], (const double*)ln.kval.p + om_off[r],
                           (float2*)q.E_out, (float2*)q.B_out, ch);
         if (st != SC_OK) return st;
+        if (r == 0 && !ch.empty()) {
+            first_cls = ch[0].cls;
+            first_splits = ch[0].f.n_splits;
+        }
     }
     st = run_chunks(ctx, ln, ch);
     if (st != SC_OK) return st;
@@ -671,6 +702,7 @@ sc_status sc_eval_batch(sc_ctx* ctx, const sc_request* reqs, int n_req, sc_eval_
         stats->launches = (int)(ctx->ctr.launches - launches_before);
         stats->tables = 0;
         for (const Table* t : tabs) stats->tables = std::max(stats->tables, (int)t->parts.size());
+        fill_shape(stats, first_cls, first_splits);
     }
     return SC_OK;
 }
@@ -1121,6 +1153,10 @@ sc_status sc_set_option(sc_ctx* ctx, int option, long long value)
     case SC_OPT_AUTOTUNE: ctx->autotune = value != 0; return SC_OK;
     case SC_OPT_OMEGA_CHUNKS: ctx->omega_chunks = value != 0; return SC_OK;
     case SC_OPT_CLASS_STREAMS: ctx->class_streams = value != 0; return SC_OK;
+    case SC_OPT_TILE_LAYOUT:
+        if (value < -1 || value > 1) return fail(ctx, SC_ERR_INVALID, "tile layout must be -1, 0 or 1");
+        ctx->tile_layout = (int)value;
+        return SC_OK;
     case SC_OPT_WORKSPACE_CAP:
         if (value < (1 << 20)) return fail(ctx, SC_ERR_INVALID, "workspace cap below 1 MiB");
         ctx->ws_cap = (size_t)value;

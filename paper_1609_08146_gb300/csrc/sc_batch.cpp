@@ -119,6 +119,59 @@ sc_status choose_splits(sc_ctx* ctx, Lane& ln, Chunk& c, const Table* tab, int s
     return SC_OK;
 }
 
+// Kernel class (tile shape: threads per point x omegas per thread) of a
+// chunk.  field_class(n) is the layout measured fastest on GB300 for n
+// omegas; where a second layout of the same n is close (alt_field_class), the
+// autotuner times both on the real chunk, each with its own tuned split
+// count, on the first request of each shape, and keeps the faster unless the
+// default is within 1%.  Chunks above kTuneMaxEvals keep the default.
+// SC_OPT_TILE_LAYOUT 0 / 1 pins the default / the alternative.
+sc_status choose_class(sc_ctx* ctx, Lane& ln, Chunk& c, const Table* tab, int* cls_out)
+{
+    const int def = sc::field_class(c.f.n_omega);
+    *cls_out = def;
+    const int alt = sc::alt_field_class(c.f.n_omega);
+    if (alt < 0 || ctx->tile_layout == 0) return SC_OK;
+    if (ctx->tile_layout == 1) {
+        *cls_out = alt;
+        return SC_OK;
+    }
+    if (!ctx->autotune || ctx->nodes_per_split > 0) return SC_OK;
+    const int tiles = tab->n_surf_tiles;
+    const auto key = std::make_tuple(-1 - c.f.n_omega, tiles, tab->n_rim_tiles, c.f.n_pts, 0, c.n_parts);
+    auto hit = ctx->tuned.find(key);
+    if (hit != ctx->tuned.end()) {
+        *cls_out = hit->second;
+        return SC_OK;
+    }
+    const double chunk_evals = (double)c.f.n_pts * tiles * sc::kTile * c.f.n_omega * c.n_parts;
+    if (chunk_evals > kTuneMaxEvals) {
+        ctx->tuned[key] = def;
+        return SC_OK;
+    }
+    float ms[2] = {1e30f, 1e30f};
+    const int cand[2] = {def, alt};
+    for (int i = 0; i < 2; ++i) {
+        Chunk t = c;
+        t.cls = cand[i];
+        int slots = 1;
+        sc::field_shape(t.cls, ctx->device, &t.ppc, &slots);
+        t.pb = (t.f.n_pts + t.ppc - 1) / t.ppc;
+        int S = 1;
+        sc_status st = choose_splits(ctx, ln, t, tab, slots, &S);
+        if (st != SC_OK) return st;
+        set_splits(t, S, tiles);
+        if (t.ws_elems * sizeof(float2) > ctx->ws_cap) continue;  // would need point chunks: not timed
+        st = ensure(ctx, ln.ws, t.ws_elems * sizeof(float2), ln.stream);
+        if (st != SC_OK) return st;
+        ms[i] = time_chunk(ctx, ln, t, S, tab, (float2*)ln.ws.p);
+    }
+    const int best = (ms[1] < 0.99f * ms[0]) ? alt : def;
+    ctx->tuned[key] = best;
+    *cls_out = best;
+    return SC_OK;
+}
+
 // Field-kernel throughput of one chunk, in 1e11 (point, node, omega)
 // evaluations per second, measured on GB300 on the broadband mirror and beam
 // at 256^2 nodes and 4160 focal points (tune_chunks.py in the package
@@ -230,9 +283,6 @@ sc_status plan_request(sc_ctx* ctx, Lane& ln, const Table* tab, const double* om
     for (int o0 = 0, no = 0; o0 < n_omega; o0 += no) {
         no = ctx->omega_chunks ? next_chunk(n_omega - o0, small_cuts) : std::min(kMaxChunk, n_omega - o0);
         Chunk c;
-        c.cls = sc::field_class(no);
-        int slots = 1;
-        sc::field_shape(c.cls, ctx->device, &c.ppc, &slots);
         const double w0 = omegas[o0];
         c.f.nodes = tab->d32;
         c.f.n_surf_tiles = tab->n_surf_tiles;
@@ -248,7 +298,6 @@ sc_status plan_request(sc_ctx* ctx, Lane& ln, const Table* tab, const double* om
         // the split count is chosen on the whole request's point count
         c.f.pts = d_pts;
         c.f.n_pts = n_points;
-        c.pb = (n_points + c.ppc - 1) / c.ppc;
         c.rl.amp = d_amp + 2 * (size_t)o0;
         c.rl.kval = d_k + o0;
         c.rl.out_pt_stride_omega = (long long)n_points * 3;
@@ -260,8 +309,15 @@ sc_status plan_request(sc_ctx* ctx, Lane& ln, const Table* tab, const double* om
         c.n_parts = (int)tab->parts.size();
         c.rl.n_parts = c.n_parts;
         c.rl.amp_stride = 2LL * n_omega;
+        // tile shape: the measured default layout for this omega count, or the
+        // autotuner's choice between it and an alternative
+        sc_status st = choose_class(ctx, ln, c, tab, &c.cls);
+        if (st != SC_OK) return st;
+        int slots = 1;
+        sc::field_shape(c.cls, ctx->device, &c.ppc, &slots);
+        c.pb = (n_points + c.ppc - 1) / c.ppc;
         int S = 1;
-        sc_status st = choose_splits(ctx, ln, c, tab, slots, &S);
+        st = choose_splits(ctx, ln, c, tab, slots, &S);
         if (st != SC_OK) return st;
         set_splits(c, S, tab->n_surf_tiles);
         const int n_splits = c.f.n_splits;

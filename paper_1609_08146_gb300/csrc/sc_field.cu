@@ -380,9 +380,33 @@ int field_class(int n_omega)
     return cls;
 }
 
+int alt_field_class(int n_omega)
+{
+    if (n_omega == 8) return 24;                         // 1 thread of 8
+    if (n_omega >= 9 && n_omega <= 12) return 25;        // 4 threads of 3
+    if (n_omega >= 13 && n_omega <= 16) return 26;       // 4 threads of 4
+    if (n_omega >= 33 && n_omega <= 48) return 27;       // 16 threads of 3
+    if (n_omega >= 49 && n_omega <= 64) return 28;       // 16 threads of 4
+    if (n_omega >= 65 && n_omega <= 128) return 29;      // 32 threads of 4
+    return -1;
+}
+
+void class_layout(int cls, int* tpp, int* opt)
+{
+    static const int kLayout[kNumClasses][2] = {
+        {1, 1}, {1, 2}, {1, 3}, {1, 4}, {1, 5}, {1, 6}, {1, 7}, {2, 4},     // 0..7
+        {2, 5}, {2, 6}, {2, 7}, {2, 8}, {4, 5}, {4, 6}, {4, 8},             // 8..14
+        {8, 5}, {8, 6}, {8, 7}, {8, 8}, {16, 8}, {32, 8},                   // 15..20
+        {64, 8}, {128, 8}, {256, 8},                                        // 21..23 grouped
+        {1, 8}, {4, 3}, {4, 4}, {16, 3}, {16, 4}, {32, 4}};                 // 24..29
+    const int c = cls < 0 || cls >= kNumClasses ? 0 : cls;
+    *tpp = kLayout[c][0];
+    *opt = kLayout[c][1];
+}
+
 void field_shape(int cls, int device, int* ppc, int* slots)
 {
-    if (cls < kFirstGroupedClass) return direct_field_shape(cls, device, ppc, slots);
+    if (is_direct_class(cls)) return direct_field_shape(cls, device, ppc, slots);
     switch (cls) {
     case 21: return grouped_shape<64>(device, ppc, slots);
     case 22: return grouped_shape<128>(device, ppc, slots);
@@ -393,7 +417,7 @@ void field_shape(int cls, int device, int* ppc, int* slots)
 int launch_field_batch(int cls, const BatchLaunch& b, int grid, cudaStream_t s)
 {
     if (grid < 1) return 0;
-    if (cls < kFirstGroupedClass) return launch_direct_field(cls, b, grid, s);
+    if (is_direct_class(cls)) return launch_direct_field(cls, b, grid, s);
     switch (cls) {
     case 21: return launch_grouped<64>(b, grid, s);
     case 22: return launch_grouped<128>(b, grid, s);

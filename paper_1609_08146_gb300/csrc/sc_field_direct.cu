@@ -283,6 +283,12 @@ void direct_field_shape(int cls, int device, int* ppc, int* slots)
     case 18: return direct_shape<8, 8>(device, ppc, slots);
     case 19: return direct_shape<8, 16>(device, ppc, slots);
     case 20: return direct_shape<8, 32>(device, ppc, slots);
+    case 24: return direct_shape<8, 1>(device, ppc, slots);
+    case 25: return direct_shape<3, 4>(device, ppc, slots);
+    case 26: return direct_shape<4, 4>(device, ppc, slots);
+    case 27: return direct_shape<3, 16>(device, ppc, slots);
+    case 28: return direct_shape<4, 16>(device, ppc, slots);
+    case 29: return direct_shape<4, 32>(device, ppc, slots);
     default: *ppc = 1; *slots = 1;
     }
 }
@@ -311,6 +317,12 @@ int launch_direct_field(int cls, const BatchLaunch& b, int grid, cudaStream_t s)
     case 18: return launch_direct<8, 8>(b, grid, s);
     case 19: return launch_direct<8, 16>(b, grid, s);
     case 20: return launch_direct<8, 32>(b, grid, s);
+    case 24: return launch_direct<8, 1>(b, grid, s);
+    case 25: return launch_direct<3, 4>(b, grid, s);
+    case 26: return launch_direct<4, 4>(b, grid, s);
+    case 27: return launch_direct<3, 16>(b, grid, s);
+    case 28: return launch_direct<4, 16>(b, grid, s);
+    case 29: return launch_direct<4, 32>(b, grid, s);
     default: return -(int)cudaErrorInvalidValue;
     }
 }

@@ -146,6 +146,8 @@ struct sc_ctx {
     bool autotune = true;
     bool omega_chunks = true;       // plan omega chunk sizes (else 2048 per chunk)
     bool class_streams = true;      // a batch's kernel classes run as concurrent branches
+    int tile_layout = -1;           // -1 autotuned, 0 default, 1 alternative layout
+    int shape_cls = -1, shape_splits = -1;  // tile shape of the last planned first chunk
     int fail_tile = -1;             // failure-path test: a node-tile copy left unissued
     int mfie_order = 0;             // 1: add the first MFIE correction (sc_eval)
     int mfie_rho = 64, mfie_phi = 128;  // its polar rule about each node

@@ -86,10 +86,20 @@ struct BatchLaunch {
 
 // Kernel class for a chunk of n_omega (<= 2048) omegas: 0..20 the direct
 // kernel (1 to 32 threads per point, 1..8 omegas per thread, up to 256
-// omegas), 21..23 the grouped kernel with 64, 128, 256 threads per point.
-constexpr int kNumClasses = 24;
-constexpr int kFirstGroupedClass = 21;
+// omegas), 21..23 the grouped kernel with 64, 128, 256 threads per point,
+// 24..29 alternative direct layouts for the autotuner.
+constexpr int kNumClasses = 30;
+constexpr int kFirstGroupedClass = 21;  // grouped classes 21..23
+constexpr int kFirstAltClass = 24;      // alternative direct layouts 24..29 (alt_field_class)
 int field_class(int n_omega);
+// The alternative direct layout the autotuner times against field_class(n)
+// for n omegas, or -1 where there is none: 8 omegas on one thread of 8
+// (against two of 4), 9..16 on four threads (against two), 33..64 on sixteen
+// (against eight), 65..128 on 32 threads of 4 (against sixteen of 8).
+int alt_field_class(int n_omega);
+// Threads per point and omegas per thread of a class.
+void class_layout(int cls, int* threads_per_point, int* omegas_per_thread);
+inline bool is_direct_class(int cls) { return cls < kFirstGroupedClass || cls >= kFirstAltClass; }
 // the direct kernel's classes (0 .. kFirstGroupedClass - 1), in sc_field_direct.cu
 void direct_field_shape(int cls, int device, int* points_per_item, int* resident_ctas);
 int launch_direct_field(int cls, const BatchLaunch& b, int grid, cudaStream_t s);

@@ -15,7 +15,13 @@ It prints both tables in the form of csrc/sc_batch.cpp (kRateSmall,
 kRateFull), in units of 1e11 evaluations per second.  `first_chunks` is the
 same split search as the library's, written again here for the tests.
 
+With --layouts it instead times both tile shapes (threads per point x omegas
+per thread) of the omega counts that have two, pinned with
+SC_OPT_TILE_LAYOUT, and the shape the autotuner takes, at 4160 and 1040
+points: one JSON line per (points, n).
+
     python -m paper_1609_08146_gb300.tune_chunks
+    python -m paper_1609_08146_gb300.tune_chunks --layouts
 """
 from __future__ import annotations
 
@@ -58,6 +64,53 @@ def measure(reps: int = 3):
         full = [rate(n) for n in FULL]
         return small, full
     finally:
+        ctx.close()
+
+
+LAYOUT_COUNTS = (8, 11, 12, 15, 16, 40, 48, 57, 64, 100, 128)
+
+
+def measure_layouts(counts=LAYOUT_COUNTS, n_points=(4160, 1040), reps: int = 5):
+    """For each point count and omega count: {layout: (1e11 evals/s, kernel
+    class, splits)} for SC_OPT_TILE_LAYOUT 0 (default shape), 1 (alternative)
+    and -1 (autotuned)."""
+    import torch
+
+    import paper_1609_08146_gb300 as sc
+    from paper_1609_08146_gb300 import workloads as wl
+
+    w = wl.broadband(256, 8)
+    ctx = sc.Context(0)
+    rows = []
+    try:
+        m = w["mirror"]
+        mir = ctx.mirror(m["f"], m["r_min"], m["r_max"], m["n_r"], m["n_theta"], rim=m["rim"])
+        b = w["beam"]
+        inc = ctx.incident(profile=b["profile"], w0=b["w0"], pol=b["pol"], spectrum=w["spectrum"])
+        allp = torch.tensor(w["points"], device="cuda")
+        ctx.set_option(sc.SC_OPT_OMEGA_CHUNKS, 0)
+        for P in n_points:
+            pts = allp[:P].contiguous()
+            for n in counts:
+                om = wl.uniform_omegas(n)
+                row = dict(points=P, n_omega=n)
+                for lay in (0, 1, -1):
+                    ctx.set_option(sc.SC_OPT_TILE_LAYOUT, lay)
+                    for _ in range(2):
+                        _, _, st = ctx.eval(mir, inc, om, pts, stats=True)
+                    ctx.set_option(sc.SC_OPT_TIME_FIELD, 1)
+                    ctx.reset_counters()
+                    for _ in range(reps):
+                        ctx.eval(mir, inc, om, pts)
+                    c = ctx.counters()
+                    ctx.set_option(sc.SC_OPT_TIME_FIELD, 0)
+                    evals = reps * P * m["n_r"] * m["n_theta"] * n
+                    row[str(lay)] = (round(evals / (c["field_ms"] * 1e-3) * 1e-11, 3),
+                                     st["kernel_class"], st["splits"])
+                rows.append(row)
+        return rows
+    finally:
+        ctx.set_option(sc.SC_OPT_TILE_LAYOUT, -1)
         ctx.close()
 
 
@@ -104,6 +157,12 @@ def plan(n_omega: int, first: list) -> list:
 
 
 def main():
+    import sys
+    if "--layouts" in sys.argv[1:]:
+        import json
+        for row in measure_layouts():
+            print(json.dumps(row), flush=True)
+        return
     small, full = measure()
     print("constexpr double kRateSmall[65] = {\n    0.0,")
     for i in range(1, 65, 8):

@@ -179,6 +179,81 @@ def test_grouped_kernel_classes(ctx, n_omega):
         ctx.set_option(sc.SC_OPT_FLUSH_NODES, 2048)
 
 
+# (omega count, default layout, alternative layout) as (class, threads per
+# point, omegas per thread)
+LAYOUTS = [(8, (7, 2, 4), (24, 1, 8)), (11, (9, 2, 6), (25, 4, 3)), (15, (11, 2, 8), (26, 4, 4)),
+           (40, (15, 8, 5), (27, 16, 3)), (57, (18, 8, 8), (28, 16, 4)),
+           (100, (19, 16, 8), (29, 32, 4))]
+
+
+@pytest.mark.parametrize("n_omega,default,alt", LAYOUTS)
+def test_tile_layouts(ctx, n_omega, default, alt):
+    # both tile shapes of the omega counts that have two, pinned with
+    # SC_OPT_TILE_LAYOUT, each against the oracle (ragged omega groups and
+    # point blocks, several splits); the shape the call took is reported
+    mirror = dict(f=700.0, r_max=1400.0, n_r=36, n_theta=40, rim=True)
+    beam = dict(profile="gauss", w0=600.0, pol="linear", zernike=[0.0, 0.05, -0.02])
+    om = wl.uniform_omegas(n_omega)
+    pts = wl.random_cube(37, 1.5, seed=n_omega)
+    E0, B0 = run_oracle(mirror, beam, om, pts)
+    m = ctx.mirror(mirror["f"], 0.0, mirror["r_max"], mirror["n_r"], mirror["n_theta"], rim=True)
+    inc = ctx.incident(profile="gauss", w0=beam["w0"], pol="linear", zernike=beam["zernike"],
+                       spectrum=unit_spectrum(om))
+    P = torch.tensor(pts, device="cuda")
+    ctx.set_option(sc.SC_OPT_OMEGA_CHUNKS, 0)
+    ctx.set_option(sc.SC_OPT_NODES_PER_SPLIT, 320)
+    try:
+        for layout, want in ((0, default), (1, alt), (-1, None)):
+            ctx.set_option(sc.SC_OPT_TILE_LAYOUT, layout)
+            E, B, st = ctx.eval(m, inc, om, P, stats=True)
+            torch.cuda.synchronize()
+            got = (st["kernel_class"], st["threads_per_point"], st["omegas_per_thread"])
+            if want is None:
+                assert got in (default, alt)
+            else:
+                assert got == want
+            assert st["splits"] == -(-mirror["n_r"] * mirror["n_theta"] // 320)
+            err = max(rel_err(E.cpu().numpy(), E0), rel_err(B.cpu().numpy(), B0))
+            assert err <= TOL32, (layout, err)
+    finally:
+        ctx.set_option(sc.SC_OPT_TILE_LAYOUT, -1)
+        ctx.set_option(sc.SC_OPT_OMEGA_CHUNKS, 1)
+        ctx.set_option(sc.SC_OPT_NODES_PER_SPLIT, 0)
+
+
+def test_tile_layout_autotuned_and_reported(ctx):
+    # with the autotuner on, an omega count with two layouts takes one of them
+    # (timed once, then cached: a second call reports the same shape); the
+    # FP64 path reports no shape; out-of-range values are refused
+    mirror = dict(f=700.0, r_max=1400.0, n_r=48, n_theta=48, rim=True)
+    om = wl.uniform_omegas(100)
+    pts = wl.random_cube(300, 1.5, seed=100)
+    m = ctx.mirror(mirror["f"], 0.0, mirror["r_max"], mirror["n_r"], mirror["n_theta"], rim=True)
+    inc = ctx.incident(profile="gauss", w0=600.0, pol="radial", spectrum=unit_spectrum(om))
+    P = torch.tensor(pts, device="cuda")
+    ctx.set_option(sc.SC_OPT_OMEGA_CHUNKS, 0)
+    try:
+        shapes = []
+        for _ in range(2):
+            E, B, st = ctx.eval(m, inc, om, P, stats=True)
+            torch.cuda.synchronize()
+            shapes.append((st["kernel_class"], st["threads_per_point"], st["omegas_per_thread"],
+                           st["splits"]))
+        assert shapes[0] == shapes[1]
+        assert shapes[0][:3] in ((19, 16, 8), (29, 32, 4))
+        assert shapes[0][3] >= 1
+        sel = np.arange(0, 300, 10)
+        E0, B0 = run_oracle(mirror, dict(profile="gauss", w0=600.0, pol="radial"), om, pts[sel])
+        assert max(rel_err(E.cpu().numpy()[:, sel], E0), rel_err(B.cpu().numpy()[:, sel], B0)) <= TOL32
+        _, _, st = ctx.eval(m, inc, om, P, precision="fp64", stats=True)
+        assert st["kernel_class"] == -1 and st["threads_per_point"] == -1
+    finally:
+        ctx.set_option(sc.SC_OPT_OMEGA_CHUNKS, 1)
+    for bad in (-2, 2):
+        with pytest.raises(sc.ScError):
+            ctx.set_option(sc.SC_OPT_TILE_LAYOUT, bad)
+
+
 @pytest.mark.parametrize("n_omega", [25, 33, 41, 49])
 def test_small_count_cuts_on_a_large_request(ctx, n_omega):
     # 64 x 64 nodes and 1030 points: above 4M pairs per omega, so small counts
