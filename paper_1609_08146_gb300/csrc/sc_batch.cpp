@@ -181,16 +181,16 @@ sc_status choose_class(sc_ctx* ctx, Lane& ln, Chunk& c, const Table* tab, int* c
 // chunk of its capacity (the next power of two >= n).
 constexpr double kRateSmall[65] = {
     0.0,
-    3.402, 4.686, 5.362, 5.555, 6.254, 6.760, 7.155, 7.456,  // 1..8
-    7.242, 8.043, 8.002, 8.709, 8.388, 9.031, 8.566, 9.082,  // 9..16
-    8.182, 8.658, 9.129, 9.614, 8.912, 9.322, 9.754, 10.150,  // 17..24
-    8.306, 8.641, 8.976, 9.278, 9.620, 9.946, 10.291, 10.553,  // 25..32
-    8.339, 8.585, 8.846, 9.095, 9.340, 9.590, 9.832, 10.093,  // 33..40
-    9.107, 9.326, 9.548, 9.755, 9.991, 10.216, 10.415, 10.640,  // 41..48
-    10.000, 10.205, 10.390, 10.594, 10.805, 10.985, 11.186, 11.413,  // 49..56
-    10.163, 10.329, 10.512, 10.681, 10.875, 11.043, 11.217, 11.342,  // 57..64
+    3.671, 4.803, 5.363, 5.954, 6.252, 6.760, 7.152, 7.663,  // 1..8
+    7.469, 8.022, 8.201, 8.904, 8.388, 9.027, 8.672, 9.210,  // 9..16
+    8.210, 8.684, 9.165, 9.648, 9.025, 9.443, 9.876, 10.282,  // 17..24
+    8.312, 8.647, 8.981, 9.281, 9.623, 9.949, 10.290, 10.556,  // 25..32
+    8.453, 8.702, 8.964, 9.217, 9.467, 9.716, 9.962, 10.231,  // 33..40
+    9.345, 9.569, 9.799, 10.008, 10.253, 10.483, 10.683, 10.914,  // 41..48
+    9.997, 10.203, 10.389, 10.592, 10.803, 10.982, 11.180, 11.409,  // 49..56
+    10.162, 10.324, 10.509, 10.676, 10.873, 11.042, 11.213, 11.340,  // 57..64
 };
-constexpr double kRateFull[6] = {11.340, 11.640, 12.000, 10.840, 11.060, 10.890};  // 64 .. 2048
+constexpr double kRateFull[6] = {11.342, 11.637, 11.995, 10.847, 11.053, 10.884};  // 64 .. 2048
 
 constexpr int kMaxChunk = 2048;
 

@@ -53,6 +53,14 @@ __global__ void __launch_bounds__(direct_threads(NB, GP), direct_min_blocks(NB, 
     constexpr int RPT = TS / GP;               // rows computed by each thread
     constexpr int ROW = 16;
     constexpr int PSTRIDE = TS * ROW + 4;
+    // Loop unrolling, measured per class: the shared rows of a sub-tile 4
+    // deep for NB <= 4 and 2 deep for NB = 5, 6 (so the next row's loads and
+    // seed overlap this row's evaluations: 1-3% faster), not at all for
+    // NB = 7, 8 (2-5% slower: their registers are already at the cap); the
+    // nodes of a one-thread-per-point tile 2 deep for NB = 1, 2, 4 (3-8%
+    // faster; 3-7% slower for NB = 3, 7, whose extra registers spill).
+    constexpr int kRowUnroll = NB <= 4 ? 4 : (NB <= 6 ? 2 : 1);
+    constexpr int kNodeUnroll = (NB == 1 || NB == 2 || NB == 4) ? 2 : 1;
     __shared__ __align__(16) float rows[GP > 1 ? PPI * PSTRIDE : 4];
     __shared__ __align__(128) float nodebuf[2 * kTileFloats];
     __shared__ __align__(8) uint64_t bar[2];
@@ -162,7 +170,7 @@ __global__ void __launch_bounds__(direct_threads(NB, GP), direct_min_blocks(NB, 
                 // two or three omegas: each phasor straight from the MUFU (its error,
                 // like the seed's, is a constant factor that does not compound),
                 // cheaper than a sincospif rotation and the recurrence
-#pragma unroll 1
+#pragma unroll kNodeUnroll
                 for (int j = 0; j < kTile; ++j) {
                     float co[10];
                     const float phi = pair_coefs(nb, j, P, co);
@@ -179,7 +187,7 @@ __global__ void __launch_bounds__(direct_threads(NB, GP), direct_min_blocks(NB, 
                     }
                 }
             } else if constexpr (GP == 1) {
-#pragma unroll 1
+#pragma unroll kNodeUnroll
                 for (int j = 0; j < kTile; ++j) {
                     float co[10];
                     const float phi = pair_coefs(nb, j, P, co);
@@ -204,7 +212,7 @@ __global__ void __launch_bounds__(direct_threads(NB, GP), direct_min_blocks(NB, 
                         r4[3] = make_float4(phi, 0.f, 0.f, 0.f);
                     }
                     __syncwarp();
-#pragma unroll 1
+#pragma unroll kRowUnroll
                     for (int q = 0; q < TS; ++q) {
                         const float4* r4 = reinterpret_cast<const float4*>(prow + q * ROW);
                         const float4 a0 = r4[0], a1 = r4[1], a2 = r4[2];
