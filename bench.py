@@ -395,15 +395,25 @@ def serving_leg(sc, torch, dev, n_req=16, seed=2016, loads=(0.5, 0.8, 0.95), bud
            "workload": c4_workload_name(n_req, seed) + ", Poisson arrivals, same requests at every load",
            "rates": []}
     rng = np.random.Generator(np.random.PCG64(5))
-    for load in loads:
-        rate = load * sat_rate
-        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
+    draws = [(load, load * sat_rate) for load in loads]
+    draws = [(load, rate, np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))) for load, rate in draws]
+
+    def point(load, rate, arrivals):
         lat, wall, _ = run(arrivals)
         lat_ms = 1000.0 * np.array(lat)
-        out["rates"].append({"load": load, "rate_req_per_s": rate, "requests": len(reqs),
-                             "p50_ms": float(np.percentile(lat_ms, 50)),
-                             "p99_ms": float(np.percentile(lat_ms, 99)),
-                             "throughput_evals_per_s": total / wall})
+        return {"load": load, "rate_req_per_s": rate, "requests": len(reqs),
+                "p50_ms": float(np.percentile(lat_ms, 50)),
+                "p99_ms": float(np.percentile(lat_ms, 99)),
+                "throughput_evals_per_s": total / wall}
+
+    for d in draws:
+        out["rates"].append(point(*d))
+    # the same arrivals, first come first served (SC_OPT_SERVE_PRIORITY = 0)
+    ctx.set_option(sc.SC_OPT_SERVE_PRIORITY, 0)
+    out["fifo_rates"] = [point(*d) for d in draws]
+    out["policy"] = ("short requests (<= 1e11 evals) first on two high-priority lanes; long ones on two "
+                     "low-priority lanes in launches of about 6e10 evals; fifo_rates: the same arrivals first "
+                     "come first served on two lanes")
     ctx.close()
     return out
 

@@ -482,11 +482,23 @@ sc_status sc_eval_batch(sc_ctx* ctx, const sc_request* reqs, int n_req, sc_eval_
  * A server thread (started by the first sc_submit) admits queued requests in
  * arrival order while the device memory they need fits the context's HBM
  * budget (staged points and, for requests without outputs, the outputs the
- * server allocates), batches up to 64 of them and runs each batch as
- * sc_eval_batch does on one of two lanes (streams with their own buffers), so
- * a batch starts while the previous one is still on the GPU.  Node tables
- * stay resident between requests.  The paper has one problem per run; this
- * is the serving pattern of the hot path.
+ * server allocates), batches them and runs each batch as sc_eval_batch does
+ * on a free lane (a stream with its own buffers), so a batch starts while
+ * others are still on the GPU.  Node tables stay resident between requests.
+ * The paper has one problem per run; this is the serving pattern of the hot
+ * path.
+ *   Short requests first (SC_OPT_SERVE_PRIORITY = 1, the default): a request
+ *   of at most 1e11 evaluations (points x surface nodes x omegas) is short.
+ *   Short requests run on two lanes of the highest stream priority, in
+ *   batches of up to 64 requests that close at 3e10 evaluations.  Long
+ *   requests run one per lane on two lanes of the lowest priority, with their
+ *   chunks cut by points into launches of about 6e10 evaluations (larger
+ *   where that would leave a launch fewer than 8 work items per resident
+ *   CTA), each launched when the previous one completes.  A short request
+ *   then waits for at most one such launch of a long one, never for all of
+ *   it.  Results are bitwise those of the request alone either way.
+ *   SC_OPT_SERVE_PRIORITY = 0: two lanes of the default priority, first come
+ *   first served, batches of up to 64 requests, launches not bounded.
  *
  * sc_submit   req->points_xyz host (copied) or device (kept by reference);
  *             req->E_out/B_out NULL: server-owned outputs, read them with
@@ -591,6 +603,11 @@ enum {
                                 /* default layout; 1 the alternative.  Other omega  */
                                 /* counts have one layout.  sc_eval_stats reports   */
                                 /* the layout taken                                 */
+    SC_OPT_SERVE_PRIORITY = 14, /* 1 (default): serving runs short requests first   */
+                                /* and long ones in bounded launches (see Serving); */
+                                /* 0: first come first served.  Stops an idle      */
+                                /* server (the next sc_submit restarts it);         */
+                                /* SC_ERR_BUSY while a ticket is not yet released   */
     SC_OPT_FAIL_COPY = 8        /* failure-path test, -1 (default) off: in every   */
                                 /* batched FP32 field launch, the work item 0 skips */
                                 /* the bulk copy of its node tile `value`, so the   */

@@ -33,7 +33,7 @@ SPECTRA = {"mono": 0, "gauss_time": 1, "supergauss_lambda": 2, "sampled": 3}
 SC_OPT_TIME_FIELD, SC_OPT_NODES_PER_SPLIT, SC_OPT_WORKSPACE_CAP, SC_OPT_FLUSH_NODES = 1, 2, 3, 4
 SC_OPT_GRAPHS, SC_OPT_AUTOTUNE, SC_OPT_OMEGA_CHUNKS, SC_OPT_FAIL_COPY = 5, 6, 7, 8
 SC_OPT_MFIE_ORDER, SC_OPT_MFIE_RHO, SC_OPT_MFIE_PHI, SC_OPT_CLASS_STREAMS = 9, 10, 11, 12
-SC_OPT_TILE_LAYOUT = 13
+SC_OPT_TILE_LAYOUT, SC_OPT_SERVE_PRIORITY = 13, 14
 
 _DP = ctypes.POINTER(ctypes.c_double)
 _VP = ctypes.c_void_p

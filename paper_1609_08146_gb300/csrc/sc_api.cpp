@@ -906,6 +906,7 @@ sc_status sc_submit(sc_ctx* ctx, const sc_request* req, uint64_t* ticket)
     t.n_points = req->n_points;
     t.n_omega = req->n_omega;
     t.dom = dom;
+    t.evals = (double)req->n_points * req->mirror->q.n_r * req->mirror->q.n_theta * req->n_omega;
     if (is_device_ptr(req->points_xyz)) {
         t.user_pts = req->points_xyz;
     } else {
@@ -1136,6 +1137,19 @@ sc_status sc_reset_counters(sc_ctx* ctx)
 sc_status sc_set_option(sc_ctx* ctx, int option, long long value)
 {
     if (!ctx) return SC_ERR_INVALID;
+    if (option == SC_OPT_SERVE_PRIORITY) {
+        // the lanes are set up when the server starts: stop an idle server
+        // (the next sc_submit starts it again with the new policy)
+        {
+            std::lock_guard<std::mutex> lock(ctx->mu);
+            if (ctx->server && !ctx->server->tickets.empty())
+                return fail(ctx, SC_ERR_BUSY, "serving policy: release every ticket first");
+        }
+        sch::stop_server(ctx);
+        std::lock_guard<std::mutex> lock(ctx->mu);
+        ctx->serve_priority = value != 0;
+        return SC_OK;
+    }
     std::lock_guard<std::mutex> lock(ctx->mu);
     switch (option) {
     case SC_OPT_TIME_FIELD: ctx->time_field = value != 0; return SC_OK;

@@ -30,11 +30,20 @@ void set_splits(Chunk& c, int S, int tiles)
     c.ws_elems = (size_t)(c.f.n_splits + 1) * c.f.n_pts * c.f.n_omega * sc::kAcc * c.n_parts;
 }
 
-int heuristic_splits(int tiles, long long pb, int slots)
+// Largest work item the split heuristic aims for, in evaluations: about 6 ms
+// of one CTA at the field kernels' rate (2 CTAs per SM).  Serving cuts a long
+// request into launches of a few dozen milliseconds, and such a launch stays
+// balanced only if each CTA takes several items.
+constexpr double kMaxItemEvals = 2.5e7;
+
+// items_evals: the evaluations of one item if the chunk had a single split
+int heuristic_splits(int tiles, long long pb, int slots, double item_evals)
 {
     // enough items for dynamic balance (about 16 per resident CTA), items of
-    // at least 32 node tiles, at most 64 splits
+    // at most kMaxItemEvals evaluations and at least 32 node tiles, at most
+    // 64 splits
     long long s = (16LL * slots + pb - 1) / pb;
+    s = std::max<long long>(s, (long long)std::ceil(item_evals / kMaxItemEvals));
     s = std::min<long long>(s, std::max(1, tiles / 32));
     return (int)std::max<long long>(1, std::min<long long>(64, s));
 }
@@ -76,7 +85,17 @@ sc_status choose_splits(sc_ctx* ctx, Lane& ln, Chunk& c, const Table* tab, int s
         *S_out = hit->second;
         return SC_OK;
     }
-    const int s0 = heuristic_splits(tiles, c.pb, slots);
+    // whole-request workspace of split count s
+    auto ws_bytes = [&](int s) {
+        const int tps = (tiles + s - 1) / s;
+        const int ns = (tiles + tps - 1) / tps;
+        return (size_t)(ns + 1) * c.f.n_pts * c.f.n_omega * sc::kAcc * c.n_parts * sizeof(float2);
+    };
+    int s0 = heuristic_splits(tiles, c.pb, slots, (double)c.ppc * tiles * sc::kTile * c.f.n_omega * c.n_parts);
+    // the item-size bound never cuts into points a request that balance alone keeps in one launch
+    const int sb = heuristic_splits(tiles, c.pb, slots, 0.0);
+    if (ws_bytes(sb) <= ctx->ws_cap)
+        while (s0 > sb && ws_bytes(s0) > ctx->ws_cap) --s0;
     int best = s0;
     if (ctx->autotune) {
         // candidates around the heuristic, each timed once on the real chunk
@@ -254,6 +273,9 @@ int next_chunk(int n, bool small)
     return chunk_plan().first[small ? 1 : 0][std::min(n, kMaxChunk)];
 }
 
+// a launch bounded in evaluations still gives each resident CTA this many items
+constexpr double kMinItemsPerCta = 8.0;
+
 // requests of at least this many (point, node) pairs per omega take the
 // splits at small omega counts
 constexpr long long kSmallCutPairs = 1LL << 22;
@@ -321,9 +343,20 @@ sc_status plan_request(sc_ctx* ctx, Lane& ln, const Table* tab, const double* om
         if (st != SC_OK) return st;
         set_splits(c, S, tab->n_surf_tiles);
         const int n_splits = c.f.n_splits;
-        // point chunks bounded by the workspace cap
+        // point chunks bounded by the workspace cap and, on a lane whose
+        // launches are bounded (serving's long requests), by its evaluations
+        // per launch; the split count above stays that of the whole request,
+        // so every point's arithmetic is the same however the points are cut
         const size_t per_pt = (size_t)(n_splits + 1) * no * sc::kAcc * c.n_parts;
         long long pchunk = std::max<long long>(1, (long long)(ctx->ws_cap / sizeof(float2) / per_pt));
+        if (ln.max_launch_evals > 0.0) {
+            // never fewer than kMinItemsPerCta items per resident CTA, or the
+            // launch's tail would idle most of the GPU
+            const double pt_evals = (double)tab->n_surf_tiles * sc::kTile * no * c.n_parts;
+            const double item = (double)c.ppc * c.f.tiles_per_split * sc::kTile * no * c.n_parts;
+            const double g = std::max(ln.max_launch_evals, kMinItemsPerCta * slots * item);
+            pchunk = std::min<long long>(pchunk, std::max<long long>(1, (long long)(g / pt_evals)));
+        }
         if (pchunk < n_points) pchunk = std::max<long long>(c.ppc, pchunk / c.ppc * c.ppc);
         for (int p0 = 0; p0 < n_points; p0 += (int)pchunk) {
             const int np = (int)std::min<long long>(pchunk, n_points - p0);
@@ -422,7 +455,7 @@ sc_status launch_chunks(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch, float2* w
         while (ln.side.size() < launches.size()) {
             cudaStream_t b = nullptr;
             cudaEvent_t e = nullptr;
-            SC_CUDA(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking), "class stream");
+            SC_CUDA(cudaStreamCreateWithPriority(&b, cudaStreamNonBlocking, ln.prio), "class stream");
             ln.side.push_back(b);
             SC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "join event");
             ln.join_ev.push_back(e);
@@ -476,7 +509,8 @@ sc_status launch_chunks(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch, float2* w
             }
         if (!exec) {
             if (!ln.cap_stream)
-                SC_CUDA(cudaStreamCreateWithFlags(&ln.cap_stream, cudaStreamNonBlocking), "capture stream");
+                SC_CUDA(cudaStreamCreateWithPriority(&ln.cap_stream, cudaStreamNonBlocking, ln.prio),
+                        "capture stream");
             SC_CUDA(cudaStreamBeginCapture(ln.cap_stream, cudaStreamCaptureModeRelaxed), "begin capture");
             st = issue(ln.cap_stream);
             cudaGraph_t g = nullptr;
@@ -527,20 +561,41 @@ sc_status launch_chunks_direct(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch, fl
     return st;
 }
 
-// Run chunks in groups whose workspace fits under the cap.
-sc_status run_chunks(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch)
+// Evaluations of one chunk, every table part.
+double chunk_evals(const Chunk& c)
+{
+    return (double)c.f.n_pts * c.f.n_surf_tiles * sc::kTile * c.f.n_omega * c.n_parts;
+}
+
+// Launch the group of chunks that starts at ch[i] -- as many as fit under
+// the workspace cap (and, on a lane with bounded launches, under its bound
+// on evaluations) -- and advance i past it.
+sc_status run_chunk_group(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch, size_t& i)
 {
     const size_t cap = std::max<size_t>(ctx->ws_cap / sizeof(float2), 1);
+    const double ecap = ln.max_launch_evals > 0.0 ? ln.max_launch_evals : 1e300;
+    size_t j = i, tot = 0;
+    double ev = 0.0;
+    while (j < ch.size() && (j == i || (tot + ch[j].ws_elems <= cap && ev + chunk_evals(ch[j]) <= ecap))) {
+        ev += chunk_evals(ch[j]);
+        tot += ch[j++].ws_elems;
+    }
+    sc_status st = ensure(ctx, ln.ws, tot * sizeof(float2), ln.stream);
+    if (st != SC_OK) return st;
+    std::vector<Chunk> part(ch.begin() + i, ch.begin() + j);
+    st = launch_chunks(ctx, ln, part, (float2*)ln.ws.p, tot, ctx->use_graphs && ln.use_graphs);
+    if (st != SC_OK) return st;
+    i = j;
+    return SC_OK;
+}
+
+// Run every chunk, group by group.
+sc_status run_chunks(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch)
+{
     size_t i = 0;
     while (i < ch.size()) {
-        size_t j = i, tot = 0;
-        while (j < ch.size() && (j == i || tot + ch[j].ws_elems <= cap)) tot += ch[j++].ws_elems;
-        sc_status st = ensure(ctx, ln.ws, tot * sizeof(float2), ln.stream);
+        const sc_status st = run_chunk_group(ctx, ln, ch, i);
         if (st != SC_OK) return st;
-        std::vector<Chunk> part(ch.begin() + i, ch.begin() + j);
-        st = launch_chunks(ctx, ln, part, (float2*)ln.ws.p, tot, ctx->use_graphs);
-        if (st != SC_OK) return st;
-        i = j;
     }
     return SC_OK;
 }

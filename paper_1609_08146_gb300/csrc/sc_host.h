@@ -107,6 +107,9 @@ struct GraphEntry {
 struct Lane {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    int prio = 0;                   // stream priority of the lane (side streams take it too)
+    bool use_graphs = true;         // capture its field launches (if the context does)
+    double max_launch_evals = 0.0;  // > 0: bound the evaluations of one launch group
     DevBuf ws, desc, amp, kval;
     cudaStream_t cap_stream = nullptr;
     std::vector<GraphEntry> graphs;
@@ -146,6 +149,7 @@ struct sc_ctx {
     bool autotune = true;
     bool omega_chunks = true;       // plan omega chunk sizes (else 2048 per chunk)
     bool class_streams = true;      // a batch's kernel classes run as concurrent branches
+    bool serve_priority = true;     // serving: short requests first, long ones preemptible
     int tile_layout = -1;           // -1 autotuned, 0 default, 1 alternative layout
     int shape_cls = -1, shape_splits = -1;  // tile shape of the last planned first chunk
     int fail_tile = -1;             // failure-path test: a node-tile copy left unissued
@@ -232,6 +236,7 @@ sc_status plan_request(sc_ctx* ctx, Lane& ln, const Table* tab, const double* om
                        const double* d_pts, int n_points, const double* d_amp, const double* d_k, float2* dE,
                        float2* dB, std::vector<Chunk>& out);
 sc_status run_chunks(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch);
+sc_status run_chunk_group(sc_ctx* ctx, Lane& ln, std::vector<Chunk>& ch, size_t& i);
 void free_lane(Lane& ln);
 
 // ---- serving (sc_serve.cpp)
@@ -255,10 +260,15 @@ struct Ticket {
     double t_submit = 0, t_start = 0, t_done = 0;
     int lane = -1;
     Table* tab = nullptr;
+    double evals = 0.0;                 // points x surface nodes x omegas
 };
 
 struct Server {
-    static constexpr int kLanes = 2;
+    // lanes 0, 1: short requests, high stream priority; lanes 2, 3: long
+    // requests, low priority, in launch groups of bounded size
+    static constexpr int kLanes = 4;
+    static constexpr int kShortLanes = 2;
+    bool priority = true;               // sc_ctx::serve_priority when the server started
     std::thread th;
     bool stop = false;
     std::condition_variable cv;
@@ -268,6 +278,10 @@ struct Server {
     cudaEvent_t done_ev[kLanes] = {};
     std::vector<uint64_t> batch[kLanes];
     bool busy[kLanes] = {};
+    // a long lane's chunks not yet launched: one bounded group is in flight
+    // at a time, the next is launched when it completes
+    std::vector<Chunk> pend[kLanes];
+    size_t pend_i[kLanes] = {};
     size_t held = 0;                    // bytes of admitted tickets not yet released
     uint64_t next_id = 1;
     int max_batch = 64;

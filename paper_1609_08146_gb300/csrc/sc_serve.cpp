@@ -9,12 +9,35 @@ namespace sch {
 // ------------------------------------------------------------------------
 // Serving (A9): continuous batching of submitted requests.  A server thread
 // admits queued requests in arrival order while their device memory (staged
-// points and server-owned outputs) fits the context's HBM budget, batches up
-// to max_batch of them and runs the batch on a free lane; with two lanes a
-// new batch starts while the previous one is still on the GPU, so requests
-// that arrive meanwhile overlap with it.  Completion is observed through an
-// event per lane; memory returns to the budget when the caller releases the
-// ticket.
+// points and server-owned outputs) fits the context's HBM budget, batches
+// them and runs each batch on a free lane (a stream with its own buffers), so
+// requests that arrive while others run overlap with them on the device.
+// Completion is observed through an event per lane; memory returns to the
+// budget when the caller releases the ticket.
+//
+// Short requests first.  A few long requests carry most of the work of a
+// mixed stream, and under first-come-first-served every short request that
+// arrives behind one waits for all of it.  So requests are classed by their
+// evaluations (points x surface nodes x omegas):
+//   * short ones (at most kLongEvals) run on two lanes whose streams have the
+//     highest priority, batched until a batch holds kShortBatchEvals;
+//   * long ones run one at a time on two lanes of the lowest priority, and
+//     their chunks are cut by points into launches of about kGroupEvals
+//     (more where that would leave fewer than 8 work items per resident CTA),
+//     launched one after another as each completes.
+// The field kernels are persistent (their CTAs stay until a launch's work
+// is drained), so a running launch is never interrupted.  But when one of a
+// long request's bounded launches ends, the block scheduler gives the freed
+// SMs to pending high-priority work first: a short request waits for at most
+// one such launch instead of a whole long request.  Two long lanes share the
+// GPU launch by launch, so a long request does not wait for a longer one
+// ahead of it either.  Cutting by points keeps every point's arithmetic (its
+// split count is that of the whole request), so results stay bitwise the same
+// as alone.  With SC_OPT_SERVE_PRIORITY = 0 the server uses two lanes of the
+// default priority, first come first served, without bounded launches.
+constexpr double kLongEvals = 1e11;        // about 90 ms of field work on one GB300
+constexpr double kGroupEvals = 6e10;       // about 50 ms
+constexpr double kShortBatchEvals = 3e10;
 
 size_t ticket_bytes(const Ticket& t)
 {
@@ -23,6 +46,8 @@ size_t ticket_bytes(const Ticket& t)
     if (t.own_out) b += (size_t)2 * t.n_omega * t.n_points * 3 * sizeof(float2);
     return b;
 }
+
+sc_status launch_next_group(sc_ctx* ctx, Server* srv, int L);
 
 // Run one batch of admitted tickets on lane L (ctx->mu held).  A ticket
 // whose node tables cannot be built (an envelope too rough to fit, a device
@@ -90,10 +115,48 @@ sc_status launch_batch(sc_ctx* ctx, Server* srv, int L, std::vector<uint64_t>& i
         if (st != SC_OK) return st;
         ctx->ctr.evals += (double)t.n_points * t.tab->n_surf * t.n_omega;
     }
+    if (ln.max_launch_evals > 0.0) {
+        // a long lane launches one bounded group now and the next when it
+        // completes, so work admitted later is never queued behind the rest
+        srv->pend[L].swap(ch);
+        srv->pend_i[L] = 0;
+        return launch_next_group(ctx, srv, L);
+    }
     st = run_chunks(ctx, ln, ch);
     if (st != SC_OK) return st;
     SC_CUDA(cudaEventRecord(srv->done_ev[L], ln.stream), "completion event");
     return SC_OK;
+}
+
+// Launch the next bounded group of lane L's pending chunks (ctx->mu held);
+// the lane's completion event follows it.
+sc_status launch_next_group(sc_ctx* ctx, Server* srv, int L)
+{
+    Lane& ln = srv->lanes[L];
+    const sc_status st = run_chunk_group(ctx, ln, srv->pend[L], srv->pend_i[L]);
+    if (st != SC_OK) return st;
+    if (srv->pend_i[L] >= srv->pend[L].size()) {
+        srv->pend[L].clear();
+        srv->pend_i[L] = 0;
+    }
+    SC_CUDA(cudaEventRecord(srv->done_ev[L], ln.stream), "completion event");
+    return SC_OK;
+}
+
+// Fail every ticket of a batch whose launch failed on lane L.
+void fail_batch(Server* srv, int L, const std::vector<uint64_t>& ids, sc_status st)
+{
+    cudaStreamSynchronize(srv->lanes[L].stream);
+    for (uint64_t id : ids) {
+        Ticket& t = srv->tickets[id];
+        if (t.tab) t.tab->inflight--;
+        t.tab = nullptr;
+        t.state = 3;
+        t.status = st;
+        t.t_done = srv->now();
+    }
+    srv->pend[L].clear();
+    srv->pend_i[L] = 0;
 }
 
 void serve(sc_ctx* ctx)
@@ -103,11 +166,22 @@ void serve(sc_ctx* ctx)
     std::unique_lock<std::mutex> lk(ctx->mu);
     while (!srv->stop) {
         bool changed = false;
+        std::vector<int> next_group;  // long lanes whose group completed, with more to launch
         // completions
         for (int L = 0; L < Server::kLanes; ++L) {
             if (!srv->busy[L]) continue;
             const cudaError_t q = cudaEventQuery(srv->done_ev[L]);
             if (q == cudaErrorNotReady) continue;
+            if (q == cudaSuccess && !srv->pend[L].empty()) {
+                bool all_cancelled = true;
+                for (uint64_t id : srv->batch[L]) all_cancelled = all_cancelled && srv->tickets[id].cancel;
+                if (!all_cancelled) {
+                    next_group.push_back(L);
+                    continue;
+                }
+            }
+            srv->pend[L].clear();  // done, failed, or all cancelled: drop what is left
+            srv->pend_i[L] = 0;
             const double t = srv->now();
             for (uint64_t id : srv->batch[L]) {
                 auto it = srv->tickets.find(id);
@@ -128,16 +202,37 @@ void serve(sc_ctx* ctx)
             srv->busy[L] = false;
             changed = true;
         }
-        // admission and launch on free lanes
-        for (int L = 0; L < Server::kLanes && !srv->queue.empty(); ++L) {
-            if (srv->busy[L]) continue;
+        // admission and launch on free lanes: the short lanes first, then the
+        // long lanes' next groups, then new long requests
+        const int n_lanes = srv->priority ? Server::kLanes : 2;
+        auto launch_groups = [&]() {
+            for (int G : next_group) {
+                const sc_status gst = launch_next_group(ctx, srv, G);
+                if (gst != SC_OK) {
+                    fail_batch(srv, G, srv->batch[G], gst);
+                    srv->batch[G].clear();
+                    srv->busy[G] = false;
+                }
+                changed = true;
+            }
+            next_group.clear();
+        };
+        for (int L = 0; L < n_lanes; ++L) {
+            if (L == Server::kShortLanes) launch_groups();
+            if (srv->busy[L] || srv->queue.empty()) continue;
             // workspace the lanes may still grow into (bounded by the cap)
             size_t reserve = size_t(16) << 20;
-            for (int M = 0; M < Server::kLanes; ++M)
+            for (int M = 0; M < n_lanes; ++M)
                 if (srv->lanes[M].ws.n < ctx->ws_cap) reserve += ctx->ws_cap - srv->lanes[M].ws.n;
+            const bool short_lane = L < Server::kShortLanes;
             std::vector<uint64_t> ids;
-            while (!srv->queue.empty() && (int)ids.size() < srv->max_batch) {
-                Ticket& t = srv->tickets[srv->queue.front()];
+            double batch_evals = 0.0;
+            for (auto it = srv->queue.begin(); it != srv->queue.end() && (int)ids.size() < srv->max_batch;) {
+                Ticket& t = srv->tickets[*it];
+                if (srv->priority && (t.evals > kLongEvals) == short_lane) {
+                    ++it;  // a request for the other kind of lane
+                    continue;
+                }
                 const size_t b = ticket_bytes(t);
                 // admit only what fits next to every lane's full workspace; the
                 // first request of an idle server is always admitted
@@ -145,31 +240,28 @@ void serve(sc_ctx* ctx)
                 if (ctx->budget && !idle && ctx->held + srv->held + b + reserve > ctx->budget) break;
                 t.bytes = b;
                 srv->held += b;
-                ids.push_back(srv->queue.front());
-                srv->queue.pop_front();
+                ids.push_back(*it);
+                it = srv->queue.erase(it);
+                batch_evals += t.evals;
+                // a long lane runs one request at a time; a short lane's batch
+                // closes once it holds enough work to fill the GPU
+                if (srv->priority && (!short_lane || batch_evals >= kShortBatchEvals)) break;
             }
-            if (ids.empty()) break;
+            if (ids.empty()) continue;
             const sc_status st = launch_batch(ctx, srv, L, ids);
             if (st == SC_OK && ids.empty()) {
                 changed = true;
                 continue;
             }
             if (st != SC_OK) {
-                cudaStreamSynchronize(srv->lanes[L].stream);
-                for (uint64_t id : ids) {
-                    Ticket& t = srv->tickets[id];
-                    if (t.tab) t.tab->inflight--;
-                    t.tab = nullptr;
-                    t.state = 3;
-                    t.status = st;
-                    t.t_done = srv->now();
-                }
+                fail_batch(srv, L, ids, st);
             } else {
                 srv->batch[L] = ids;
                 srv->busy[L] = true;
             }
             changed = true;
         }
+        launch_groups();
         if (changed) srv->cv.notify_all();
         srv->cv.wait_for(lk, std::chrono::microseconds(100));
     }
@@ -179,14 +271,31 @@ sc_status start_server(sc_ctx* ctx)
 {
     if (ctx->server) return SC_OK;
     Server* srv = new Server();
+    srv->priority = ctx->serve_priority;
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        least = greatest = 0;
+    }
     for (int L = 0; L < Server::kLanes; ++L) {
-        if (cudaStreamCreateWithFlags(&srv->lanes[L].stream, cudaStreamNonBlocking) != cudaSuccess ||
+        Lane& ln = srv->lanes[L];
+        const bool short_lane = srv->priority && L < Server::kShortLanes;
+        const bool long_lane = srv->priority && L >= Server::kShortLanes;
+        ln.prio = short_lane ? greatest : least;
+        // captured launches are not relied on to keep the stream's priority
+        ln.use_graphs = !short_lane;
+        ln.max_launch_evals = long_lane ? kGroupEvals : 0.0;
+        if (cudaStreamCreateWithPriority(&ln.stream, cudaStreamNonBlocking, ln.prio) != cudaSuccess ||
             cudaEventCreateWithFlags(&srv->done_ev[L], cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
+            for (int M = 0; M <= L; ++M) {
+                if (srv->lanes[M].stream) cudaStreamDestroy(srv->lanes[M].stream);
+                if (srv->done_ev[M]) cudaEventDestroy(srv->done_ev[M]);
+            }
             delete srv;
             return fail(ctx, SC_ERR_CUDA, "serving lane set-up failed");
         }
-        srv->lanes[L].own_stream = true;
+        ln.own_stream = true;
     }
     ctx->server = srv;
     srv->th = std::thread(serve, ctx);

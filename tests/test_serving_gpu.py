@@ -1,9 +1,10 @@
 """Serving: continuous batching of submitted requests (sc_submit/poll/wait).
 
 Requests submitted while others run are admitted as memory frees up, run in
-overlapping batches on two lanes, and each result is bitwise the same as the
-request evaluated alone.  Admission respects the HBM budget, a request that
-can never fit is refused, and cancellation is honoured.
+overlapping batches on several lanes, and each result is bitwise the same as
+the request evaluated alone.  Short requests pass a long one that runs in
+bounded launches on a low-priority lane.  Admission respects the HBM budget,
+a request that can never fit is refused, and cancellation is honoured.
 """
 import time
 
@@ -113,5 +114,44 @@ def test_admission_by_budget():
         with pytest.raises(sc.ScError) as e:
             ctx.submit(m, inc, np.linspace(0.5, 1.5, 256), big)
         assert e.value.status == sc.SC_ERR_BUSY
+    finally:
+        ctx.close()
+
+
+def test_short_requests_pass_a_long_one():
+    # a long request (512^2 nodes x 4160 points x 128 omegas = 1.4e11
+    # evaluations, above the 1e11 bound) runs on a low-priority lane in
+    # launches of about 6e10 evaluations; short requests submitted after it
+    # run on the high-priority lanes between those launches and finish first
+    ctx = sc.Context(0)
+    try:
+        long_req = make(ctx, 6.25e4, 512, 512, 128, 4160, 3)
+        small = [make(ctx, 1e3 * (1 + i), 64, 64, 16 + 8 * i, 500 + 100 * i, 20 + i,
+                      pol=("linear", "radial", "azimuthal")[i % 3]) for i in range(4)]
+        reqs = [long_req] + small
+        alone = [ctx.eval(m, inc, om, torch.tensor(p, device="cuda")) for (m, inc, om, p) in reqs]
+        torch.cuda.synchronize()
+        for priority in (1, 0):
+            ctx.set_option(sc.SC_OPT_SERVE_PRIORITY, priority)
+            ts = [ctx.submit(m, inc, om, p) for (m, inc, om, p) in reqs]
+            for t in ts:
+                ctx.wait(t, 120.0)
+            for t, (Ea, Ba) in zip(ts, alone):
+                E, B = ctx.fetch(t)
+                assert torch.equal(E, Ea) and torch.equal(B, Ba)
+            times = [ctx.ticket_times(t) for t in ts]
+            done = [x[2] for x in times]
+            if priority:
+                assert all(d < done[0] for d in done[1:]), times
+            for t in ts:
+                ctx.release(t)
+        # the policy changes only while no ticket is outstanding
+        t = ctx.submit(*small[0])
+        with pytest.raises(sc.ScError) as e:
+            ctx.set_option(sc.SC_OPT_SERVE_PRIORITY, 1)
+        assert e.value.status == sc.SC_ERR_BUSY
+        ctx.wait(t, 60.0)
+        ctx.release(t)
+        ctx.set_option(sc.SC_OPT_SERVE_PRIORITY, 1)
     finally:
         ctx.close()
