@@ -1,5 +1,5 @@
 // sc_serve.cpp -- serving (A9): the server thread that admits, batches and
-// completes submitted requests on two lanes.
+// completes submitted requests on four lanes (two for short requests, two for long ones).
 #include <algorithm>
 
 #include "sc_host.h"
