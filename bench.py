@@ -63,14 +63,15 @@ def parse():
                     help="skip the batched and serving legs")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="broadband",
-                    choices=["broadband", "profile", "small_omega", "c5", "c4", "sweep"],
+                    choices=["broadband", "profile", "small_omega", "c5", "c4", "tiny", "sweep"],
                     help="broadband: the benchmark workload; profile: the same kernel "
                          "configuration at 128 x 128 nodes, for ncu captures; small_omega: the "
                          "broadband mirror, pulse and points at 256 x 256 nodes and 8 omegas (the "
                          "direct kernel of small requests); c5: the largest "
                          "serving request (1024^2 nodes, GRID^3 points over +-3, 512 omegas, "
                          "512 times) through the fused time-domain path, timed once; c4: the "
-                         "batched leg at its full size (64 requests); sweep: the precision "
+                         "batched leg at its full size (64 requests); tiny: 512 small requests "
+                         "batched against one by one; sweep: the precision "
                          "sweep over f and node counts (per-component errors)")
     ap.add_argument("--grid", type=int, default=128, help="points per axis of the c5 workload")
     ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
@@ -298,14 +299,19 @@ def c4_workload_name(n, seed):
             "linear/radial/azimuthal, Zernike j=2..15 N(0, 0.1) waves" % (n, seed))
 
 
-def batch_leg(sc, torch, dev, n_req=16, seed=1609, check=True):
+def batch_leg(sc, torch, dev, n_req=16, seed=1609, check=True, tiny=False):
     """The uneven batch at the batched workload's full ranges: one
     sc_eval_batch against the same requests one by one (both timed after a
     warm-up pass that builds the tables and tunes the shapes); the batch
-    must equal the one-by-one results bitwise."""
+    must equal the one-by-one results bitwise.  tiny: a mix of small
+    requests instead (64^2-128^2 nodes, 256-2048 points, 1-16 omegas), the
+    regime where one scheduled pass pays over a call per request."""
     from paper_1609_08146_gb300 import workloads as wl
 
-    configs, reqs = wl.config4_requests(n_req, seed=seed)
+    if tiny:
+        configs, reqs = wl.uneven_requests(n_req, seed, max_nodes=128, max_points=2048, max_omega=16)
+    else:
+        configs, reqs = wl.config4_requests(n_req, seed=seed)
     stream = torch.cuda.Stream(device=dev)
     ctx = sc.Context(dev.index or 0, stream=stream)
     hs = make_config_handles(ctx, configs)
@@ -334,7 +340,11 @@ def batch_leg(sc, torch, dev, n_req=16, seed=1609, check=True):
             "sequential_value": evals / t_seq, "batch_ms": 1000 * t_batch, "sequential_ms": 1000 * t_seq,
             "bitwise_equal_alone": bool(same), "oracle_rel_l2_err": err,
             "oracle_sample": "first 4 points x up to 16 omegas of every request, FP64 oracle",
-            "warmup_s": warm_s, "workload": c4_workload_name(n_req, seed)}
+            "warmup_s": warm_s,
+            "workload": (("%d seeded small requests (seed %d) over 8 mirror/beam configurations: f 1e3-1e5 "
+                          "lambda0, 64^2-128^2 nodes, 256-2048 points, 1-16 omegas, Gaussian/super-Gaussian, "
+                          "linear/radial/azimuthal, Zernike" % (n_req, seed)) if tiny
+                         else c4_workload_name(n_req, seed))}
 
 
 def serving_leg(sc, torch, dev, n_req=16, seed=2016, loads=(0.5, 0.8, 0.95), budget=150 << 30):
@@ -582,10 +592,13 @@ def main():
     if args.workload == "sweep":
         run_sweep(args, ctx, sc, torch, dev, stream, wl)
         return
-    if args.workload == "c4":
+    if args.workload in ("c4", "tiny"):
         clk = ClockSampler(local)
         clk.start()
-        res = batch_leg(sc, torch, dev, n_req=64, seed=1609)
+        if args.workload == "c4":
+            res = batch_leg(sc, torch, dev, n_req=64, seed=1609)
+        else:
+            res = batch_leg(sc, torch, dev, n_req=512, seed=7, tiny=True)
         res["clocks"] = clk.stop()
         res["metric"] = "Stratton-Chu obs*node*omega evals/s (batched)"
         print(json.dumps(res), flush=True)
