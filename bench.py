@@ -63,17 +63,17 @@ def parse():
                     help="skip the batched and serving legs")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="broadband",
-                    choices=["broadband", "profile", "small_omega", "c5", "c4", "tiny", "sweep"],
+                    choices=["broadband", "profile", "small_omega", "largest", "batched", "tiny", "sweep"],
                     help="broadband: the benchmark workload; profile: the same kernel "
                          "configuration at 128 x 128 nodes, for ncu captures; small_omega: the "
                          "broadband mirror, pulse and points at 256 x 256 nodes and 8 omegas (the "
-                         "direct kernel of small requests); c5: the largest "
+                         "direct kernel of small requests); largest: the largest "
                          "serving request (1024^2 nodes, GRID^3 points over +-3, 512 omegas, "
-                         "512 times) through the fused time-domain path, timed once; c4: the "
+                         "512 times) through the fused time-domain path, timed once; batched: the "
                          "batched leg at its full size (64 requests); tiny: 512 small requests "
                          "batched against one by one; sweep: the precision "
                          "sweep over f and node counts (per-component errors)")
-    ap.add_argument("--grid", type=int, default=128, help="points per axis of the c5 workload")
+    ap.add_argument("--grid", type=int, default=128, help="points per axis of the largest workload")
     ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
                     help="N > 1: weak = every rank evaluates the whole workload (replicas); strong = the "
                          "points are sharded across ranks (sharding.py, no data-path collective) and the "
@@ -293,7 +293,7 @@ def sampled_oracle_error(configs, reqs, outs, n_points=4, n_omega=16):
     return worst
 
 
-def c4_workload_name(n, seed):
+def full_range_workload_name(n, seed):
     return ("%d seeded uneven requests (seed %d), each its own mirror and beam: f 1e3-1e5 lambda0 "
             "log-uniform, 128^2-1024^2 nodes, 1k-262k points, 1-512 omegas, Gaussian/super-Gaussian, "
             "linear/radial/azimuthal, Zernike j=2..15 N(0, 0.1) waves" % (n, seed))
@@ -311,7 +311,7 @@ def batch_leg(sc, torch, dev, n_req=16, seed=1609, check=True, tiny=False):
     if tiny:
         configs, reqs = wl.uneven_requests(n_req, seed, max_nodes=128, max_points=2048, max_omega=16)
     else:
-        configs, reqs = wl.config4_requests(n_req, seed=seed)
+        configs, reqs = wl.full_range_requests(n_req, seed=seed)
     stream = torch.cuda.Stream(device=dev)
     ctx = sc.Context(dev.index or 0, stream=stream)
     hs = make_config_handles(ctx, configs)
@@ -344,7 +344,7 @@ def batch_leg(sc, torch, dev, n_req=16, seed=1609, check=True, tiny=False):
             "workload": (("%d seeded small requests (seed %d) over 8 mirror/beam configurations: f 1e3-1e5 "
                           "lambda0, 64^2-128^2 nodes, 256-2048 points, 1-16 omegas, Gaussian/super-Gaussian, "
                           "linear/radial/azimuthal, Zernike" % (n_req, seed)) if tiny
-                         else c4_workload_name(n_req, seed))}
+                         else full_range_workload_name(n_req, seed))}
 
 
 def serving_leg(sc, torch, dev, n_req=16, seed=2016, loads=(0.5, 0.8, 0.95), budget=150 << 30):
@@ -355,7 +355,7 @@ def serving_leg(sc, torch, dev, n_req=16, seed=2016, loads=(0.5, 0.8, 0.95), bud
     by the server."""
     from paper_1609_08146_gb300 import workloads as wl
 
-    configs, reqs = wl.config4_requests(n_req, seed=seed)
+    configs, reqs = wl.full_range_requests(n_req, seed=seed)
     ctx = sc.Context(dev.index or 0, budget_bytes=budget)
     ctx.set_option(sc.SC_OPT_AUTOTUNE, 0)  # no timing runs on the serving path
     hs = make_config_handles(ctx, configs)
@@ -402,7 +402,7 @@ def serving_leg(sc, torch, dev, n_req=16, seed=2016, loads=(0.5, 0.8, 0.95), bud
            "requests": n_req, "evals": total, "budget_bytes": budget,
            "oracle_rel_l2_err": err,
            "oracle_sample": "the two smallest requests as served: first 4 points x up to 16 omegas",
-           "workload": c4_workload_name(n_req, seed) + ", Poisson arrivals, same requests at every load",
+           "workload": full_range_workload_name(n_req, seed) + ", Poisson arrivals, same requests at every load",
            "rates": []}
     rng = np.random.Generator(np.random.PCG64(5))
     draws = [(load, load * sat_rate) for load in loads]
@@ -528,7 +528,7 @@ def run_sweep(args, ctx, sc, torch, dev, stream, wl):
     print(json.dumps(line), flush=True)
 
 
-def run_c5(args, ctx, sc, torch, dev, stream, wl):
+def run_largest(args, ctx, sc, torch, dev, stream, wl):
     """The largest serving request: the broadband mirror and pulse at 1024^2
     nodes and 512 omegas, a GRID^3 point grid over +-3 lambda0 and 512 time
     samples, straight to E(t), B(t) through sc_eval_time_domain (device
@@ -586,16 +586,16 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     ctx = sc.Context(local, stream=stream)
-    if args.workload == "c5":
-        run_c5(args, ctx, sc, torch, dev, stream, wl)
+    if args.workload == "largest":
+        run_largest(args, ctx, sc, torch, dev, stream, wl)
         return
     if args.workload == "sweep":
         run_sweep(args, ctx, sc, torch, dev, stream, wl)
         return
-    if args.workload in ("c4", "tiny"):
+    if args.workload in ("batched", "tiny"):
         clk = ClockSampler(local)
         clk.start()
-        if args.workload == "c4":
+        if args.workload == "batched":
             res = batch_leg(sc, torch, dev, n_req=64, seed=1609)
         else:
             res = batch_leg(sc, torch, dev, n_req=512, seed=7, tiny=True)

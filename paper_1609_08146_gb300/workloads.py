@@ -14,7 +14,7 @@ lambda0, omega in units of omega0, time in lambda0/c (2.6685 fs at 800 nm).
             points on the axis over +-5, 512 time samples t = (m - 256)/8.
   sweep     the broadband pulse with f in {1e2, 1e3, 1e4, 1e5}, r_max = 2f,
             w0 = 0.6 f, N x N nodes, 4096 uniform random points in [-2, 2]^3.
-  config4_requests  uneven requests, each its own mirror and beam, 128^2 to
+  full_range_requests  uneven requests, each its own mirror and beam, 128^2 to
             1024^2 nodes, 1k to 262k points, 1 to 512 omegas.
 """
 from __future__ import annotations
@@ -114,7 +114,7 @@ def uneven_requests(n: int, seed: int, max_nodes: int = 256, max_points: int = 8
     return configs, reqs
 
 
-def config4_requests(n: int, seed: int):
+def full_range_requests(n: int, seed: int):
     """Seeded uneven requests at the batched workload's full ranges, each with
     its own mirror and beam: f log-uniform in [1e3, 1e5], r_max = 2f,
     w0 = 0.6 f, N x N nodes with N = 2^U{7..10} (128^2 to 1024^2), Gaussian
