@@ -200,16 +200,16 @@ sc_status choose_class(sc_ctx* ctx, Lane& ln, Chunk& c, const Table* tab, int* c
 // chunk of its capacity (the next power of two >= n).
 constexpr double kRateSmall[65] = {
     0.0,
-    3.671, 4.803, 5.363, 5.954, 6.252, 6.760, 7.152, 7.663,  // 1..8
-    7.469, 8.022, 8.201, 8.904, 8.388, 9.027, 8.672, 9.210,  // 9..16
-    8.210, 8.684, 9.165, 9.648, 9.025, 9.443, 9.876, 10.282,  // 17..24
-    8.312, 8.647, 8.981, 9.281, 9.623, 9.949, 10.290, 10.556,  // 25..32
-    8.453, 8.702, 8.964, 9.217, 9.467, 9.716, 9.962, 10.231,  // 33..40
-    9.345, 9.569, 9.799, 10.008, 10.253, 10.483, 10.683, 10.914,  // 41..48
-    9.997, 10.203, 10.389, 10.592, 10.803, 10.982, 11.180, 11.409,  // 49..56
-    10.162, 10.324, 10.509, 10.676, 10.873, 11.042, 11.213, 11.340,  // 57..64
+    3.669, 4.907, 5.611, 6.067, 6.591, 7.171, 6.940, 7.982,  // 1..8
+    7.440, 8.268, 8.135, 8.854, 8.567, 9.226, 8.795, 9.347,  // 9..16
+    8.338, 8.819, 9.305, 9.805, 9.101, 9.525, 9.963, 10.373,  // 17..24
+    8.348, 8.683, 9.015, 9.312, 9.663, 9.988, 10.337, 10.594,  // 25..32
+    8.848, 9.108, 9.379, 9.639, 9.900, 10.170, 10.431, 10.707,  // 33..40
+    9.547, 9.778, 10.006, 10.222, 10.465, 10.702, 10.916, 11.151,  // 41..48
+    10.127, 10.333, 10.519, 10.727, 10.940, 11.126, 11.326, 11.552,  // 49..56
+    10.336, 10.506, 10.692, 10.859, 11.060, 11.229, 11.408, 11.539,  // 57..64
 };
-constexpr double kRateFull[6] = {11.342, 11.637, 11.995, 10.847, 11.053, 10.884};  // 64 .. 2048
+constexpr double kRateFull[6] = {11.536, 12.204, 12.196, 10.848, 11.060, 10.884};  // 64 .. 2048
 
 constexpr int kMaxChunk = 2048;
 
@@ -274,7 +274,7 @@ int next_chunk(int n, bool small)
 }
 
 // a launch bounded in evaluations still gives each resident CTA this many items
-constexpr double kMinItemsPerCta = 8.0;
+constexpr double kMinItemsPerCta = 4.0;
 
 // requests of at least this many (point, node) pairs per omega take the
 // splits at small omega counts

@@ -269,6 +269,10 @@ struct Server {
     static constexpr int kLanes = 4;
     static constexpr int kShortLanes = 2;
     bool priority = true;               // sc_ctx::serve_priority when the server started
+    // the server's own stream-ordered pool for ticket memory: it keeps what is
+    // freed and is warmed at start, so that admitting a request rarely has to
+    // grow device memory while other lanes' kernels run (nullptr: default pool)
+    cudaMemPool_t pool = nullptr;
     std::thread th;
     bool stop = false;
     std::condition_variable cv;

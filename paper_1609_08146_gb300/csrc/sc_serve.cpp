@@ -49,6 +49,12 @@ size_t ticket_bytes(const Ticket& t)
 
 sc_status launch_next_group(sc_ctx* ctx, Server* srv, int L);
 
+// Ticket memory, stream-ordered, from the server's pool when it has one.
+cudaError_t serve_alloc(Server* srv, void** p, size_t bytes, cudaStream_t s)
+{
+    return srv->pool ? cudaMallocFromPoolAsync(p, bytes, srv->pool, s) : cudaMallocAsync(p, bytes, s);
+}
+
 // Run one batch of admitted tickets on lane L (ctx->mu held).  A ticket
 // whose node tables cannot be built (an envelope too rough to fit, a device
 // allocation that failed) fails alone and leaves ids; the others run.
@@ -77,7 +83,7 @@ sc_status launch_batch(sc_ctx* ctx, Server* srv, int L, std::vector<uint64_t>& i
         t.tab->inflight++;
         run.push_back(id);
         if (t.own_pts) {
-            SC_CUDA(cudaMallocAsync((void**)&t.pts, (size_t)t.n_points * 3 * sizeof(double), ln.stream),
+            SC_CUDA(serve_alloc(srv, (void**)&t.pts, (size_t)t.n_points * 3 * sizeof(double), ln.stream),
                     "serving points");
             SC_CUDA(cudaMemcpyAsync(t.pts, t.host_pts.data(), (size_t)t.n_points * 3 * sizeof(double),
                                     cudaMemcpyHostToDevice, ln.stream), "stage points");
@@ -86,8 +92,8 @@ sc_status launch_batch(sc_ctx* ctx, Server* srv, int L, std::vector<uint64_t>& i
         }
         if (t.own_out) {
             const size_t ob = (size_t)t.n_omega * t.n_points * 3 * sizeof(float2);
-            SC_CUDA(cudaMallocAsync(&t.E, ob, ln.stream), "serving outputs");
-            SC_CUDA(cudaMallocAsync(&t.B, ob, ln.stream), "serving outputs");
+            SC_CUDA(serve_alloc(srv, &t.E, ob, ln.stream), "serving outputs");
+            SC_CUDA(serve_alloc(srv, &t.B, ob, ln.stream), "serving outputs");
         } else {
             t.E = t.E_user;
             t.B = t.B_user;
@@ -297,6 +303,28 @@ sc_status start_server(sc_ctx* ctx)
         }
         ln.own_stream = true;
     }
+    // The server's memory pool keeps what tickets free (no release threshold)
+    // and is warmed with min(budget / 8, 1 GiB): growing device memory while
+    // other lanes' kernels run can stall the server thread, which admits and
+    // launches everything.  Without a pool of its own it uses the default one.
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = ctx->device;
+    if (cudaMemPoolCreate(&srv->pool, &props) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(srv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        size_t warm = size_t(1) << 30;
+        if (ctx->budget) warm = std::min(warm, ctx->budget / 8);
+        void* p = nullptr;
+        cudaStream_t s0 = srv->lanes[0].stream;
+        if (warm && cudaMallocFromPoolAsync(&p, warm, srv->pool, s0) == cudaSuccess) cudaFreeAsync(p, s0);
+        cudaStreamSynchronize(s0);
+        cudaGetLastError();
+    } else {
+        srv->pool = nullptr;
+        cudaGetLastError();
+    }
     ctx->server = srv;
     srv->th = std::thread(serve, ctx);
     return SC_OK;
@@ -335,6 +363,7 @@ void stop_server(sc_ctx* ctx)
         free_lane(srv->lanes[L]);
         if (srv->done_ev[L]) cudaEventDestroy(srv->done_ev[L]);
     }
+    if (srv->pool) cudaMemPoolDestroy(srv->pool);  // its memory is all freed by now
     delete srv;
     ctx->server = nullptr;
 }
