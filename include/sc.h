@@ -493,7 +493,7 @@ sc_status sc_eval_batch(sc_ctx* ctx, const sc_request* reqs, int n_req, sc_eval_
  *   batches of up to 64 requests that close at 3e10 evaluations.  Long
  *   requests run one per lane on two lanes of the lowest priority, with their
  *   chunks cut by points into launches of about 6e10 evaluations (larger
- *   where that would leave a launch fewer than 8 work items per resident
+ *   where that would leave a launch fewer than 4 work items per resident
  *   CTA), each launched when the previous one completes.  A short request
  *   then waits for at most one such launch of a long one, never for all of
  *   it.  Results are bitwise those of the request alone either way.

@@ -23,7 +23,7 @@ namespace sch {
 //     highest priority, batched until a batch holds kShortBatchEvals;
 //   * long ones run one at a time on two lanes of the lowest priority, and
 //     their chunks are cut by points into launches of about kGroupEvals
-//     (more where that would leave fewer than 8 work items per resident CTA),
+//     (more where that would leave fewer than 4 work items per resident CTA),
 //     launched one after another as each completes.
 // The field kernels are persistent (their CTAs stay until a launch's work
 // is drained), so a running launch is never interrupted.  But when one of a
