@@ -119,13 +119,14 @@ def test_admission_by_budget():
 
 
 def test_short_requests_pass_a_long_one():
-    # a long request (512^2 nodes x 4160 points x 128 omegas = 1.4e11
-    # evaluations, above the 1e11 bound) runs on a low-priority lane in
-    # launches of about 6e10 evaluations; short requests submitted after it
-    # run on the high-priority lanes between those launches and finish first
+    # a long request (512^2 nodes x 4160 points x 256 omegas = 2.8e11
+    # evaluations, above the 1e11 bound; about 0.24 s) runs on a low-priority
+    # lane in launches of about 6e10 evaluations; short requests submitted
+    # after it run on the high-priority lanes between those launches and
+    # finish first
     ctx = sc.Context(0)
     try:
-        long_req = make(ctx, 6.25e4, 512, 512, 128, 4160, 3)
+        long_req = make(ctx, 6.25e4, 512, 512, 256, 4160, 3)
         small = [make(ctx, 1e3 * (1 + i), 64, 64, 16 + 8 * i, 500 + 100 * i, 20 + i,
                       pol=("linear", "radial", "azimuthal")[i % 3]) for i in range(4)]
         reqs = [long_req] + small
