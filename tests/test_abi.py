@@ -31,6 +31,27 @@ def test_library_exports_every_declared_symbol():
     assert set(names) == set(sc.SIGNATURES), set(names) ^ set(sc.SIGNATURES)
 
 
+def _header_constants():
+    """Every NAME = value enumerator of include/sc.h (comments removed)."""
+    txt = open(os.path.join(ROOT, "include", "sc.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return {k: int(v) for k, v in re.findall(r"\b(SC_[A-Z0-9_]+)\s*=\s*(-?\d+)\b", txt)}
+
+
+def test_binding_constants_match_the_header():
+    # the binding marshals statuses and option numbers as plain integers, so
+    # each of its SC_* names must carry the header's value
+    hdr = _header_constants()
+    assert len(hdr) >= 20
+    mine = {k: v for k, v in vars(sc).items() if k.startswith("SC_") and isinstance(v, int)}
+    common = set(hdr) & set(mine)
+    assert {"SC_OK", "SC_ERR_BUSY", "SC_OPT_SERVE_PRIORITY", "SC_OPT_TILE_LAYOUT"} <= common
+    for k in sorted(common):
+        assert mine[k] == hdr[k], (k, mine[k], hdr[k])
+    # every option the header declares is reachable from the binding
+    assert {k for k in hdr if k.startswith("SC_OPT_")} <= set(mine)
+
+
 def test_host_validation_without_gpu():
     lib = sc.load()
     h = ctypes.c_void_p()
